@@ -1,0 +1,152 @@
+"""TEST INFRASTRUCTURE: the CPU oracle of the spatial-join filter step.
+
+Plain, slow, obviously correct implementations of what the GPU path computes,
+written from the paper ("Parallel In-Memory Evaluation of Spatial Joins"):
+
+* ``brute``  -- the definition of Sec. 1, every pair tested (C);
+* ``sweep``  -- Algorithm 1, forward-scan plane sweep over the whole space (C);
+* ``pbsm``   -- uniform-grid PBSM with replication, per-tile sort by x_l,
+  Algorithm 1 per tile and the reference-point test of Eq. 1 (C);
+* ``tile_counts`` / ``cell`` -- the partitioning counts of Sec. 3.4 step 2;
+* ``features`` / ``mlp``    -- in :mod:`oracle.learned` (numpy, float64).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA
+library and never imports it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sj_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libsj_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no OpenMP, no vector intrinsics)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        F = ctypes.c_float
+        lib.orc_brute.restype = P
+        lib.orc_brute.argtypes = [P, I64, P, I64]
+        lib.orc_sweep.restype = P
+        lib.orc_sweep.argtypes = [P, I64, P, I64, P]
+        lib.orc_pbsm_ex.restype = P
+        lib.orc_pbsm_ex.argtypes = [P, I64, P, I64, I, I, F, F, F, F, P, P, P, P]
+        lib.orc_res_count.restype = I64
+        lib.orc_res_count.argtypes = [P]
+        lib.orc_res_failed.restype = I
+        lib.orc_res_failed.argtypes = [P]
+        lib.orc_res_copy.restype = None
+        lib.orc_res_copy.argtypes = [P, P]
+        lib.orc_res_free.restype = None
+        lib.orc_res_free.argtypes = [P]
+        lib.orc_cell.restype = I
+        lib.orc_cell.argtypes = [F, F, F, I]
+        lib.orc_tile_counts.restype = None
+        lib.orc_tile_counts.argtypes = [P, I64, I, I, F, F, F, F, P]
+        _lib = lib
+        return lib
+
+
+def _rects(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 4:
+        raise ValueError("rectangles must be float32[n, 4] (xl, yl, xu, yu)")
+    return a
+
+
+def _take(lib, res) -> np.ndarray:
+    if not res:
+        raise MemoryError("oracle: allocation failed or bad arguments")
+    try:
+        if lib.orc_res_failed(res):
+            raise MemoryError("oracle: result buffer allocation failed")
+        n = lib.orc_res_count(res)
+        out = np.empty((n, 2), np.int32)
+        if n:
+            lib.orc_res_copy(res, out.ctypes.data)
+        return out
+    finally:
+        lib.orc_res_free(res)
+
+
+def brute(R, S) -> np.ndarray:
+    """All intersecting pairs by testing every (r, s); int32[P, 2] sorted."""
+    lib = _load()
+    R, S = _rects(R), _rects(S)
+    return _take(lib, lib.orc_brute(R.ctypes.data, len(R), S.ctypes.data, len(S)))
+
+
+def sweep(R, S, return_candidates: bool = False):
+    """Algorithm 1 over the whole space; int32[P, 2] sorted by (r, s)."""
+    lib = _load()
+    R, S = _rects(R), _rects(S)
+    nc = ctypes.c_int64(0)
+    out = _take(lib, lib.orc_sweep(R.ctypes.data, len(R), S.ctypes.data, len(S),
+                                   ctypes.addressof(nc)))
+    return (out, nc.value) if return_candidates else out
+
+
+def pbsm(R, S, nx: int, ny: int | None = None, x0: float = 0.0, y0: float = 0.0,
+         x1: float = 1.0, y1: float = 1.0, per_tile: bool = False):
+    """Single-threaded PBSM on an nx x ny grid over [x0,x1] x [y0,y1].
+
+    Returns the sorted int32[P, 2] pairs; with ``per_tile`` also a dict of
+    int64[ny*nx] arrays ``cnt_r``, ``cnt_s`` (replicated entries per tile),
+    ``pairs`` (pairs reported by the tile) and the candidate count ``cand``
+    (pairs that x-intersect, examined by Algorithm 1's inner loops)."""
+    lib = _load()
+    ny = nx if ny is None else ny
+    R, S = _rects(R), _rects(S)
+    T = nx * ny
+    cr = np.zeros(T, np.int64) if per_tile else None
+    cs = np.zeros(T, np.int64) if per_tile else None
+    tp = np.zeros(T, np.int64) if per_tile else None
+    nc = ctypes.c_int64(0)
+    ptr = lambda a: a.ctypes.data if a is not None else None  # noqa: E731
+    out = _take(lib, lib.orc_pbsm_ex(R.ctypes.data, len(R), S.ctypes.data, len(S),
+                                     nx, ny, x0, y0, x1, y1, ptr(cr), ptr(cs), ptr(tp),
+                                     ctypes.addressof(nc)))
+    if per_tile:
+        return out, {"cnt_r": cr, "cnt_s": cs, "pairs": tp, "cand": nc.value}
+    return out
+
+
+def cell(v: float, g0: float, g1: float, n: int) -> int:
+    """Tile index of coordinate v on an n-tile axis over [g0, g1]."""
+    return _load().orc_cell(v, g0, g1, n)
+
+
+def tile_counts(A, nx: int, ny: int | None = None, x0=0.0, y0=0.0, x1=1.0, y1=1.0):
+    """Replicated entries per tile, int64[ny*nx] (row-major, row = y cell)."""
+    lib = _load()
+    ny = nx if ny is None else ny
+    A = _rects(A)
+    out = np.zeros(nx * ny, np.int64)
+    lib.orc_tile_counts(A.ctypes.data, len(A), nx, ny, x0, y0, x1, y1, out.ctypes.data)
+    return out

@@ -1,0 +1,351 @@
+/*
+ * sj_oracle.c -- TEST INFRASTRUCTURE: the plain, slow, single-threaded CPU
+ * oracle for the filter step of the partitioning-based spatial join (PBSM) of
+ * "Parallel In-Memory Evaluation of Spatial Joins" (Tsitsigkos, Bouros,
+ * Mamoulis, Terrovitis).
+ *
+ * Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+ * load this library.  It shares no code, header or constant with the CUDA
+ * library; neither includes the other.  Build: plain C, -O2
+ * -ffp-contract=off, no fast-math (so float compares and the two float
+ * operations of the cell function are exactly IEEE single precision).
+ *
+ * What it computes (Sec. 1): J = {(i,j) : R[i] and S[j] have at least one
+ * common point}, i.e. the closed test
+ *     R.xl <= S.xu && S.xl <= R.xu && R.yl <= S.yu && S.yl <= R.yu
+ * on the float32 values as given.  Three independent routes reach J:
+ *   orc_brute  -- the definition, all |R||S| pairs (tiny inputs only);
+ *   orc_sweep  -- Algorithm 1 (forward-scan plane sweep, Sec. 2.1) over the
+ *                 whole space, no partitioning;
+ *   orc_pbsm   -- PBSM on a uniform nx x ny grid (Sec. 1, Sec. 2.2): every
+ *                 rectangle is copied into every tile it overlaps (counted
+ *                 first, then written, Sec. 3.4 steps 2-4), each tile is
+ *                 sorted by x_l and joined with Algorithm 1, and a pair is
+ *                 reported only where its reference point lies (Eq. 1).
+ * All three return the pairs sorted by (r, s).
+ *
+ * Readings of the paper used here:
+ *  - Tile membership: cell(v) = clamp(floor((v - g0) * ginv), 0, n-1), with
+ *    ginv = (float)n / (g1 - g0) and the subtraction and product rounded
+ *    to float32.  The function is monotone in v, so it partitions the line;
+ *    coordinates outside [g0, g1] fall into the border tiles.
+ *  - Eq. 1 ("max{r.xl,s.xl} >= T.xl and max{r.yl,s.yl} >= T.yl") is taken
+ *    in tile-index form: cell_x(max xl) >= col and cell_y(max yl) >= row.
+ *    With the lower bound of tile col read as "the first value whose cell is
+ *    col", this is Eq. 1 exactly, and it avoids a float T.x_l that could
+ *    round differently from the assignment.  Both rectangles lie in the tile,
+ *    so ">=" can only hold as "==": the pair is reported in exactly one tile.
+ *  - The "top-left corner" of the prose is the lower corner of Eq. 1 (y axis
+ *    pointing down in the figure); Eq. 1 is followed.
+ *  - Ties r.x_l == s.x_l make s the pivot (the strict "<" of Algorithm 1).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct { float xl, yl, xu, yu; } orc_rect;
+typedef struct { float xl, yl, xu, yu; int32_t id; } orc_ent;
+typedef struct { int32_t r, s; } orc_pair;
+
+typedef struct {
+    orc_pair *p;
+    int64_t n, cap;
+    int failed;
+} orc_res;
+
+/* ---- result buffer --------------------------------------------------- */
+static void res_push(orc_res *res, int32_t r, int32_t s)
+{
+    if (res->failed) return;
+    if (res->n == res->cap) {
+        int64_t nc = res->cap ? 2 * res->cap : 1024;
+        orc_pair *q = (orc_pair *)realloc(res->p, (size_t)nc * sizeof(orc_pair));
+        if (!q) { res->failed = 1; return; }
+        res->p = q;
+        res->cap = nc;
+    }
+    res->p[res->n].r = r;
+    res->p[res->n].s = s;
+    res->n++;
+}
+
+static int cmp_pair(const void *a, const void *b)
+{
+    const orc_pair *x = (const orc_pair *)a, *y = (const orc_pair *)b;
+    if (x->r != y->r) return x->r < y->r ? -1 : 1;
+    if (x->s != y->s) return x->s < y->s ? -1 : 1;
+    return 0;
+}
+
+static orc_res *res_new(void) { return (orc_res *)calloc(1, sizeof(orc_res)); }
+
+static orc_res *res_finish(orc_res *res)
+{
+    if (res->n > 1) qsort(res->p, (size_t)res->n, sizeof(orc_pair), cmp_pair);
+    return res;
+}
+
+int64_t orc_res_count(const orc_res *res) { return res ? res->n : -1; }
+int orc_res_failed(const orc_res *res) { return res ? res->failed : 1; }
+void orc_res_copy(const orc_res *res, int32_t *out)
+{
+    if (res->n) memcpy(out, res->p, (size_t)res->n * sizeof(orc_pair));
+}
+void orc_res_free(orc_res *res)
+{
+    if (!res) return;
+    free(res->p);
+    free(res);
+}
+
+/* ---- the intersection test (Sec. 1: at least one common point) ------- */
+static int y_intersects(float ryl, float ryu, float syl, float syu)
+{
+    return ryl <= syu && syl <= ryu;
+}
+
+/* Definition, all pairs. */
+orc_res *orc_brute(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS)
+{
+    orc_res *res = res_new();
+    if (!res) return NULL;
+    for (int64_t i = 0; i < nR; i++)
+        for (int64_t j = 0; j < nS; j++)
+            if (R[i].xl <= S[j].xu && S[j].xl <= R[i].xu &&
+                R[i].yl <= S[j].yu && S[j].yl <= R[i].yu)
+                res_push(res, (int32_t)i, (int32_t)j);
+    return res_finish(res);
+}
+
+/* ---- Algorithm 1 ----------------------------------------------------- */
+static int cmp_ent_xl(const void *a, const void *b)
+{
+    const orc_ent *x = (const orc_ent *)a, *y = (const orc_ent *)b;
+    if (x->xl < y->xl) return -1;
+    if (x->xl > y->xl) return 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* Duplicate test context of one tile (Eq. 1 in tile-index form).  When
+ * `on` is 0 every candidate that intersects is reported (whole space). */
+typedef struct {
+    int on;
+    int col, row, nx, ny;
+    float gx0, gy0, ginvx, ginvy;
+} dedup_ctx;
+
+static int cell_of(float v, float g0, float ginv, int n)
+{
+    float t = (v - g0) * ginv;     /* two float32 roundings, no contraction */
+    float f = floorf(t);
+    if (!(f >= 0.0f)) return 0;
+    if (f >= (float)(n - 1)) return n - 1;
+    return (int)f;
+}
+
+static int report_here(const dedup_ctx *d, const orc_ent *r, const orc_ent *s)
+{
+    if (!d->on) return 1;
+    float mx = r->xl > s->xl ? r->xl : s->xl;
+    float my = r->yl > s->yl ? r->yl : s->yl;
+    return cell_of(mx, d->gx0, d->ginvx, d->nx) >= d->col &&
+           cell_of(my, d->gy0, d->ginvy, d->ny) >= d->row;
+}
+
+/* Forward-scan plane sweep of R and S, both already sorted by x_l. */
+static void alg1(const orc_ent *R, int64_t nr, const orc_ent *S, int64_t ns,
+                 const dedup_ctx *d, orc_res *res, int64_t *ncand)
+{
+    int64_t i = 0, j = 0, cand = 0;
+    while (i < nr && j < ns) {
+        if (R[i].xl < S[j].xl) {
+            /* r = R[i] is the pivot; scan S forward from s = S[j]. */
+            for (int64_t k = j; k < ns && R[i].xu >= S[k].xl; k++) {
+                cand++;
+                if (y_intersects(R[i].yl, R[i].yu, S[k].yl, S[k].yu) &&
+                    report_here(d, &R[i], &S[k]))
+                    res_push(res, R[i].id, S[k].id);
+            }
+            i++;
+        } else {
+            /* s = S[j] is the pivot; scan R forward from r = R[i]. */
+            for (int64_t k = i; k < nr && S[j].xu >= R[k].xl; k++) {
+                cand++;
+                if (y_intersects(R[k].yl, R[k].yu, S[j].yl, S[j].yu) &&
+                    report_here(d, &R[k], &S[j]))
+                    res_push(res, R[k].id, S[j].id);
+            }
+            j++;
+        }
+    }
+    if (ncand) *ncand += cand;
+}
+
+static orc_ent *to_entries(const orc_rect *A, int64_t n)
+{
+    orc_ent *e = (orc_ent *)malloc((size_t)(n ? n : 1) * sizeof(orc_ent));
+    if (!e) return NULL;
+    for (int64_t i = 0; i < n; i++) {
+        e[i].xl = A[i].xl; e[i].yl = A[i].yl;
+        e[i].xu = A[i].xu; e[i].yu = A[i].yu;
+        e[i].id = (int32_t)i;
+    }
+    return e;
+}
+
+/* Algorithm 1 over the whole space (no partitioning, no duplicates). */
+orc_res *orc_sweep(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
+                   int64_t *ncand)
+{
+    orc_res *res = res_new();
+    orc_ent *er = to_entries(R, nR), *es = to_entries(S, nS);
+    if (!res || !er || !es) { free(er); free(es); orc_res_free(res); return NULL; }
+    qsort(er, (size_t)nR, sizeof(orc_ent), cmp_ent_xl);   /* Alg. 1, line "sort" */
+    qsort(es, (size_t)nS, sizeof(orc_ent), cmp_ent_xl);
+    dedup_ctx d;
+    memset(&d, 0, sizeof d);
+    if (ncand) *ncand = 0;
+    alg1(er, nR, es, nS, &d, res, ncand);
+    free(er);
+    free(es);
+    return res_finish(res);
+}
+
+/* ---- PBSM on a uniform grid ------------------------------------------ */
+typedef struct {
+    int nx, ny;
+    float gx0, gy0, ginvx, ginvy;
+} grid_t;
+
+static grid_t make_grid(int nx, int ny, float x0, float y0, float x1, float y1)
+{
+    grid_t g;
+    g.nx = nx; g.ny = ny;
+    g.gx0 = x0; g.gy0 = y0;
+    g.ginvx = (float)nx / (x1 - x0);
+    g.ginvy = (float)ny / (y1 - y0);
+    return g;
+}
+
+/* Partitioning phase for one collection (Sec. 3.4 steps 2-4, one thread):
+ * count per tile, prefix-sum to segment starts, then write each rectangle
+ * into every tile it overlaps.  cnt has nx*ny slots, off nx*ny+1. */
+static orc_ent *partition(const orc_rect *A, int64_t n, const grid_t *g,
+                          int64_t *cnt, int64_t *off)
+{
+    int64_t T = (int64_t)g->nx * g->ny;
+    memset(cnt, 0, (size_t)T * sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++) {
+        int cx0 = cell_of(A[i].xl, g->gx0, g->ginvx, g->nx);
+        int cx1 = cell_of(A[i].xu, g->gx0, g->ginvx, g->nx);
+        int cy0 = cell_of(A[i].yl, g->gy0, g->ginvy, g->ny);
+        int cy1 = cell_of(A[i].yu, g->gy0, g->ginvy, g->ny);
+        for (int cy = cy0; cy <= cy1; cy++)
+            for (int cx = cx0; cx <= cx1; cx++)
+                cnt[(int64_t)cy * g->nx + cx]++;
+    }
+    off[0] = 0;
+    for (int64_t t = 0; t < T; t++) off[t + 1] = off[t] + cnt[t];
+    orc_ent *e = (orc_ent *)malloc((size_t)(off[T] ? off[T] : 1) * sizeof(orc_ent));
+    int64_t *cur = (int64_t *)malloc((size_t)(T ? T : 1) * sizeof(int64_t));
+    if (!e || !cur) { free(e); free(cur); return NULL; }
+    memcpy(cur, off, (size_t)T * sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++) {
+        int cx0 = cell_of(A[i].xl, g->gx0, g->ginvx, g->nx);
+        int cx1 = cell_of(A[i].xu, g->gx0, g->ginvx, g->nx);
+        int cy0 = cell_of(A[i].yl, g->gy0, g->ginvy, g->ny);
+        int cy1 = cell_of(A[i].yu, g->gy0, g->ginvy, g->ny);
+        for (int cy = cy0; cy <= cy1; cy++)
+            for (int cx = cx0; cx <= cx1; cx++) {
+                orc_ent *d = &e[cur[(int64_t)cy * g->nx + cx]++];
+                d->xl = A[i].xl; d->yl = A[i].yl;
+                d->xu = A[i].xu; d->yu = A[i].yu;
+                d->id = (int32_t)i;
+            }
+    }
+    free(cur);
+    return e;
+}
+
+/* Optional per-tile outputs: tile_cnt_r/s (|R_T|, |S_T|) and tile_pairs
+ * (pairs reported by tile T); each nx*ny long, or NULL. */
+orc_res *orc_pbsm_ex(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
+                     int nx, int ny, float x0, float y0, float x1, float y1,
+                     int64_t *tile_cnt_r, int64_t *tile_cnt_s, int64_t *tile_pairs,
+                     int64_t *ncand)
+{
+    if (nx < 1 || ny < 1 || !(x1 > x0) || !(y1 > y0)) return NULL;
+    grid_t g = make_grid(nx, ny, x0, y0, x1, y1);
+    int64_t T = (int64_t)nx * ny;
+    int64_t *cr = (int64_t *)malloc((size_t)T * sizeof(int64_t));
+    int64_t *cs = (int64_t *)malloc((size_t)T * sizeof(int64_t));
+    int64_t *orr = (int64_t *)malloc((size_t)(T + 1) * sizeof(int64_t));
+    int64_t *os = (int64_t *)malloc((size_t)(T + 1) * sizeof(int64_t));
+    orc_res *res = res_new();
+    orc_ent *er = NULL, *es = NULL;
+    if (!cr || !cs || !orr || !os || !res) goto fail;
+    er = partition(R, nR, &g, cr, orr);
+    es = partition(S, nS, &g, cs, os);
+    if (!er || !es) goto fail;
+    if (ncand) *ncand = 0;
+    /* Joining phase (Sec. 3.4 steps 5-6): per tile, sort both sides by x_l,
+     * then Algorithm 1 with the duplicate test of Eq. 1. */
+    for (int64_t t = 0; t < T; t++) {
+        orc_ent *rt = er + orr[t], *st = es + os[t];
+        int64_t nr = cr[t], ns = cs[t];
+        if (tile_cnt_r) tile_cnt_r[t] = nr;
+        if (tile_cnt_s) tile_cnt_s[t] = ns;
+        int64_t before = res->n;
+        if (nr && ns) {
+            qsort(rt, (size_t)nr, sizeof(orc_ent), cmp_ent_xl);
+            qsort(st, (size_t)ns, sizeof(orc_ent), cmp_ent_xl);
+            dedup_ctx d;
+            d.on = 1;
+            d.col = (int)(t % nx);
+            d.row = (int)(t / nx);
+            d.nx = nx; d.ny = ny;
+            d.gx0 = g.gx0; d.gy0 = g.gy0;
+            d.ginvx = g.ginvx; d.ginvy = g.ginvy;
+            alg1(rt, nr, st, ns, &d, res, ncand);
+        }
+        if (tile_pairs) tile_pairs[t] = res->n - before;
+    }
+    free(cr); free(cs); free(orr); free(os); free(er); free(es);
+    return res_finish(res);
+fail:
+    free(cr); free(cs); free(orr); free(os); free(er); free(es);
+    orc_res_free(res);
+    return NULL;
+}
+
+orc_res *orc_pbsm(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
+                  int nx, int ny, float x0, float y0, float x1, float y1)
+{
+    return orc_pbsm_ex(R, nR, S, nS, nx, ny, x0, y0, x1, y1, NULL, NULL, NULL, NULL);
+}
+
+/* The cell function alone, for tests of the per-tile counts. */
+int orc_cell(float v, float g0, float g1, int n)
+{
+    float ginv = (float)n / (g1 - g0);
+    return cell_of(v, g0, ginv, n);
+}
+
+/* Per-tile counts of one collection (Sec. 3.4 step 2), int64[nx*ny]. */
+void orc_tile_counts(const orc_rect *A, int64_t n, int nx, int ny,
+                     float x0, float y0, float x1, float y1, int64_t *cnt)
+{
+    grid_t g = make_grid(nx, ny, x0, y0, x1, y1);
+    int64_t T = (int64_t)nx * ny;
+    memset(cnt, 0, (size_t)T * sizeof(int64_t));
+    for (int64_t i = 0; i < n; i++) {
+        int cx0 = cell_of(A[i].xl, g.gx0, g.ginvx, nx);
+        int cx1 = cell_of(A[i].xu, g.gx0, g.ginvx, nx);
+        int cy0 = cell_of(A[i].yl, g.gy0, g.ginvy, ny);
+        int cy1 = cell_of(A[i].yu, g.gy0, g.ginvy, ny);
+        for (int cy = cy0; cy <= cy1; cy++)
+            for (int cx = cx0; cx <= cx1; cx++)
+                cnt[(int64_t)cy * nx + cx]++;
+    }
+}
