@@ -1,0 +1,331 @@
+"""Benchmark of the spatial-join filter step on one GB300 (or N, one process
+per GPU, each joining its own independent workload: weak scaling).
+
+Workload: the GIS-shaped plain join, |R| = 10M, |S| = 20M float32 MBRs
+(64-component Gaussian mixture + 20% uniform background, log-normal extents
+with median 2e-5), on a uniform grid (default 3000 x 3000, the rule of thumb
+"tile extent about 10x the average rectangle extent").  A step is one full
+join: partition (count, scan, scatter), per-tile sort, sweep, duplicate test
+and output, device-resident inputs -> device pair buffer with its count on
+the host.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1908_11740_gb300 import inputs  # noqa: E402
+
+METRIC = "join time and result pairs/s on 1 GB300; learned one-pass vs plain two-pass"
+UNIT = "pairs/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=3000)
+    ap.add_argument("--mode", default="two_pass")
+    ap.add_argument("--n-r", type=int, default=10_000_000)
+    ap.add_argument("--n-s", type=int, default=20_000_000)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--cpu-frac", type=float, default=0.125,
+                    help="CPU sample: rectangles whose centre has y < frac")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"GIS-shaped plain join |R|={a.n_r:,} |S|={a.n_s:,} fp32 MBRs, 64-comp Gaussian mixture "
+            f"+20% uniform, log-normal extents median 2e-5 sigma 1; grid {a.grid}x{a.grid}")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic():
+    """ncu DRAM bytes per launch of the dominant kernel, from the committed
+    profile summary (None when absent or stale)."""
+    p = os.path.join(ROOT, "profiles", "traffic_gis_10Mx20M.txt")
+    out = {}
+    if os.path.exists(p):
+        for line in open(p):
+            line = line.split("#")[0].strip()
+            if ":" in line:
+                k, v = line.split(":", 1)
+                try:
+                    out[k.strip()] = float(v)
+                except ValueError:
+                    pass
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.seek(0)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample(R, S, frac):
+    """Sub-join of the rectangles whose centre lies in the strip y < frac
+    (every tile row of that strip, same tile size as the GPU grid)."""
+    r = R[(R[:, 1] + R[:, 3]) * 0.5 < frac]
+    s = S[(S[:, 1] + S[:, 3]) * 0.5 < frac]
+    return r, s
+
+
+def run_cpu_oracle(R, S, args, reps=1):
+    import oracle
+
+    r, s = cpu_sample(R, S, args.cpu_frac)
+    ny = max(1, int(round(args.grid * args.cpu_frac)))
+    times, npairs = [], 0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        p = oracle.pbsm(r, s, args.grid, ny, 0.0, 0.0, 1.0, args.cpu_frac)
+        times.append(time.perf_counter() - t0)
+        npairs = len(p)
+    t = statistics.median(times)
+    return {"value": npairs / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"single-threaded oracle PBSM on the strip y<{args.cpu_frac} of the same workload "
+                       f"({len(r):,} x {len(s):,} rectangles, {npairs:,} pairs, grid {args.grid}x{ny}), "
+                       f"{t:.2f} s per run")}, t
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    R, S = inputs.gis_pair(args.n_r, args.n_s, seed=args.seed)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up runs would only burn CPU time
+    vals = []
+    cb = None
+    for _ in range(args.steps):
+        cb, t = run_cpu_oracle(R, S, args)
+        vals.append(t)
+    t = statistics.median(vals)
+    value = cb["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args), "grid": args.grid, "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# algorithmic bytes per launch of each single-kernel phase
+def alg_bytes(phase, n_in, E, P):
+    return {"count": 16 * n_in, "scatter": 16 * n_in + 20 * E, "sweep_count": 20 * E,
+            "sweep_write": 20 * E + 8 * P}.get(phase)
+
+
+KERNEL_OF_PHASE = {"count": "k_count", "scatter": "k_scatter", "sweep_count": "k_sweep_chunks<COUNT>",
+                   "sweep_write": "k_sweep_chunks<WRITE>"}
+
+
+def ours(args):
+    import torch
+
+    from paper_1908_11740_gb300 import build, sj
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    # each rank joins its own independent workload (weak scaling)
+    R, S = inputs.gis_pair(args.n_r, args.n_s, seed=args.seed + rank)
+    hR = torch.from_numpy(R).pin_memory()
+    hS = torch.from_numpy(S).pin_memory()
+    dR, dS = hR.cuda(), hS.cuda()
+    ctx = sj.sj_create(local)
+    grid = sj.make_grid(args.grid)
+    opts = sj.make_opts(args.mode)
+    stream = torch.cuda.current_stream()
+
+    P = 0
+    for _ in range(max(3, args.warmup)):
+        P = sj.sj_join(ctx, dR, dS, grid, opts).shape[0]
+    cr, cs, _ = sj.sj_tile_stats(ctx, dR, dS, grid)
+    E = int(cr.sum().item()) + int(cs.sum().item())
+    del cr, cs
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sj.sj_timing_enable(ctx, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        out = sj.sj_join(ctx, dR, dS, grid, opts)
+        del out
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    timing = sj.sj_timing_read(ctx)
+    sj.sj_timing_enable(ctx, False)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tp = torch.tensor([float(P)], device="cuda")
+        dist.all_reduce(tp, op=dist.ReduceOp.SUM)
+        p_all = float(tp.item())
+    else:
+        p_all = float(P)
+    value = p_all / (ms / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host arrays)
+    hout = torch.empty((P + 1024, 2), dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        sj.sj_join_host(ctx, hR, hS, grid, hout, opts)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        res = sj.sj_join_host(ctx, hR, hS, grid, hout, opts)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    assert res.shape[0] == P
+
+    phases = {k: v for k, v in timing.items() if k != "launches" and v[0] > 0}
+    n_in = args.n_r + args.n_s
+    cand = {k: v for k, v in phases.items() if k in KERNEL_OF_PHASE}
+    dom = max(cand, key=lambda k: cand[k][1])
+    dom_ms = cand[dom][1] / cand[dom][0]
+    ab = alg_bytes(dom, n_in, E, P)
+    peak, peak_kind = load_peaks()
+    achieved = ab / (dom_ms / 1e3) / 1e9
+    traffic = load_traffic().get(KERNEL_OF_PHASE[dom])
+    b_join = 16 * n_in + 40 * E + 8 * P
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu, _ = run_cpu_oracle(R, S, args)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(args), "grid": args.grid, "mode": args.mode,
+                       "pairs": P, "entries": E, "l2": "inputs 480 MB > 129 MB L2 (no flush needed)",
+                       "per_rank": "independent join per GPU, seed 2 + rank"},
+            "roofline": {"bound": "hbm", "kernel": KERNEL_OF_PHASE[dom], "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         else "fallback 6.8 TB/s", "traffic": traffic,
+                         "alg_bytes_per_launch": ab, "launch_ms": dom_ms},
+            "join_roofline": {"alg_bytes": b_join, "achieved_gbs": b_join / (ms / 1e3) / 1e9,
+                              "frac": b_join / (ms / 1e3) / 1e9 / peak},
+            "phases_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in phases.items()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": p_all / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": 16 * n_in, "d2h_bytes_per_step": 8 * P,
+                    "api": "sj_join_host (pinned host buffers)"},
+            "clocks": clk,
+            "gpu_launches": timing["launches"],
+        }
+        print(json.dumps(line), flush=True)
+    sj.sj_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

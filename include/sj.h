@@ -1,0 +1,207 @@
+/*
+ * sj.h -- C ABI of the GB300 (sm_103a) spatial-join filter step.
+ *
+ * The library computes the filter step of the partitioning-based spatial
+ * join (PBSM) studied in "Parallel In-Memory Evaluation of Spatial Joins"
+ * (Tsitsigkos, Bouros, Mamoulis, Terrovitis): given two collections R and S
+ * of axis-aligned rectangles (MBRs), it returns every pair (r, s) whose
+ * rectangles have at least one common point (Sec. 1), each pair exactly once.
+ *
+ * Method (all steps run as CUDA kernels on the device):
+ *   1. uniform nx x ny grid; each rectangle is assigned to every tile it
+ *      overlaps (multi-assignment, Sec. 2.2), with the count -> prefix-sum ->
+ *      write scheme of Sec. 3.4 steps 2-4;
+ *   2. per tile, both sides are sorted by the lower x endpoint x_l
+ *      (Algorithm 1, "sort"; Sec. 3.4 step 5);
+ *   3. per tile, a forward-scan plane sweep (Algorithm 1) with a y-overlap
+ *      test; a pair is reported only by the tile that holds the reference
+ *      point (max x_l, max y_l) of the intersection (Eq. 1, Sec. 3.2).
+ *
+ * Conventions for every entry point:
+ *  - Rectangle and pair pointers marked d_ are DEVICE pointers on the
+ *    context's device; the caller owns them and keeps them alive until the
+ *    context's stream has passed the call.  h_ pointers are host memory.
+ *  - Rectangles are sj_rect (16 bytes, float32 xl, yl, xu, yu); d_R / d_S
+ *    must be 16-byte aligned.  Valid input: every coordinate finite,
+ *    xl <= xu, yl <= yu.  0 <= n <= SJ_MAX_N.
+ *  - Intersection is closed: touching edges and corners count.  Comparisons
+ *    are exact float32 compares (no arithmetic on coordinates other than the
+ *    cell function), so the result does not depend on the grid.
+ *  - Pair ids are 0-based indices into R and S.  Pair order is unspecified
+ *    unless sj_opts.sort_output is set (then ascending by (r, s)).
+ *  - All work is enqueued on the context's stream.  Calls that return a
+ *    count to the host synchronise that stream once at the end (and the
+ *    two-pass join once more, after counting, to size its output).
+ *  - Status codes are returned; nothing aborts and no exception crosses the
+ *    ABI.  sj_last_error() gives a message for the last failure.
+ *  - A context is not thread-safe; use one context per host thread/stream.
+ */
+#ifndef SJ_H
+#define SJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------- */
+#define SJ_OK         0
+#define SJ_EINVAL     1   /* bad argument, NaN/Inf coordinate, xl > xu, size limit */
+#define SJ_ENOMEM     2   /* an allocation failed                                 */
+#define SJ_EOVERFLOW  3   /* caller-owned output too small (see sj_join_into)     */
+#define SJ_ETIMEOUT   4   /* a bounded device-side wait gave up                   */
+#define SJ_ECUDA      5   /* a CUDA runtime call failed                           */
+#define SJ_EINTERNAL  6   /* an internal consistency check failed                 */
+
+#define SJ_MAX_N      ((int64_t)1 << 30)   /* ids carry two flag bits above bit 29 */
+#define SJ_MAX_TILES  ((int64_t)1 << 26)   /* nx * ny                               */
+
+/* ---- plain data types ------------------------------------------------- */
+typedef struct { float xl, yl, xu, yu; } sj_rect;       /* an MBR, Sec. 1        */
+typedef struct { int32_t r, s; } sj_pair;               /* one result of J       */
+
+/* Uniform grid over [x0, x1] x [y0, y1] with nx columns and ny rows (Sec. 2.2;
+ * ny = 1 gives vertical stripes, Sec. 3.1).  Tile (col, row) has index
+ * row * nx + col.  A coordinate v falls in column
+ *   clamp(floor((v - x0) * gx), 0, nx - 1),  gx = (float)nx / (x1 - x0),
+ * with the subtraction and the product each rounded to float32; rows alike.
+ * Rectangles outside the grid's extent land in the border tiles, so the
+ * extent only shapes the partitioning, never the result. */
+typedef struct { int32_t nx, ny; float x0, y0, x1, y1; } sj_grid;
+
+/* Join modes. */
+#define SJ_TWO_PASS      0   /* count pairs, allocate exactly, sweep again and write   */
+#define SJ_ONE_PASS      1   /* sweep once into a buffer sized by the learned
+                                per-tile predictor; exact two-pass rerun of the
+                                chunks that do not fit                                 */
+#define SJ_ONE_PASS_HEUR 2   /* as SJ_ONE_PASS, sized by the Eq. 2 histogram estimate  */
+#define SJ_AUTO          3   /* SJ_ONE_PASS when a model is loaded, else SJ_TWO_PASS   */
+
+typedef struct {
+    int32_t mode;         /* one of the modes above                          */
+    int32_t sort_output;  /* nonzero: pairs ascending by (r, s)              */
+    float   margin;       /* one-pass capacity = predicted * (1 + margin) + slack */
+    int32_t reserved;     /* must be 0                                      */
+} sj_opts;
+
+typedef struct sj_ctx sj_ctx;     /* device, stream, allocator, workspace    */
+typedef struct sj_part sj_part;   /* a partitioned (R, S, grid)              */
+
+/* Optional allocator for every device buffer the library obtains (workspace
+ * and result buffers).  alloc returns a device pointer aligned to 256 bytes
+ * or NULL; free releases one.  Default: cudaMallocAsync / cudaFreeAsync on
+ * the context's stream. */
+typedef void *(*sj_alloc_fn)(size_t bytes, void *user);
+typedef void (*sj_free_fn)(void *ptr, void *user);
+
+/* ---- context ---------------------------------------------------------- */
+/* Create a context on `device` issuing all work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle.  Returns SJ_EINVAL for a bad device, SJ_ECUDA / SJ_ENOMEM. */
+int sj_create(sj_ctx **out, int device, void *cuda_stream);
+
+/* Release the context and its workspace (synchronises its stream). */
+int sj_destroy(sj_ctx *ctx);
+
+/* Install (alloc, free, user) as the context's allocator; both NULL restores
+ * the default.  Frees the current workspace. */
+int sj_set_allocator(sj_ctx *ctx, sj_alloc_fn alloc, sj_free_fn free_fn, void *user);
+
+/* Free a buffer the library returned (a pair buffer of sj_join). */
+void sj_free(sj_ctx *ctx, void *d_ptr);
+
+/* Message of the last failure on this context ("" if none); static text for
+ * a status code. */
+const char *sj_last_error(sj_ctx *ctx);
+const char *sj_strerror(int status);
+
+/* ---- partitioning (Sec. 3.4 steps 2-4) -------------------------------- */
+/* Partition R and S on grid *g: per-tile counts, exclusive prefix sums and
+ * the replicated entries of every tile, contiguous per tile.  *out receives
+ * a handle that owns that device state; reuse it with sj_part_join and
+ * release it with sj_part_free.  Synchronises once (to size the entries).
+ * Errors: SJ_EINVAL (arguments or invalid rectangles), SJ_ENOMEM. */
+int sj_partition(sj_ctx *ctx, const sj_rect *d_R, int64_t nR,
+                 const sj_rect *d_S, int64_t nS, const sj_grid *g, sj_part **out);
+
+/* Per-tile state of a partition, for inspection (all device pointers owned
+ * by the partition, valid until sj_part_free):
+ *   off    : uint32[2 * (T + 1)], (R offset, S offset) per tile, exclusive
+ *            prefix sums of the per-tile counts; off[2T], off[2T+1] = E_R, E_S
+ *   ent_r  : float4[E_R] the replicated R rectangles, grouped by tile
+ *   id_r   : uint32[E_R] original index | 1<<30 if the tile is the first
+ *            column the rectangle covers | 1<<31 if it is the first row
+ *   ent_s, id_s : the same for S
+ * Order inside a tile's segment is unspecified.  T = nx * ny. */
+typedef struct {
+    int64_t n_tiles, e_r, e_s;
+    const void *off, *ent_r, *id_r, *ent_s, *id_s;
+} sj_part_view;
+int sj_part_view_get(const sj_part *p, sj_part_view *out);
+
+/* Join a partition (steps 5-6 and Eq. 1).  Same output contract as sj_join. */
+int sj_part_join(sj_ctx *ctx, sj_part *p, const sj_opts *o,
+                 sj_pair **d_pairs, int64_t *npairs);
+
+void sj_part_free(sj_part *p);
+
+/* ---- joins -------------------------------------------------------------- */
+/* Exact number of result pairs of R join S on grid *g, without writing
+ * pairs (partition + sort + sweep in count mode).  *out_npairs on host. */
+int sj_count(sj_ctx *ctx, const sj_rect *d_R, int64_t nR,
+             const sj_rect *d_S, int64_t nS, const sj_grid *g, int64_t *out_npairs);
+
+/* Full filter step.  On SJ_OK, *d_pairs receives a device buffer holding
+ * *npairs sj_pair (allocated with the context's allocator; release it with
+ * sj_free, or through the installed allocator's owner), or NULL when
+ * *npairs == 0.  o may be NULL (two-pass, unsorted). */
+int sj_join(sj_ctx *ctx, const sj_rect *d_R, int64_t nR,
+            const sj_rect *d_S, int64_t nS, const sj_grid *g, const sj_opts *o,
+            sj_pair **d_pairs, int64_t *npairs);
+
+/* As sj_join but writing into a caller-owned device buffer of `cap` pairs.
+ * If the result does not fit, nothing beyond cap is written, *npairs gets
+ * the required count and SJ_EOVERFLOW is returned. */
+int sj_join_into(sj_ctx *ctx, const sj_rect *d_R, int64_t nR,
+                 const sj_rect *d_S, int64_t nS, const sj_grid *g, const sj_opts *o,
+                 sj_pair *d_buf, int64_t cap, int64_t *npairs);
+
+/* Per-tile statistics of a join on grid *g (device outputs, caller-owned,
+ * each nx*ny long; any may be NULL): replicated entries per side and the
+ * exact number of pairs each tile reports.  Used to train and judge the
+ * per-tile result-count predictor.  Synchronises once. */
+int sj_tile_stats(sj_ctx *ctx, const sj_rect *d_R, int64_t nR,
+                  const sj_rect *d_S, int64_t nS, const sj_grid *g,
+                  uint32_t *d_cnt_r, uint32_t *d_cnt_s, uint32_t *d_pairs_per_tile);
+
+/* ---- host buffers ------------------------------------------------------ */
+/* sj_join for HOST arrays: copies R and S to the device (into the context's
+ * workspace), joins them, and copies the pairs back into h_out (cap pairs).
+ * If the result has more than cap pairs, *npairs gets the required count
+ * and SJ_EOVERFLOW is returned (h_out untouched).  Page-locked host memory
+ * makes the copies asynchronous.  Synchronises the context's stream. */
+int sj_join_host(sj_ctx *ctx, const sj_rect *h_R, int64_t nR, const sj_rect *h_S, int64_t nS,
+                 const sj_grid *g, const sj_opts *o, sj_pair *h_out, int64_t cap,
+                 int64_t *npairs);
+
+/* ---- device-side timing ------------------------------------------------- */
+/* When enabled, every phase of every join is bracketed by CUDA events on the
+ * context's stream; sj_timing_read synchronises the stream and returns the
+ * summed device time of each phase since the last enable/read, with the
+ * number of kernel launches.  Phase names: sj_timing_phase_name(i). */
+#define SJ_NPHASE 12
+typedef struct {
+    int64_t launches;        /* kernels of this library launched (all phases)  */
+    int64_t n[SJ_NPHASE];    /* timed occurrences of each phase                 */
+    double ms[SJ_NPHASE];    /* summed device milliseconds of each phase        */
+} sj_timing;
+int sj_timing_enable(sj_ctx *ctx, int on);
+int sj_timing_read(sj_ctx *ctx, sj_timing *out);
+const char *sj_timing_phase_name(int phase);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SJ_H */

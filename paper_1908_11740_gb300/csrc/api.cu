@@ -1,0 +1,781 @@
+// api.cu -- the C ABI of include/sj.h: contexts, the allocator, a grow-only
+// device workspace, and the host orchestration of the kernels of the
+// partitioning-based spatial join (PBSM) filter step.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "../../include/sj.h"
+#include "sj_common.cuh"
+#include "sj_internal.h"
+#include "sj_kernels.h"
+
+using namespace sj;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+extern "C" const char *sj_strerror(int status) {
+    switch (status) {
+        case SJ_OK: return "ok";
+        case SJ_EINVAL: return "invalid argument or input";
+        case SJ_ENOMEM: return "out of device memory";
+        case SJ_EOVERFLOW: return "output buffer too small";
+        case SJ_ETIMEOUT: return "device-side wait timed out";
+        case SJ_ECUDA: return "CUDA runtime error";
+        case SJ_EINTERNAL: return "internal error";
+        default: return "unknown status";
+    }
+}
+
+int sj::fail(sj_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->msg, sizeof(ctx->msg), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+int sj::cuda_fail(sj_ctx *ctx, cudaError_t e, const char *where) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(ctx, SJ_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+    return fail(ctx, SJ_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+extern "C" const char *sj_last_error(sj_ctx *ctx) { return ctx ? ctx->msg : "no context"; }
+
+// ---------------------------------------------------------------------------
+// allocation
+// ---------------------------------------------------------------------------
+void *sj::dev_alloc(sj_ctx *ctx, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (ctx->alloc) return ctx->alloc(bytes, ctx->user);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void sj::dev_free(sj_ctx *ctx, void *p) {
+    if (!p) return;
+    if (ctx->alloc) {
+        if (ctx->free_fn) ctx->free_fn(p, ctx->user);
+        return;
+    }
+    cudaFreeAsync(p, ctx->stream);
+}
+
+// Grow `b` to hold at least `bytes` (contents are not kept).
+int sj::ensure(sj_ctx *ctx, Buf &b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return SJ_OK;
+    dev_free(ctx, b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = bytes + bytes / 8 + 256;
+    want = (want + 255) & ~(size_t)255;
+    void *p = dev_alloc(ctx, want);
+    if (!p) return fail(ctx, SJ_ENOMEM, "device allocation of %zu bytes failed", want);
+    b.p = p;
+    b.bytes = want;
+    return SJ_OK;
+}
+
+void sj::release(sj_ctx *ctx, Workspace &w) {
+    Buf *all[] = {&w.stats, &w.cnt, &w.off, &w.bsum, &w.ts, &w.large, &w.ent_r, &w.id_r,
+                  &w.ent_s, &w.id_s, &w.seg_off, &w.seg_src, &w.seg_vb, &w.hist, &w.key_a,
+                  &w.key_b, &w.val_a, &w.val_b, &w.lmbr, &w.lid, &w.pc, &w.poff, &w.resv,
+                  &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out};
+    for (Buf *b : all) {
+        dev_free(ctx, b->p);
+        b->p = nullptr;
+        b->bytes = 0;
+    }
+    w.cap_r = w.cap_s = 0;
+}
+
+// ---------------------------------------------------------------------------
+// device-side timing
+// ---------------------------------------------------------------------------
+static const char *kPhaseNames[PH_N] = {"reset",        "count",       "scan",
+                                        "scatter",      "large_sort",  "sweep_count",
+                                        "pair_scan",    "sweep_write", "large_sweep_count",
+                                        "large_sweep_write", "model",  "other"};
+
+static cudaEvent_t take_event(Timer &t) {
+    if (!t.pool.empty()) {
+        cudaEvent_t e = t.pool.back();
+        t.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+sj::PhaseScope::PhaseScope(sj_ctx *c, int ph, int kernels) : ctx(c), phase(ph) {
+    ctx->launches += kernels;
+    if (ctx->timer.on) {
+        a = take_event(ctx->timer);
+        if (a) cudaEventRecord(a, ctx->stream);
+    }
+}
+
+sj::PhaseScope::~PhaseScope() {
+    if (!a) return;
+    cudaEvent_t b = take_event(ctx->timer);
+    if (!b) return;
+    cudaEventRecord(b, ctx->stream);
+    ctx->timer.pending.push_back({phase, a, b});
+}
+
+static void timing_resolve(sj_ctx *ctx) {
+    Timer &t = ctx->timer;
+    if (t.pending.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &r : t.pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            t.ms[r.phase] += ms;
+            t.n[r.phase] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        t.pool.push_back(r.a);
+        t.pool.push_back(r.b);
+    }
+    t.pending.clear();
+}
+
+extern "C" int sj_timing_enable(sj_ctx *ctx, int on) {
+    if (!ctx) return SJ_EINVAL;
+    DeviceGuard g(ctx->device);
+    timing_resolve(ctx);
+    ctx->timer.on = on != 0;
+    for (int i = 0; i < PH_N; i++) {
+        ctx->timer.ms[i] = 0;
+        ctx->timer.n[i] = 0;
+    }
+    ctx->launches = 0;
+    return SJ_OK;
+}
+
+extern "C" int sj_timing_read(sj_ctx *ctx, sj_timing *out) {
+    if (!ctx || !out) return SJ_EINVAL;
+    DeviceGuard g(ctx->device);
+    timing_resolve(ctx);
+    memset(out, 0, sizeof *out);
+    out->launches = ctx->launches;
+    for (int i = 0; i < PH_N && i < SJ_NPHASE; i++) {
+        out->ms[i] = ctx->timer.ms[i];
+        out->n[i] = ctx->timer.n[i];
+        ctx->timer.ms[i] = 0;
+        ctx->timer.n[i] = 0;
+    }
+    ctx->launches = 0;
+    return SJ_OK;
+}
+
+extern "C" const char *sj_timing_phase_name(int phase) {
+    return (phase >= 0 && phase < PH_N) ? kPhaseNames[phase] : "";
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" int sj_create(sj_ctx **out, int device, void *cuda_stream) {
+    if (!out) return SJ_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return SJ_EINVAL;
+    }
+    sj_ctx *c = new (std::nothrow) sj_ctx();
+    if (!c) return SJ_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    DeviceGuard g(device);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return SJ_ECUDA;
+    }
+    if (sweep_setup() != cudaSuccess) {
+        delete c;
+        return SJ_ECUDA;
+    }
+    c->sweep_bps = sweep_blocks_per_sm();
+    if (cudaMallocHost(&c->h_stats, sizeof(Stats)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SJ_ENOMEM;
+    }
+    c->msg[0] = 0;
+    *out = c;
+    return SJ_OK;
+}
+
+extern "C" int sj_destroy(sj_ctx *ctx) {
+    if (!ctx) return SJ_EINVAL;
+    DeviceGuard g(ctx->device);
+    release(ctx, ctx->ws);
+    mlp_release(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    timing_resolve(ctx);
+    for (cudaEvent_t e : ctx->timer.pool) cudaEventDestroy(e);
+    cudaFreeHost(ctx->h_stats);
+    delete ctx;
+    return SJ_OK;
+}
+
+extern "C" int sj_set_allocator(sj_ctx *ctx, sj_alloc_fn alloc, sj_free_fn free_fn, void *user) {
+    if (!ctx) return SJ_EINVAL;
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(ctx, SJ_EINVAL, "allocator needs both alloc and free (or neither)");
+    DeviceGuard g(ctx->device);
+    release(ctx, ctx->ws);
+    mlp_release(ctx);
+    ctx->alloc = alloc;
+    ctx->free_fn = free_fn;
+    ctx->user = user;
+    return SJ_OK;
+}
+
+extern "C" void sj_free(sj_ctx *ctx, void *d_ptr) {
+    if (!ctx || !d_ptr) return;
+    DeviceGuard g(ctx->device);
+    dev_free(ctx, d_ptr);
+}
+
+// ---------------------------------------------------------------------------
+// argument checks
+// ---------------------------------------------------------------------------
+int sj::check_inputs(sj_ctx *ctx, const sj_rect *R, int64_t nR, const sj_rect *S, int64_t nS,
+                     const sj_grid *g, GridDev *gd) {
+    if (!ctx) return SJ_EINVAL;
+    if (nR < 0 || nS < 0 || nR >= SJ_MAX_N || nS >= SJ_MAX_N)
+        return fail(ctx, SJ_EINVAL, "sizes must satisfy 0 <= n < 2^30 (got %lld, %lld)",
+                    (long long)nR, (long long)nS);
+    if ((nR && !R) || (nS && !S)) return fail(ctx, SJ_EINVAL, "null rectangle pointer");
+    if (((uintptr_t)R & 15) || ((uintptr_t)S & 15))
+        return fail(ctx, SJ_EINVAL, "rectangle arrays must be 16-byte aligned");
+    if (!g) return fail(ctx, SJ_EINVAL, "null grid");
+    if (g->nx < 1 || g->ny < 1 || g->nx > (1 << 24) || g->ny > (1 << 24) ||
+        (int64_t)g->nx * g->ny > SJ_MAX_TILES)
+        return fail(ctx, SJ_EINVAL, "grid %d x %d out of range", g->nx, g->ny);
+    if (!isfinite(g->x0) || !isfinite(g->x1) || !isfinite(g->y0) || !isfinite(g->y1) ||
+        !(g->x1 > g->x0) || !(g->y1 > g->y0))
+        return fail(ctx, SJ_EINVAL, "grid extent must be finite with x1 > x0, y1 > y0");
+    volatile float wx = g->x1 - g->x0, wy = g->y1 - g->y0;
+    volatile float gx = (float)g->nx / wx, gy = (float)g->ny / wy;
+    if (!isfinite(gx) || !isfinite(gy) || !(gx > 0.0f) || !(gy > 0.0f))
+        return fail(ctx, SJ_EINVAL, "grid resolution overflows float32");
+    gd->nx = g->nx;
+    gd->ny = g->ny;
+    gd->x0 = g->x0;
+    gd->y0 = g->y0;
+    gd->gx = gx;
+    gd->gy = gy;
+    return SJ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the pipeline
+// ---------------------------------------------------------------------------
+// Size every workspace buffer for T tiles and the current entry capacities.
+int sj::size_workspace(sj_ctx *ctx, Workspace &w, long long T) {
+    int st;
+    const unsigned long long ecap = w.cap_r + w.cap_s;
+    w.T = T;
+    w.nch_cap = (unsigned)((ecap + T) / kChunk + 2);
+    w.nl_cap = (unsigned)((ecap + T) / (kChunk + 1) + 1);
+    w.items_cap = ecap;
+    w.vb_cap = (unsigned)(ecap / kRadixBlock + 2ull * w.nl_cap + 1);
+    const unsigned long long nslots = (unsigned long long)w.nch_cap + w.vb_cap;
+    if ((st = ensure(ctx, w.stats, sizeof(Stats)))) return st;
+    if ((st = ensure(ctx, w.cnt, 8ull * T))) return st;
+    if ((st = ensure(ctx, w.off, 8ull * (T + 1)))) return st;
+    if ((st = ensure(ctx, w.bsum, 16ull * (scan_blocks(T) + 1)))) return st;
+    if ((st = ensure(ctx, w.ts, 4ull * (w.nch_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.large, 4ull * (w.nl_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.ent_r, 16ull * (w.cap_r + 1)))) return st;
+    if ((st = ensure(ctx, w.id_r, 4ull * (w.cap_r + 1)))) return st;
+    if ((st = ensure(ctx, w.ent_s, 16ull * (w.cap_s + 1)))) return st;
+    if ((st = ensure(ctx, w.id_s, 4ull * (w.cap_s + 1)))) return st;
+    if ((st = ensure(ctx, w.seg_off, 4ull * (2ull * w.nl_cap + 2)))) return st;
+    if ((st = ensure(ctx, w.seg_src, 4ull * (2ull * w.nl_cap + 2)))) return st;
+    if ((st = ensure(ctx, w.seg_vb, 4ull * (2ull * w.nl_cap + 2)))) return st;
+    if ((st = ensure(ctx, w.hist, 1024ull * (w.vb_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.key_a, 4ull * (w.items_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.key_b, 4ull * (w.items_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.val_a, 4ull * (w.items_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.val_b, 4ull * (w.items_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.lmbr, 16ull * (w.items_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.lid, 4ull * (w.items_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.pc, 4ull * nslots))) return st;
+    if ((st = ensure(ctx, w.poff, 8ull * nslots))) return st;
+    if ((st = ensure(ctx, w.resv, 8ull * nslots))) return st;
+    if ((st = ensure(ctx, w.fail_c, 4ull * (w.nch_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.fail_l, 4ull * (w.vb_cap + 1)))) return st;
+    return SJ_OK;
+}
+
+LargeArgs sj::large_args(Workspace &w) {
+    LargeArgs a;
+    a.off = (const uint2 *)w.off.p;
+    a.large = (const unsigned *)w.large.p;
+    a.ent_r = (const float4 *)w.ent_r.p;
+    a.id_r = (const unsigned *)w.id_r.p;
+    a.ent_s = (const float4 *)w.ent_s.p;
+    a.id_s = (const unsigned *)w.id_s.p;
+    a.seg_off = (unsigned *)w.seg_off.p;
+    a.seg_src = (unsigned *)w.seg_src.p;
+    a.seg_vb = (unsigned *)w.seg_vb.p;
+    a.hist = (unsigned *)w.hist.p;
+    a.key_in = (unsigned *)w.key_a.p;
+    a.val_in = (unsigned *)w.val_a.p;
+    a.key_out = (unsigned *)w.key_b.p;
+    a.val_out = (unsigned *)w.val_b.p;
+    a.lmbr = (float4 *)w.lmbr.p;
+    a.lid = (unsigned *)w.lid.p;
+    a.items_cap = w.items_cap;
+    a.vb_cap = w.vb_cap;
+    a.st = (Stats *)w.stats.p;
+    return a;
+}
+
+SweepArgs sj::sweep_args(Workspace &w) {
+    SweepArgs a;
+    memset(&a, 0, sizeof a);
+    a.off = (const uint2 *)w.off.p;
+    a.ts = (const unsigned *)w.ts.p;
+    a.ent_r = (const float4 *)w.ent_r.p;
+    a.id_r = (const unsigned *)w.id_r.p;
+    a.ent_s = (const float4 *)w.ent_s.p;
+    a.id_s = (const unsigned *)w.id_s.p;
+    a.st = (Stats *)w.stats.p;
+    a.cnt_out = (unsigned *)w.pc.p;
+    a.off_in = (const unsigned long long *)w.poff.p;
+    a.resv = (unsigned long long *)w.resv.p;
+    a.cnt_base = w.nch_cap;
+    return a;
+}
+
+// Partitioning (count, scan, scatter) and the sort of the large tiles.
+// Enqueued only; errors of the device show up in the stats.
+int sj::enqueue_partition(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S,
+                          long long nS, const GridDev &g) {
+    cudaStream_t s = ctx->stream;
+    cudaError_t e;
+    Stats *st = (Stats *)w.stats.p;
+    {
+        PhaseScope ph(ctx, PH_RESET, 0);
+        if ((e = cudaMemsetAsync(w.stats.p, 0, sizeof(Stats), s))) return cuda_fail(ctx, e, "memset");
+        if ((e = cudaMemsetAsync(w.cnt.p, 0, 8ull * w.T, s))) return cuda_fail(ctx, e, "memset");
+    }
+    const int grid_stream = ctx->num_sms * 8;
+    const bool any = nR + nS > 0;
+    {
+        PhaseScope ph(ctx, PH_COUNT, any ? 1 : 0);
+        if ((e = launch_count(R, nR, S, nS, g, (unsigned *)w.cnt.p, st, grid_stream, s)))
+            return cuda_fail(ctx, e, "count kernel");
+    }
+    {
+        PhaseScope ph(ctx, PH_SCAN, 3);
+        if ((e = launch_scan((const uint2 *)w.cnt.p, w.T, (unsigned long long *)w.bsum.p, (uint2 *)w.off.p,
+                             (unsigned *)w.ts.p, w.nch_cap + 1, (unsigned *)w.large.p, w.nl_cap, st, s)))
+            return cuda_fail(ctx, e, "scan kernels");
+    }
+    {
+        PhaseScope ph(ctx, PH_SCATTER, any ? 1 : 0);
+        if ((e = launch_scatter(R, nR, S, nS, g, (unsigned *)w.cnt.p, (const uint2 *)w.off.p,
+                                (float4 *)w.ent_r.p, (unsigned *)w.id_r.p, w.cap_r, (float4 *)w.ent_s.p,
+                                (unsigned *)w.id_s.p, w.cap_s, st, grid_stream, s)))
+            return cuda_fail(ctx, e, "scatter kernel");
+    }
+    {
+        PhaseScope ph(ctx, PH_LSORT, 14);
+        if ((e = launch_large_sort(large_args(w), ctx->num_sms * 4, s)))
+            return cuda_fail(ctx, e, "large-tile sort");
+    }
+    return SJ_OK;
+}
+
+// Sweep both paths in `mode`; for MODE_WRITE the offsets come from `off_in`.
+int sj::enqueue_sweep(sj_ctx *ctx, Workspace &w, int mode, int2 *out, unsigned long long cap,
+                      const unsigned long long *off_in, unsigned *tile_pairs, int slot_base) {
+    cudaStream_t s = ctx->stream;
+    cudaError_t e;
+    SweepArgs a = sweep_args(w);
+    a.out = out;
+    a.cap = cap;
+    a.tile_pairs = tile_pairs;
+    if (off_in) a.off_in = off_in;
+    a.fail = (unsigned *)w.fail_c.p;
+    a.nfail = &((Stats *)w.stats.p)->nfail;
+    a.work_slot = slot_base;
+    {
+        PhaseScope ph(ctx, mode == MODE_WRITE || mode == MODE_RESERVE ? PH_SWEEP_WRITE : PH_SWEEP_COUNT, 1);
+        if ((e = launch_sweep_chunks(mode, a, ctx->num_sms * ctx->sweep_bps, s)))
+            return cuda_fail(ctx, e, "sweep kernel");
+    }
+    SweepArgs b = a;
+    b.fail = (unsigned *)w.fail_l.p;
+    b.nfail = &((Stats *)w.stats.p)->nfail_large;
+    b.work_slot = slot_base + 1;
+    {
+        PhaseScope ph(ctx, mode == MODE_WRITE || mode == MODE_RESERVE ? PH_LSWEEP_WRITE : PH_LSWEEP_COUNT, 1);
+        if ((e = launch_sweep_large(mode, large_args(w), b, ctx->num_sms * 4, s)))
+            return cuda_fail(ctx, e, "large-tile sweep kernel");
+    }
+    return SJ_OK;
+}
+
+int sj::read_stats(sj_ctx *ctx, Workspace &w, Stats *out) {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(ctx->h_stats, w.stats.p, sizeof(Stats), cudaMemcpyDeviceToHost, ctx->stream)))
+        return cuda_fail(ctx, e, "stats copy");
+    if ((e = cudaStreamSynchronize(ctx->stream))) return cuda_fail(ctx, e, "stream sync");
+    memcpy(out, ctx->h_stats, sizeof(Stats));
+    return SJ_OK;
+}
+
+// Partition + count pass with capacity retry.  On return the workspace
+// holds the partition, pc/poff the per-item pair counts / offsets, *stats
+// the device counters (npairs = exact total).
+int sj::partition_and_count(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR,
+                            const float4 *S, long long nS, const GridDev &g, Stats *stats,
+                            bool count_pass) {
+    const long long T = (long long)g.nx * g.ny;
+    w.cap_r = std::max<unsigned long long>(w.cap_r, (unsigned long long)nR + nR / 4 + 1024);
+    w.cap_s = std::max<unsigned long long>(w.cap_s, (unsigned long long)nS + nS / 4 + 1024);
+    for (int attempt = 0; attempt < 3; attempt++) {
+        int st;
+        if ((st = size_workspace(ctx, w, T))) return st;
+        if ((st = enqueue_partition(ctx, w, R, nR, S, nS, g))) return st;
+        if (count_pass) {
+            cudaError_t e;
+            const unsigned nslots = w.nch_cap + w.vb_cap;
+            if ((e = cudaMemsetAsync(w.pc.p, 0, 4ull * nslots, ctx->stream)))
+                return cuda_fail(ctx, e, "memset");
+            if ((st = enqueue_sweep(ctx, w, MODE_COUNT, nullptr, 0, nullptr, nullptr, 0))) return st;
+            PhaseScope ph(ctx, PH_PAIRSCAN, 1);
+            if ((e = launch_scan_pairs((const unsigned *)w.pc.p, nslots, (unsigned long long *)w.poff.p,
+                                       (Stats *)w.stats.p, ctx->stream)))
+                return cuda_fail(ctx, e, "pair-count scan");
+        }
+        if ((st = read_stats(ctx, w, stats))) return st;
+        if (stats->err & kErrBadRect)
+            return fail(ctx, SJ_EINVAL, "invalid rectangle: NaN/Inf coordinate or xl > xu / yl > yu");
+        if (stats->err & kErrTooMany)
+            return fail(ctx, SJ_EINVAL, "more than 2^31 replicated entries on one side");
+        if (stats->err & (kErrEntCap | kErrChunkCap | kErrLargeCap)) {
+            w.cap_r = std::max<unsigned long long>(w.cap_r, stats->e_r + stats->e_r / 8 + 1024);
+            w.cap_s = std::max<unsigned long long>(w.cap_s, stats->e_s + stats->e_s / 8 + 1024);
+            continue;   // grow and redo
+        }
+        if (stats->err) return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", stats->err);
+        return SJ_OK;
+    }
+    return fail(ctx, SJ_EINTERNAL, "workspace did not converge");
+}
+
+// ---------------------------------------------------------------------------
+// public joins
+// ---------------------------------------------------------------------------
+// Where the pairs of a join go once their number P is known.
+struct OutSpec {
+    enum Kind { LIB, INTO, WS } kind;
+    sj_pair *into = nullptr;   // INTO: caller buffer
+    int64_t cap = 0;           // INTO: its capacity
+    int2 *got = nullptr;       // the buffer written
+};
+
+static int out_acquire(sj_ctx *ctx, Workspace &w, OutSpec &os, unsigned long long P) {
+    if (os.kind == OutSpec::INTO) {
+        if ((unsigned long long)os.cap < P)
+            return fail(ctx, SJ_EOVERFLOW, "need %llu pairs, cap %lld", P, (long long)os.cap);
+        if (P && !os.into) return fail(ctx, SJ_EINVAL, "null output buffer");
+        os.got = (int2 *)os.into;
+        return SJ_OK;
+    }
+    if (P == 0) return SJ_OK;
+    if (os.kind == OutSpec::WS) {
+        int st = ensure(ctx, w.out, P * sizeof(int2));
+        if (st) return st;
+        os.got = (int2 *)w.out.p;
+        return SJ_OK;
+    }
+    os.got = (int2 *)dev_alloc(ctx, P * sizeof(int2));
+    if (!os.got) return fail(ctx, SJ_ENOMEM, "pair buffer of %llu pairs", P);
+    return SJ_OK;
+}
+
+static void out_abandon(sj_ctx *ctx, OutSpec &os) {
+    if (os.kind == OutSpec::LIB && os.got) dev_free(ctx, os.got);
+    os.got = nullptr;
+}
+
+// The exact two-pass join (count, allocate, write) of a partitioned workspace
+// whose count pass has run; stats->npairs is the total.
+static int write_pass(sj_ctx *ctx, Workspace &w, const Stats &stats, const sj_opts *o, OutSpec &os,
+                      int64_t *npairs) {
+    const unsigned long long P = stats.npairs;
+    *npairs = (int64_t)P;
+    int st = out_acquire(ctx, w, os, P);
+    if (st) return st;
+    if (P == 0) return SJ_OK;
+    if ((st = enqueue_sweep(ctx, w, MODE_WRITE, os.got, P, nullptr, nullptr, 2))) {
+        out_abandon(ctx, os);
+        return st;
+    }
+    if (o && o->sort_output && (st = sort_pairs(ctx, w, os.got, P))) {
+        out_abandon(ctx, os);
+        return st;
+    }
+    return SJ_OK;
+}
+
+static int join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
+                     int64_t nS, const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs) {
+    const int mode = o ? o->mode : SJ_TWO_PASS;
+    const bool one_pass = (mode == SJ_ONE_PASS || mode == SJ_ONE_PASS_HEUR ||
+                           (mode == SJ_AUTO && ctx->mlp_loaded));
+    if (one_pass) {
+        sj_pair *lib_out = nullptr;
+        sj_pair **plib = os.kind == OutSpec::LIB ? &lib_out : nullptr;
+        int st = join_one_pass(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, o,
+                               mode == SJ_ONE_PASS_HEUR ? 1 : 0, plib, os.into, os.cap, npairs);
+        os.got = os.kind == OutSpec::LIB ? (int2 *)lib_out : (int2 *)os.into;
+        return st;
+    }
+    Stats stats;
+    int st = partition_and_count(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &stats, true);
+    if (st) return st;
+    return write_pass(ctx, w, stats, o, os, npairs);
+}
+
+static int check_opts(sj_ctx *ctx, const sj_opts *o) {
+    if (!o) return SJ_OK;
+    if (o->reserved != 0) return fail(ctx, SJ_EINVAL, "sj_opts.reserved must be 0");
+    if (o->mode < SJ_TWO_PASS || o->mode > SJ_AUTO) return fail(ctx, SJ_EINVAL, "unknown mode %d", o->mode);
+    if (!(o->margin >= 0.0f) || !(o->margin < 1e6f)) return fail(ctx, SJ_EINVAL, "margin out of range");
+    return SJ_OK;
+}
+
+extern "C" int sj_join(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+                       const sj_grid *g, const sj_opts *o, sj_pair **d_pairs, int64_t *npairs) {
+    GridDev gd;
+    int st = check_inputs(ctx, d_R, nR, d_S, nS, g, &gd);
+    if (st) return st;
+    if ((st = check_opts(ctx, o))) return st;
+    if (!d_pairs || !npairs) return fail(ctx, SJ_EINVAL, "null output pointer");
+    DeviceGuard dg(ctx->device);
+    ctx->msg[0] = 0;
+    *d_pairs = nullptr;
+    OutSpec os{OutSpec::LIB};
+    if ((st = join_core(ctx, ctx->ws, d_R, nR, d_S, nS, gd, o, os, npairs))) return st;
+    *d_pairs = (sj_pair *)os.got;
+    return SJ_OK;
+}
+
+extern "C" int sj_join_into(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
+                            int64_t nS, const sj_grid *g, const sj_opts *o, sj_pair *d_buf,
+                            int64_t cap, int64_t *npairs) {
+    GridDev gd;
+    int st = check_inputs(ctx, d_R, nR, d_S, nS, g, &gd);
+    if (st) return st;
+    if ((st = check_opts(ctx, o))) return st;
+    if (cap < 0 || !npairs) return fail(ctx, SJ_EINVAL, "negative capacity or null npairs");
+    DeviceGuard dg(ctx->device);
+    ctx->msg[0] = 0;
+    OutSpec os{OutSpec::INTO};
+    os.into = d_buf;
+    os.cap = cap;
+    return join_core(ctx, ctx->ws, d_R, nR, d_S, nS, gd, o, os, npairs);
+}
+
+extern "C" int sj_join_host(sj_ctx *ctx, const sj_rect *h_R, int64_t nR, const sj_rect *h_S,
+                            int64_t nS, const sj_grid *g, const sj_opts *o, sj_pair *h_out,
+                            int64_t cap, int64_t *npairs) {
+    if (!ctx) return SJ_EINVAL;
+    if ((nR && !h_R) || (nS && !h_S)) return fail(ctx, SJ_EINVAL, "null rectangle pointer");
+    if (nR < 0 || nS < 0 || nR >= SJ_MAX_N || nS >= SJ_MAX_N)
+        return fail(ctx, SJ_EINVAL, "sizes must satisfy 0 <= n < 2^30");
+    if (cap < 0 || !npairs) return fail(ctx, SJ_EINVAL, "negative capacity or null npairs");
+    int st;
+    if ((st = check_opts(ctx, o))) return st;
+    DeviceGuard dg(ctx->device);
+    ctx->msg[0] = 0;
+    Workspace &w = ctx->ws;
+    if ((st = ensure(ctx, w.in_r, 16ull * nR + 16))) return st;
+    if ((st = ensure(ctx, w.in_s, 16ull * nS + 16))) return st;
+    cudaError_t e;
+    {
+        PhaseScope ph(ctx, PH_OTHER, 0);
+        if (nR && (e = cudaMemcpyAsync(w.in_r.p, h_R, 16ull * nR, cudaMemcpyHostToDevice, ctx->stream)))
+            return cuda_fail(ctx, e, "copy of R to the device");
+        if (nS && (e = cudaMemcpyAsync(w.in_s.p, h_S, 16ull * nS, cudaMemcpyHostToDevice, ctx->stream)))
+            return cuda_fail(ctx, e, "copy of S to the device");
+    }
+    GridDev gd;
+    if ((st = check_inputs(ctx, (const sj_rect *)w.in_r.p, nR, (const sj_rect *)w.in_s.p, nS, g, &gd)))
+        return st;
+    OutSpec os{OutSpec::WS};
+    if ((st = join_core(ctx, w, (const sj_rect *)w.in_r.p, nR, (const sj_rect *)w.in_s.p, nS, gd, o, os,
+                        npairs)))
+        return st;
+    if (*npairs > cap) return fail(ctx, SJ_EOVERFLOW, "need %lld pairs, cap %lld", (long long)*npairs, (long long)cap);
+    if (*npairs) {
+        if (!h_out) return fail(ctx, SJ_EINVAL, "null output buffer");
+        if ((e = cudaMemcpyAsync(h_out, os.got, 8ull * *npairs, cudaMemcpyDeviceToHost, ctx->stream)))
+            return cuda_fail(ctx, e, "copy of the pairs to the host");
+    }
+    if ((e = cudaStreamSynchronize(ctx->stream))) return cuda_fail(ctx, e, "stream sync");
+    return SJ_OK;
+}
+
+extern "C" int sj_count(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+                        const sj_grid *g, int64_t *out_npairs) {
+    GridDev gd;
+    int st = check_inputs(ctx, d_R, nR, d_S, nS, g, &gd);
+    if (st) return st;
+    if (!out_npairs) return fail(ctx, SJ_EINVAL, "null out_npairs");
+    DeviceGuard dg(ctx->device);
+    ctx->msg[0] = 0;
+    Stats stats;
+    if ((st = partition_and_count(ctx, ctx->ws, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd,
+                                  &stats, true)))
+        return st;
+    *out_npairs = (int64_t)stats.npairs;
+    return SJ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-tile statistics
+// ---------------------------------------------------------------------------
+extern "C" int sj_tile_stats(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
+                             int64_t nS, const sj_grid *g, uint32_t *d_cnt_r, uint32_t *d_cnt_s,
+                             uint32_t *d_pairs_per_tile) {
+    GridDev gd;
+    int st = check_inputs(ctx, d_R, nR, d_S, nS, g, &gd);
+    if (st) return st;
+    DeviceGuard dg(ctx->device);
+    ctx->msg[0] = 0;
+    Workspace &w = ctx->ws;
+    Stats stats;
+    if ((st = partition_and_count(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &stats,
+                                  false)))
+        return st;
+    cudaError_t e;
+    const long long T = (long long)gd.nx * gd.ny;
+    if (d_cnt_r || d_cnt_s) {
+        PhaseScope ph(ctx, PH_OTHER, 1);
+        if ((e = launch_tile_counts((const uint2 *)w.off.p, T, d_cnt_r, d_cnt_s, ctx->stream)))
+            return cuda_fail(ctx, e, "tile counts");
+    }
+    if (d_pairs_per_tile) {
+        if ((e = cudaMemsetAsync(d_pairs_per_tile, 0, 4ull * T, ctx->stream))) return cuda_fail(ctx, e, "memset");
+        if ((st = enqueue_sweep(ctx, w, MODE_TILES, nullptr, 0, nullptr, d_pairs_per_tile, 4))) return st;
+    }
+    if ((st = read_stats(ctx, w, &stats))) return st;
+    if (stats.err) return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", stats.err);
+    return SJ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// partitions as objects
+// ---------------------------------------------------------------------------
+extern "C" int sj_partition(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
+                            int64_t nS, const sj_grid *g, sj_part **out) {
+    GridDev gd;
+    int st = check_inputs(ctx, d_R, nR, d_S, nS, g, &gd);
+    if (st) return st;
+    if (!out) return fail(ctx, SJ_EINVAL, "null out");
+    *out = nullptr;
+    DeviceGuard dg(ctx->device);
+    ctx->msg[0] = 0;
+    sj_part *p = new (std::nothrow) sj_part();
+    if (!p) return fail(ctx, SJ_ENOMEM, "host allocation");
+    p->ctx = ctx;
+    p->grid = gd;
+    p->nR = nR;
+    p->nS = nS;
+    Stats stats;
+    if ((st = partition_and_count(ctx, p->ws, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &stats,
+                                  false))) {
+        release(ctx, p->ws);
+        delete p;
+        return st;
+    }
+    p->e_r = stats.e_r;
+    p->e_s = stats.e_s;
+    *out = p;
+    return SJ_OK;
+}
+
+extern "C" int sj_part_view_get(const sj_part *p, sj_part_view *v) {
+    if (!p || !v) return SJ_EINVAL;
+    v->n_tiles = (int64_t)p->grid.nx * p->grid.ny;
+    v->e_r = (int64_t)p->e_r;
+    v->e_s = (int64_t)p->e_s;
+    v->off = p->ws.off.p;
+    v->ent_r = p->ws.ent_r.p;
+    v->id_r = p->ws.id_r.p;
+    v->ent_s = p->ws.ent_s.p;
+    v->id_s = p->ws.id_s.p;
+    return SJ_OK;
+}
+
+extern "C" int sj_part_join(sj_ctx *ctx, sj_part *p, const sj_opts *o, sj_pair **d_pairs,
+                            int64_t *npairs) {
+    if (!ctx || !p || !d_pairs || !npairs) return SJ_EINVAL;
+    if (p->ctx != ctx) return fail(ctx, SJ_EINVAL, "partition belongs to another context");
+    int st = check_opts(ctx, o);
+    if (st) return st;
+    DeviceGuard dg(ctx->device);
+    ctx->msg[0] = 0;
+    Workspace &w = p->ws;
+    cudaError_t e;
+    const unsigned nslots = w.nch_cap + w.vb_cap;
+    // reset the per-call counters but keep the partition's totals
+    {
+        PhaseScope ph(ctx, PH_RESET, 1);
+        if ((e = launch_reset_counters((Stats *)w.stats.p, ctx->stream))) return cuda_fail(ctx, e, "reset");
+        if ((e = cudaMemsetAsync(w.pc.p, 0, 4ull * nslots, ctx->stream))) return cuda_fail(ctx, e, "memset");
+    }
+    if ((st = enqueue_sweep(ctx, w, MODE_COUNT, nullptr, 0, nullptr, nullptr, 0))) return st;
+    {
+        PhaseScope ph(ctx, PH_PAIRSCAN, 1);
+        if ((e = launch_scan_pairs((const unsigned *)w.pc.p, nslots, (unsigned long long *)w.poff.p,
+                                   (Stats *)w.stats.p, ctx->stream)))
+            return cuda_fail(ctx, e, "pair-count scan");
+    }
+    Stats stats;
+    if ((st = read_stats(ctx, w, &stats))) return st;
+    if (stats.err) return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", stats.err);
+    OutSpec os{OutSpec::LIB};
+    *d_pairs = nullptr;
+    if ((st = write_pass(ctx, w, stats, o, os, npairs))) return st;
+    *d_pairs = (sj_pair *)os.got;
+    return SJ_OK;
+}
+
+extern "C" void sj_part_free(sj_part *p) {
+    if (!p) return;
+    DeviceGuard dg(p->ctx->device);
+    release(p->ctx, p->ws);
+    delete p;
+}

@@ -1,0 +1,51 @@
+// misc.cu -- small helper kernels of the host runtime.
+#include "sj_internal.h"
+
+namespace sj {
+
+// cnt_r[t], cnt_s[t] = replicated entries of tile t (differences of the
+// exclusive prefix sums written by the partitioning scan).
+__global__ void k_tile_counts(const uint2 *__restrict__ off, long long T, unsigned *__restrict__ cr,
+                              unsigned *__restrict__ cs) {
+    for (long long t = blockIdx.x * 256ll + threadIdx.x; t < T; t += 256ll * gridDim.x) {
+        const uint2 a = off[t], b = off[t + 1];
+        if (cr) cr[t] = b.x - a.x;
+        if (cs) cs[t] = b.y - a.y;
+    }
+}
+
+cudaError_t launch_tile_counts(const uint2 *off, long long T, unsigned *cnt_r, unsigned *cnt_s,
+                               cudaStream_t s) {
+    long long nb = (T + 255) / 256;
+    if (nb > 65535) nb = 65535;
+    k_tile_counts<<<(unsigned)nb, 256, 0, s>>>(off, T, cnt_r, cnt_s);
+    return cudaGetLastError();
+}
+
+// Clear the per-call counters of a partition's stats, keep its totals.
+__global__ void k_reset_counters(Stats *st) {
+    if (threadIdx.x == 0) {
+        st->npairs = 0;
+        st->nfail = 0;
+        st->nfail_large = 0;
+        st->err = 0;
+    }
+    if (threadIdx.x < 8) st->work[threadIdx.x] = 0;
+}
+
+cudaError_t launch_reset_counters(Stats *st, cudaStream_t s) {
+    k_reset_counters<<<1, 32, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+// Not yet available: filled in by the one-pass / sorting / model sources.
+int join_one_pass(sj_ctx *ctx, Workspace &, const float4 *, long long, const float4 *, long long,
+                  const GridDev &, const sj_opts *, int, sj_pair **, sj_pair *, int64_t, int64_t *) {
+    return fail(ctx, SJ_EINVAL, "one-pass mode is not available in this build");
+}
+int sort_pairs(sj_ctx *ctx, Workspace &, int2 *, unsigned long long) {
+    return fail(ctx, SJ_EINVAL, "sort_output is not available in this build");
+}
+void mlp_release(sj_ctx *) {}
+
+}  // namespace sj

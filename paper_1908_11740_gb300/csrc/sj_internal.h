@@ -1,0 +1,126 @@
+// sj_internal.h -- host-side state of the library (contexts, workspaces) and
+// the internal entry points shared by the translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/sj.h"
+#include "sj_common.cuh"
+#include "sj_kernels.h"
+
+namespace sj {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Device workspace of one join (grow-only; reused across calls).
+struct Workspace {
+    Buf stats, cnt, off, bsum, ts, large;
+    Buf ent_r, id_r, ent_s, id_s;
+    Buf seg_off, seg_src, seg_vb, hist, key_a, key_b, val_a, val_b, lmbr, lid;
+    Buf pc, poff, resv, fail_c, fail_l;
+    Buf sort_tmp;
+    Buf in_r, in_s, out;      // staging of sj_join_host
+    unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
+    long long T = 0;
+    unsigned nch_cap = 0, nl_cap = 0, vb_cap = 0;
+    unsigned long long items_cap = 0;
+};
+
+struct MlpState;   // learned per-tile result-count predictor (mlp.cu)
+
+// Phases of a join, for the device-side timing of sj_timing_*.
+enum Phase {
+    PH_RESET = 0, PH_COUNT, PH_SCAN, PH_SCATTER, PH_LSORT, PH_SWEEP_COUNT, PH_PAIRSCAN,
+    PH_SWEEP_WRITE, PH_LSWEEP_COUNT, PH_LSWEEP_WRITE, PH_MODEL, PH_OTHER, PH_N
+};
+
+struct Timer {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    struct Rec { int phase; cudaEvent_t a, b; };
+    std::vector<Rec> pending;
+    double ms[PH_N] = {};
+    long long n[PH_N] = {};
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int fail(sj_ctx *ctx, int code, const char *fmt, ...);
+int cuda_fail(sj_ctx *ctx, cudaError_t e, const char *where);
+void *dev_alloc(sj_ctx *ctx, size_t bytes);
+void dev_free(sj_ctx *ctx, void *p);
+int ensure(sj_ctx *ctx, Buf &b, size_t bytes);
+void release(sj_ctx *ctx, Workspace &w);
+int check_inputs(sj_ctx *ctx, const sj_rect *R, int64_t nR, const sj_rect *S, int64_t nS,
+                 const sj_grid *g, GridDev *gd);
+int size_workspace(sj_ctx *ctx, Workspace &w, long long T);
+LargeArgs large_args(Workspace &w);
+SweepArgs sweep_args(Workspace &w);
+int enqueue_partition(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S,
+                      long long nS, const GridDev &g);
+int enqueue_sweep(sj_ctx *ctx, Workspace &w, int mode, int2 *out, unsigned long long cap,
+                  const unsigned long long *off_in, unsigned *tile_pairs, int slot_base);
+int read_stats(sj_ctx *ctx, Workspace &w, Stats *out);
+int partition_and_count(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S,
+                        long long nS, const GridDev &g, Stats *stats, bool count_pass);
+int join_one_pass(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S,
+                  long long nS, const GridDev &g, const sj_opts *o, int heuristic, sj_pair **lib_out,
+                  sj_pair *into, int64_t cap, int64_t *npairs);
+int sort_pairs(sj_ctx *ctx, Workspace &w, int2 *pairs, unsigned long long n);
+void mlp_release(sj_ctx *ctx);
+
+// misc.cu
+cudaError_t launch_tile_counts(const uint2 *off, long long T, unsigned *cnt_r, unsigned *cnt_s,
+                               cudaStream_t s);
+cudaError_t launch_reset_counters(Stats *st, cudaStream_t s);
+
+// timing (api.cu): brackets the launches of one phase with events when on,
+// and counts the kernels launched.
+struct PhaseScope {
+    sj_ctx *ctx;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseScope(sj_ctx *c, int ph, int kernels);
+    ~PhaseScope();
+};
+
+}  // namespace sj
+
+struct sj_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 1;
+    int sweep_bps = 1;
+    sj_alloc_fn alloc = nullptr;
+    sj_free_fn free_fn = nullptr;
+    void *user = nullptr;
+    sj::Workspace ws;
+    void *h_stats = nullptr;   // pinned copy of sj::Stats
+    sj::Timer timer;
+    long long launches = 0;
+    bool mlp_loaded = false;
+    sj::MlpState *mlp = nullptr;
+    char msg[512];
+};
+
+struct sj_part {
+    sj_ctx *ctx = nullptr;
+    sj::GridDev grid;
+    long long nR = 0, nS = 0;
+    unsigned long long e_r = 0, e_s = 0;
+    sj::Workspace ws;
+};

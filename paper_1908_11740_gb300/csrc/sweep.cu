@@ -1,0 +1,726 @@
+// sweep.cu -- joining phase of PBSM on the GPU (Sec. 3.4 steps 5-6):
+// per tile, sort both sides by x_l and run the forward-scan plane sweep of
+// Algorithm 1 with a y-overlap test and the reference-point duplicate test of
+// Eq. 1.
+//
+// Pivot-parallel form of Algorithm 1.  Algorithm 1 walks the merged x_l order;
+// when r comes first (r.x_l < s.x_l) r scans S forward while s.x_l <= r.x_u,
+// otherwise (ties included) s scans R forward while r.x_l <= s.x_u.  So a
+// pair (r, s) that x-overlaps is examined exactly once: by r when
+// s.x_l in (r.x_l, r.x_u], by s when r.x_l in [s.x_l, s.x_u].  Every entry is
+// therefore an independent pivot: it locates its start in the other side's
+// sorted segment by binary search and scans forward.  The set of examined
+// candidates and reported pairs is the same as Algorithm 1's.
+#include "sj_common.cuh"
+#include "sj_kernels.h"
+
+namespace sj {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// first index k in [lo, hi) with x[k] > v (strict) or >= v (!strict)
+template <bool STRICT, typename Get>
+__device__ __forceinline__ int lower_pos(int lo, int hi, float v, Get get) {
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        float xm = get(mid);
+        bool right = STRICT ? (xm > v) : (xm >= v);
+        if (right) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// ----------------------------------------------------------------------------
+// Small tiles: one chunk of consecutive tiles per CTA iteration, staged in
+// shared memory.  Persistent CTAs take chunks from a device counter.
+//   MODE_COUNT : pairs per chunk -> cnt_out[c]
+//   MODE_WRITE : pairs written at out[off_in[c] ...]
+//   MODE_RESERVE : count, reserve a range with one atomic on st->npairs,
+//                  write if it fits below cap, else record the chunk
+//   MODE_TILES : pairs per tile -> tile_pairs[t] (statistics / labels)
+// ----------------------------------------------------------------------------
+struct SmemChunk {
+    uint2 off[kChunk + 1];          // absolute (R, S) offsets of the chunk's tiles
+    float4 mbr[kChunkEnt];          // sorted entries: R segment, then S segment
+    unsigned id[kChunkEnt];
+    unsigned key[kChunkEnt];        // x_l keys, load order
+    unsigned short tile[kChunkEnt]; // chunk-local tile of each position
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_chunks(SweepArgs a) {
+    if (block_skip(a.st)) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemChunk &sm = *reinterpret_cast<SmemChunk *>(smem_raw);
+    __shared__ unsigned s_chunk;
+    __shared__ unsigned s_cursor;
+    __shared__ unsigned long long s_base;
+    __shared__ int s_ok;
+    __shared__ unsigned s_red[kSweepThreads / 32];
+
+    const int tid = threadIdx.x;
+    const unsigned lane = tid & 31;
+    const unsigned nlist = a.list ? *a.list_n : a.st->nchunks;
+
+    for (;;) {
+        if (tid == 0) s_chunk = atomicAdd(&a.st->work[a.work_slot], 1u);
+        __syncthreads();
+        const unsigned item = s_chunk;
+        if (item >= nlist) break;
+        const unsigned c = a.list ? a.list[item] : item;
+        unsigned t0 = a.ts[c], t1 = a.ts[c + 1];
+        if (t1 > t0) {
+            const uint2 lo = a.off[t1 - 1], hi = a.off[t1];
+            if ((hi.x - lo.x) + (hi.y - lo.y) + 1u > (unsigned)kChunk) t1--;   // large tile
+        }
+        const int nt = (int)(t1 - t0);
+        const uint2 b0 = a.off[t0], b1 = a.off[t1];
+        const int nR = (int)(b1.x - b0.x), nS = (int)(b1.y - b0.y);
+        const int nc = nR + nS;
+        if (nt > kChunk || nc > kChunkEnt) {   // cannot happen by construction
+            if (tid == 0) atomicOr(&a.st->err, kErrChunkCap);
+            __syncthreads();
+            continue;
+        }
+        for (int k = tid; k <= nt; k += kSweepThreads) sm.off[k] = a.off[t0 + k];
+        __syncthreads();
+
+        // Phase 1: load entries, keys and chunk-local tile of every position.
+        float4 m[kItems];
+        unsigned idv[kItems], key[kItems];
+        int tl[kItems];
+#pragma unroll
+        for (int it = 0; it < kItems; it++) {
+            const int e = it * kSweepThreads + tid;
+            tl[it] = -1;
+            if (e < nc) {
+                const bool isS = e >= nR;
+                const unsigned loc = isS ? (unsigned)(e - nR) : (unsigned)e;
+                const unsigned gi = (isS ? b0.y : b0.x) + loc;
+                m[it] = isS ? a.ent_s[gi] : a.ent_r[gi];
+                idv[it] = isS ? a.id_s[gi] : a.id_r[gi];
+                key[it] = xkey(m[it].x);
+                // largest j with rel_off(j) <= loc
+                int lo = 0, hi = nt;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    const unsigned o = isS ? sm.off[mid].y - b0.y : sm.off[mid].x - b0.x;
+                    if (o <= loc) lo = mid;
+                    else hi = mid;
+                }
+                tl[it] = lo;
+                sm.key[e] = key[it];
+                sm.tile[e] = (unsigned short)lo;
+            }
+        }
+        __syncthreads();
+
+        // Phase 2: rank of every entry inside its tile segment (ties by
+        // position) -> write it to its sorted place.
+#pragma unroll
+        for (int it = 0; it < kItems; it++) {
+            const int e = it * kSweepThreads + tid;
+            if (e < nc) {
+                const bool isS = e >= nR;
+                const int j = tl[it];
+                const int s0 = isS ? nR + (int)(sm.off[j].y - b0.y) : (int)(sm.off[j].x - b0.x);
+                const int s1 = isS ? nR + (int)(sm.off[j + 1].y - b0.y) : (int)(sm.off[j + 1].x - b0.x);
+                const unsigned k0 = key[it];
+                int r = 0;
+                for (int q = s0; q < s1; q++) {
+                    const unsigned kq = sm.key[q];
+                    r += (kq < k0) | ((kq == k0) & (q < e));
+                }
+                sm.mbr[s0 + r] = m[it];
+                sm.id[s0 + r] = idv[it];
+            }
+        }
+        if (tid == 0) s_cursor = 0;
+        __syncthreads();
+
+        // Phase 3: sweep.  Pivot p scans the other side of its tile.
+        unsigned my = 0;
+        auto pivot_setup = [&](int p, float4 &pv, unsigned &pid, int &k, int &kend, bool &isR) {
+            isR = p < nR;
+            const int j = sm.tile[p];
+            pv = sm.mbr[p];
+            pid = sm.id[p];
+            if (isR) {
+                const int o0 = nR + (int)(sm.off[j].y - b0.y), o1 = nR + (int)(sm.off[j + 1].y - b0.y);
+                k = lower_pos<true>(o0, o1, pv.x, [&](int q) { return sm.mbr[q].x; });
+                kend = o1;
+            } else {
+                const int o0 = (int)(sm.off[j].x - b0.x), o1 = (int)(sm.off[j + 1].x - b0.x);
+                k = lower_pos<false>(o0, o1, pv.x, [&](int q) { return sm.mbr[q].x; });
+                kend = o1;
+            }
+        };
+
+        if (MODE == MODE_COUNT || MODE == MODE_RESERVE || MODE == MODE_TILES) {
+            for (int p = tid; p < nc; p += kSweepThreads) {
+                float4 pv;
+                unsigned pid;
+                int k, kend;
+                bool isR;
+                pivot_setup(p, pv, pid, k, kend, isR);
+                unsigned cnt = 0;
+                for (; k < kend; k++) {
+                    const float4 o = sm.mbr[k];
+                    if (o.x > pv.z) break;
+                    if (o.y <= pv.w && pv.y <= o.w && reported_here(pid, sm.id[k])) cnt++;
+                }
+                if (MODE == MODE_TILES) {
+                    if (cnt) atomicAdd(a.tile_pairs + t0 + sm.tile[p], cnt);
+                }
+                my += cnt;
+            }
+            if (MODE == MODE_TILES) {
+                __syncthreads();
+                continue;
+            }
+            // block reduction
+            unsigned v = my;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+            if (lane == 0) s_red[tid >> 5] = v;
+            __syncthreads();
+            if (tid == 0) {
+                unsigned tot = 0;
+                for (int w = 0; w < kSweepThreads / 32; w++) tot += s_red[w];
+                if (MODE == MODE_COUNT) {
+                    a.cnt_out[c] = tot;
+                } else {
+                    const unsigned long long base = atomicAdd(&a.st->npairs, (unsigned long long)tot);
+                    a.resv[c] = base;
+                    const bool ok = tot == 0 || base + tot <= a.cap;
+                    s_ok = ok;
+                    s_base = base;
+                    if (!ok) {
+                        const unsigned f = atomicAdd(a.nfail, 1u);
+                        a.fail[f] = c;
+                    }
+                }
+            }
+            __syncthreads();
+            if (MODE == MODE_COUNT || !s_ok) continue;
+        }
+
+        // Write pass: warp-synchronous scan; hits are compacted with a ballot
+        // and appended to the chunk's range with one shared atomic per warp.
+        {
+            const unsigned long long base = MODE == MODE_WRITE ? a.off_in[c] : s_base;
+            for (int pb = 0; pb < nc; pb += kSweepThreads) {
+                const int p = pb + tid;
+                const bool active = p < nc;
+                float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+                unsigned pid = 0;
+                int k = 0, kend = 0;
+                bool isR = true;
+                if (active) pivot_setup(p, pv, pid, k, kend, isR);
+                bool go = active;
+                for (;;) {
+                    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+                    bool cand = false;
+                    if (go && k < kend) {
+                        o = sm.mbr[k];
+                        cand = o.x <= pv.z;
+                    }
+                    if (!__any_sync(kFull, cand)) break;
+                    go = cand;
+                    bool hit = false;
+                    int2 pr = make_int2(0, 0);
+                    if (cand) {
+                        if (o.y <= pv.w && pv.y <= o.w) {
+                            const unsigned oid = sm.id[k];
+                            if (reported_here(pid, oid)) {
+                                hit = true;
+                                pr = isR ? make_int2((int)(pid & kIdMask), (int)(oid & kIdMask))
+                                         : make_int2((int)(oid & kIdMask), (int)(pid & kIdMask));
+                            }
+                        }
+                        k++;
+                    }
+                    const unsigned hm = __ballot_sync(kFull, hit);
+                    if (hm) {
+                        const int leader = __ffs(hm) - 1;
+                        unsigned pos = 0;
+                        if ((int)lane == leader) pos = atomicAdd(&s_cursor, (unsigned)__popc(hm));
+                        pos = __shfl_sync(kFull, pos, leader);
+                        if (hit) a.out[base + pos + __popc(hm & lanemask_lt())] = pr;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Large tiles: segmented LSD radix sort (8-bit digits) of every large tile's
+// R and S segments by x_l, then a pivot-parallel sweep over global memory.
+// Segment 2*i / 2*i+1 = R / S entries of large tile large[i].  Every segment
+// is cut into virtual blocks of kRadixBlock items; all kernels loop over
+// virtual blocks (their number is read on the device).
+// ----------------------------------------------------------------------------
+
+// Segment sizes, item offsets and virtual-block offsets of the large tiles.
+__global__ void __launch_bounds__(1024) k_large_prep(LargeArgs a) {
+    if (block_skip(a.st)) return;
+    const unsigned nl = a.st->nlarge;   // <= capacity, else the fatal bit is set
+    const unsigned nseg = 2 * nl;
+    const unsigned per = (nseg + 1023) / 1024;
+    const unsigned s0 = threadIdx.x * per;
+    unsigned long long items = 0, vbs = 0;
+    for (unsigned k = 0; k < per; k++) {
+        const unsigned sg = s0 + k;
+        if (sg < nseg) {
+            const unsigned t = a.large[sg >> 1];
+            const uint2 lo = a.off[t], hi = a.off[t + 1];
+            const unsigned n = (hi.x == lo.x || hi.y == lo.y) ? 0u : ((sg & 1) ? hi.y - lo.y : hi.x - lo.x);
+            items += n;
+            vbs += (n + kRadixBlock - 1) / kRadixBlock;
+        }
+    }
+    // block exclusive scans (inline: two 64-bit values)
+    __shared__ unsigned long long sh_i[1024], sh_v[1024];
+    sh_i[threadIdx.x] = items;
+    sh_v[threadIdx.x] = vbs;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        unsigned long long xi = threadIdx.x >= (unsigned)d ? sh_i[threadIdx.x - d] : 0;
+        unsigned long long xv = threadIdx.x >= (unsigned)d ? sh_v[threadIdx.x - d] : 0;
+        __syncthreads();
+        sh_i[threadIdx.x] += xi;
+        sh_v[threadIdx.x] += xv;
+        __syncthreads();
+    }
+    unsigned long long pi = sh_i[threadIdx.x] - items, pv = sh_v[threadIdx.x] - vbs;
+    for (unsigned k = 0; k < per; k++) {
+        const unsigned sg = s0 + k;
+        if (sg < nseg) {
+            const unsigned t = a.large[sg >> 1];
+            const uint2 lo = a.off[t], hi = a.off[t + 1];
+            const unsigned n = (hi.x == lo.x || hi.y == lo.y) ? 0u : ((sg & 1) ? hi.y - lo.y : hi.x - lo.x);
+            a.seg_off[sg] = (unsigned)pi;
+            a.seg_src[sg] = (sg & 1) ? lo.y : lo.x;
+            a.seg_vb[sg] = (unsigned)pv;
+            pi += n;
+            pv += (n + kRadixBlock - 1) / kRadixBlock;
+        }
+    }
+    if (threadIdx.x == 1023) {
+        a.seg_off[nseg] = (unsigned)sh_i[1023];
+        a.seg_vb[nseg] = (unsigned)sh_v[1023];
+        a.st->large_items = sh_i[1023];
+        a.st->nvb = (unsigned)sh_v[1023];
+        if (sh_i[1023] > a.items_cap || sh_v[1023] > a.vb_cap) atomicOr(&a.st->err, kErrLargeCap);
+    }
+}
+
+// segment of virtual block vb: largest sg with seg_vb[sg] <= vb
+__device__ __forceinline__ unsigned seg_of_vb(const unsigned *seg_vb, unsigned nseg, unsigned vb) {
+    unsigned lo = 0, hi = nseg;
+    while (hi - lo > 1) {
+        unsigned mid = (lo + hi) >> 1;
+        if (seg_vb[mid] <= vb) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Key and value of item q of virtual block vb (pass 0 reads the entries).
+__device__ __forceinline__ void radix_item(const LargeArgs &a, int pass, unsigned sg, unsigned q,
+                                           unsigned &key, unsigned &val) {
+    if (pass == 0) {
+        const unsigned src = a.seg_src[sg] + q;
+        const float4 *ent = (sg & 1) ? a.ent_s : a.ent_r;
+        key = xkey(ent[src].x);
+        val = src;
+    } else {
+        const unsigned gi = a.seg_off[sg] + q;
+        key = a.key_in[gi];
+        val = a.val_in[gi];
+    }
+}
+
+__global__ void __launch_bounds__(kRadixThreads) k_radix_hist(LargeArgs a, int pass) {
+    if (block_skip(a.st)) return;
+    __shared__ unsigned h[256];
+    const unsigned nvb = a.st->nvb, nseg = 2 * a.st->nlarge;
+    const int shift = 8 * pass;
+    for (unsigned vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        const unsigned sg = seg_of_vb(a.seg_vb, nseg, vb);
+        const unsigned q0 = (vb - a.seg_vb[sg]) * kRadixBlock;
+        const unsigned n = a.seg_off[sg + 1] - a.seg_off[sg];
+        const unsigned q1 = min(n, q0 + kRadixBlock);
+        for (unsigned q = q0 + threadIdx.x; q < q1; q += kRadixThreads) {
+            unsigned key, val;
+            radix_item(a, pass, sg, q, key, val);
+            atomicAdd(&h[(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        a.hist[(unsigned long long)vb * 256 + threadIdx.x] = h[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// Per segment: hist[vb][d] -> absolute destination of the first item of
+// digit d of virtual block vb (digit-major order inside the segment).
+__global__ void __launch_bounds__(256) k_radix_offsets(LargeArgs a) {
+    if (block_skip(a.st)) return;
+    __shared__ unsigned s_tot[256];
+    const unsigned nseg = 2 * a.st->nlarge;
+    for (unsigned sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+        const unsigned v0 = a.seg_vb[sg], v1 = a.seg_vb[sg + 1];
+        const unsigned d = threadIdx.x;
+        unsigned run = 0;
+        for (unsigned vb = v0; vb < v1; vb++) {
+            const unsigned x = a.hist[(unsigned long long)vb * 256 + d];
+            a.hist[(unsigned long long)vb * 256 + d] = run;
+            run += x;
+        }
+        s_tot[d] = run;
+        __syncthreads();
+        if (d == 0) {
+            unsigned acc = 0;
+            for (int q = 0; q < 256; q++) {
+                const unsigned x = s_tot[q];
+                s_tot[q] = acc;
+                acc += x;
+            }
+        }
+        __syncthreads();
+        const unsigned add = s_tot[d] + a.seg_off[sg];
+        for (unsigned vb = v0; vb < v1; vb++) a.hist[(unsigned long long)vb * 256 + d] += add;
+        __syncthreads();
+    }
+}
+
+// Stable scatter: items are taken in rounds of 256 in order; inside a round
+// a warp ranks equal digits with match_any, warps are ordered through a
+// shared per-warp digit table.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(LargeArgs a, int pass) {
+    if (block_skip(a.st)) return;
+    constexpr int NW = kRadixThreads / 32;
+    __shared__ unsigned s_run[256];
+    __shared__ unsigned s_w[NW][256];
+    __shared__ unsigned s_dst[256];
+    const unsigned nvb = a.st->nvb, nseg = 2 * a.st->nlarge;
+    const int shift = 8 * pass;
+    const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < NW * 256; q += kRadixThreads) (&s_w[0][0])[q] = 0;
+    for (unsigned vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        s_run[threadIdx.x] = 0;
+        s_dst[threadIdx.x] = a.hist[(unsigned long long)vb * 256 + threadIdx.x];
+        __syncthreads();
+        const unsigned sg = seg_of_vb(a.seg_vb, nseg, vb);
+        const unsigned q0 = (vb - a.seg_vb[sg]) * kRadixBlock;
+        const unsigned n = a.seg_off[sg + 1] - a.seg_off[sg];
+        const unsigned q1 = min(n, q0 + kRadixBlock);
+        for (unsigned qb = q0; qb < q1; qb += kRadixThreads) {
+            const unsigned q = qb + threadIdx.x;
+            const bool valid = q < q1;
+            unsigned key = 0, val = 0, dg = 0xffffffffu;
+            if (valid) {
+                radix_item(a, pass, sg, q, key, val);
+                dg = (key >> shift) & 255u;
+            }
+            const unsigned peers = __match_any_sync(kFull, dg);
+            const unsigned rank = __popc(peers & lanemask_lt());
+            const int leader = __ffs(peers) - 1;
+            if (valid && (int)lane == leader) s_w[w][dg] = __popc(peers);
+            __syncthreads();
+            if (valid) {
+                unsigned before = s_run[dg];
+                for (unsigned ww = 0; ww < w; ww++) before += s_w[ww][dg];
+                const unsigned dst = s_dst[dg] + before + rank;
+                a.key_out[dst] = key;
+                a.val_out[dst] = val;
+            }
+            __syncthreads();
+            {
+                const unsigned d = threadIdx.x;
+                unsigned add = 0;
+                for (int ww = 0; ww < NW; ww++) {
+                    add += s_w[ww][d];
+                    s_w[ww][d] = 0;
+                }
+                s_run[d] += add;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Sorted entries of the large tiles: mbr/id gathered through the sorted values.
+__global__ void __launch_bounds__(256) k_large_gather(LargeArgs a) {
+    if (block_skip(a.st)) return;
+    const unsigned long long n = a.st->large_items;
+    const unsigned nseg = 2 * a.st->nlarge;
+    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n; i += 256ull * gridDim.x) {
+        // segment of item i
+        unsigned lo = 0, hi = nseg;
+        while (hi - lo > 1) {
+            unsigned mid = (lo + hi) >> 1;
+            if (a.seg_off[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        const unsigned v = a.val_in[i];
+        if (lo & 1) {
+            a.lmbr[i] = a.ent_s[v];
+            a.lid[i] = a.id_s[v];
+        } else {
+            a.lmbr[i] = a.ent_r[v];
+            a.lid[i] = a.id_r[v];
+        }
+    }
+}
+
+// Sweep of the large tiles: every entry is a pivot; virtual blocks of
+// kRadixBlock pivots are taken from a device counter.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_sweep_large(LargeArgs a, SweepArgs o) {
+    if (block_skip(o.st)) return;
+    __shared__ unsigned s_vb;
+    __shared__ unsigned s_cursor;
+    __shared__ unsigned long long s_base;
+    __shared__ int s_ok;
+    __shared__ unsigned s_red[8];
+    const unsigned nvb_all = a.st->nvb;
+    const unsigned nlist = o.list ? *o.list_n : nvb_all;
+    const unsigned nseg = 2 * a.st->nlarge;
+    const unsigned lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_vb = atomicAdd(&o.st->work[o.work_slot], 1u);
+            s_cursor = 0;
+        }
+        __syncthreads();
+        const unsigned item = s_vb;
+        if (item >= nlist) break;
+        const unsigned vb = o.list ? o.list[item] : item;
+        const unsigned sg = seg_of_vb(a.seg_vb, nseg, vb);
+        const bool isR = (sg & 1) == 0;
+        const unsigned og = sg ^ 1u;
+        const int o0 = (int)a.seg_off[og], o1 = (int)a.seg_off[og + 1];
+        const unsigned q0 = a.seg_off[sg] + (vb - a.seg_vb[sg]) * kRadixBlock;
+        const unsigned q1 = min(a.seg_off[sg + 1], q0 + kRadixBlock);
+        const unsigned tile = a.large[sg >> 1];
+        auto setup = [&](unsigned p, float4 &pv, unsigned &pid, int &k) {
+            pv = a.lmbr[p];
+            pid = a.lid[p];
+            if (isR) k = lower_pos<true>(o0, o1, pv.x, [&](int q) { return a.lmbr[q].x; });
+            else k = lower_pos<false>(o0, o1, pv.x, [&](int q) { return a.lmbr[q].x; });
+        };
+        unsigned long long base = 0;
+        bool do_write = MODE == MODE_WRITE;
+        if (MODE != MODE_WRITE) {
+            unsigned my = 0;
+            for (unsigned p = q0 + threadIdx.x; p < q1; p += 256) {
+                float4 pv;
+                unsigned pid;
+                int k;
+                setup(p, pv, pid, k);
+                unsigned cnt = 0;
+                for (; k < o1; k++) {
+                    const float4 ob = a.lmbr[k];
+                    if (ob.x > pv.z) break;
+                    if (ob.y <= pv.w && pv.y <= ob.w && reported_here(pid, a.lid[k])) cnt++;
+                }
+                my += cnt;
+            }
+            if (MODE == MODE_TILES) {
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) my += __shfl_xor_sync(kFull, my, d);
+                if (lane == 0 && my) atomicAdd(o.tile_pairs + tile, my);
+                __syncthreads();
+                continue;
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) my += __shfl_xor_sync(kFull, my, d);
+            if (lane == 0) s_red[threadIdx.x >> 5] = my;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned tot = 0;
+                for (int w = 0; w < 8; w++) tot += s_red[w];
+                if (MODE == MODE_COUNT) {
+                    o.cnt_out[o.cnt_base + vb] = tot;
+                } else {
+                    const unsigned long long b = atomicAdd(&o.st->npairs, (unsigned long long)tot);
+                    o.resv[o.cnt_base + vb] = b;
+                    const bool ok = tot == 0 || b + tot <= o.cap;
+                    s_ok = ok;
+                    s_base = b;
+                    if (!ok) {
+                        const unsigned f = atomicAdd(o.nfail, 1u);
+                        o.fail[f] = vb;
+                    }
+                }
+            }
+            __syncthreads();
+            if (MODE == MODE_COUNT) continue;
+            do_write = s_ok;
+            base = s_base;
+        } else {
+            base = o.off_in[o.cnt_base + vb];
+        }
+        if (!do_write) {
+            __syncthreads();
+            continue;
+        }
+        for (unsigned pb = q0; pb < q1; pb += 256) {
+            const unsigned p = pb + threadIdx.x;
+            const bool active = p < q1;
+            float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+            unsigned pid = 0;
+            int k = 0;
+            if (active) setup(p, pv, pid, k);
+            bool go = active;
+            for (;;) {
+                float4 ob = make_float4(0.f, 0.f, 0.f, 0.f);
+                bool cand = false;
+                if (go && k < o1) {
+                    ob = a.lmbr[k];
+                    cand = ob.x <= pv.z;
+                }
+                if (!__any_sync(kFull, cand)) break;
+                go = cand;
+                bool hit = false;
+                int2 pr = make_int2(0, 0);
+                if (cand) {
+                    if (ob.y <= pv.w && pv.y <= ob.w) {
+                        const unsigned oid = a.lid[k];
+                        if (reported_here(pid, oid)) {
+                            hit = true;
+                            pr = isR ? make_int2((int)(pid & kIdMask), (int)(oid & kIdMask))
+                                     : make_int2((int)(oid & kIdMask), (int)(pid & kIdMask));
+                        }
+                    }
+                    k++;
+                }
+                const unsigned hm = __ballot_sync(kFull, hit);
+                if (hm) {
+                    const int leader = __ffs(hm) - 1;
+                    unsigned pos = 0;
+                    if ((int)lane == leader) pos = atomicAdd(&s_cursor, (unsigned)__popc(hm));
+                    pos = __shfl_sync(kFull, pos, leader);
+                    if (hit) o.out[base + pos + __popc(hm & lanemask_lt())] = pr;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of n uint32 pair counts into uint64 offsets; the total goes
+// to st->npairs.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_pairs(const unsigned *__restrict__ cnt, unsigned n,
+                                                     unsigned long long *__restrict__ off,
+                                                     Stats *__restrict__ st) {
+    __shared__ unsigned long long sh[1024];
+    const unsigned per = (n + 1023) / 1024;
+    const unsigned i0 = threadIdx.x * per;
+    unsigned long long sum = 0;
+    for (unsigned k = 0; k < per; k++)
+        if (i0 + k < n) sum += cnt[i0 + k];
+    sh[threadIdx.x] = sum;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        unsigned long long x = threadIdx.x >= (unsigned)d ? sh[threadIdx.x - d] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += x;
+        __syncthreads();
+    }
+    unsigned long long run = sh[threadIdx.x] - sum;
+    for (unsigned k = 0; k < per; k++)
+        if (i0 + k < n) {
+            off[i0 + k] = run;
+            run += cnt[i0 + k];
+        }
+    if (threadIdx.x == 1023) st->npairs = sh[1023];
+}
+
+// ---- launchers ---------------------------------------------------------------
+size_t sweep_smem_bytes() { return sizeof(SmemChunk); }
+
+cudaError_t sweep_setup() {
+    cudaError_t e;
+    const int sm = (int)sizeof(SmemChunk);
+    if ((e = cudaFuncSetAttribute(k_sweep_chunks<MODE_COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_chunks<MODE_WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_chunks<MODE_RESERVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_sweep_chunks<MODE_TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)))
+        return e;
+    return cudaSuccess;
+}
+
+int sweep_blocks_per_sm() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_chunks<MODE_WRITE>, kSweepThreads,
+                                                  sizeof(SmemChunk));
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_sweep_chunks(int mode, const SweepArgs &a, int grid, cudaStream_t s) {
+    const size_t sm = sizeof(SmemChunk);
+    switch (mode) {
+        case MODE_COUNT: k_sweep_chunks<MODE_COUNT><<<grid, kSweepThreads, sm, s>>>(a); break;
+        case MODE_WRITE: k_sweep_chunks<MODE_WRITE><<<grid, kSweepThreads, sm, s>>>(a); break;
+        case MODE_RESERVE: k_sweep_chunks<MODE_RESERVE><<<grid, kSweepThreads, sm, s>>>(a); break;
+        default: k_sweep_chunks<MODE_TILES><<<grid, kSweepThreads, sm, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_large_sort(LargeArgs a, int grid, cudaStream_t s) {
+    k_large_prep<<<1, 1024, 0, s>>>(a);
+    for (int pass = 0; pass < 4; pass++) {
+        k_radix_hist<<<grid, kRadixThreads, 0, s>>>(a, pass);
+        k_radix_offsets<<<grid, 256, 0, s>>>(a);
+        k_radix_scatter<<<grid, kRadixThreads, 0, s>>>(a, pass);
+        // ping-pong
+        unsigned *tk = a.key_in;
+        a.key_in = a.key_out;
+        a.key_out = tk;
+        unsigned *tv = a.val_in;
+        a.val_in = a.val_out;
+        a.val_out = tv;
+        if (pass == 0) {
+            // pass 0 read the entries; later passes read key_in/val_in, which
+            // now hold pass 0's output.  Nothing else to do.
+        }
+    }
+    k_large_gather<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_large(int mode, const LargeArgs &a, const SweepArgs &o, int grid,
+                               cudaStream_t s) {
+    switch (mode) {
+        case MODE_COUNT: k_sweep_large<MODE_COUNT><<<grid, 256, 0, s>>>(a, o); break;
+        case MODE_WRITE: k_sweep_large<MODE_WRITE><<<grid, 256, 0, s>>>(a, o); break;
+        case MODE_RESERVE: k_sweep_large<MODE_RESERVE><<<grid, 256, 0, s>>>(a, o); break;
+        default: k_sweep_large<MODE_TILES><<<grid, 256, 0, s>>>(a, o); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_pairs(const unsigned *cnt, unsigned n, unsigned long long *off, Stats *st,
+                              cudaStream_t s) {
+    k_scan_pairs<<<1, 1024, 0, s>>>(cnt, n, off, st);
+    return cudaGetLastError();
+}
+
+}  // namespace sj

@@ -20,8 +20,9 @@ available here):
 
 * ``uniform_pair``  -- plain join: uniform centres, uniform extents.
 * ``gis_pair``      -- layers shaped like large GIS layers: 64-component Gaussian
-  mixture (sigma ~ U[0.01, 0.1]) plus 20% uniform background, log-normal
-  extents (median 2e-5, sigma 1, clipped at 1e-2).
+  mixture (sigma ~ U[0.01, 0.1], truncated to the unit square) plus 20%
+  uniform background, log-normal extents (median 2e-5, sigma 1, clipped at
+  1e-2).
 * ``zipf_pair``     -- extent / skew stress: Zipf(s=1.2) ranks onto a 1024^2
   lattice with uniform jitter inside the cell; S uses R's rank->cell map with
   probability ``rho`` and an independent map otherwise.
@@ -87,14 +88,20 @@ def _mixture_world(world, n_comp: int = 64):
 
 def _mixture_centres(g, n, mu, sigma, background: float):
     """cx, cy from an equal-weight isotropic Gaussian mixture plus a uniform
-    background fraction; clipped to [0,1]."""
+    background fraction, truncated to [0,1]^2: a component draw that falls
+    outside is redrawn from the same component (clipping instead would pile
+    thousands of centres onto the border lines)."""
     comp = g.integers(0, mu.shape[0], n)
     is_bg = g.random(n) < background
     z = g.standard_normal((n, 2))
     u = g.random((n, 2))
     c = mu[comp] + sigma[comp, None] * z
+    out = ~is_bg & ((c < 0.0) | (c > 1.0)).any(axis=1)
+    while out.any():
+        idx = np.nonzero(out)[0]
+        c[idx] = mu[comp[idx]] + sigma[comp[idx], None] * g.standard_normal((len(idx), 2))
+        out[idx] = ((c[idx] < 0.0) | (c[idx] > 1.0)).any(axis=1)
     c = np.where(is_bg[:, None], u, c)
-    np.clip(c, 0.0, 1.0, out=c)
     return c[:, 0], c[:, 1]
 
 
@@ -105,7 +112,7 @@ def gis_pair(n_r: int = 10_000_000, n_s: int = 20_000_000, seed: int = 2,
 
     Defaults: |R| = 10M, |S| = 20M; centres from a 64-component Gaussian
     mixture (sigma U[0.01,0.1], means U[0,1]^2, equal weights, shared by R and
-    S) plus 20% uniform background, clipped to [0,1]; width and height
+    S, truncated to [0,1]^2) plus 20% uniform background; width and height
     independently log-normal with median 2e-5 and sigma 1.0, clipped to 1e-2.
     Smaller n give the same spatial distribution at lower density."""
     world, gr, gs = _streams(seed)
