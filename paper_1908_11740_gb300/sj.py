@@ -335,7 +335,7 @@ class _CudaArray:
 
     def __init__(self, ptr: int, shape, typestr: str):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (int(ptr), True), "version": 3, "strides": None}
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
 
 
 def device_view(ptr: int, shape, dtype: torch.dtype) -> torch.Tensor:
