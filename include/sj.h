@@ -201,6 +201,38 @@ int sj_timing_enable(sj_ctx *ctx, int on);
 int sj_timing_read(sj_ctx *ctx, sj_timing *out);
 const char *sj_timing_phase_name(int phase);
 
+/* ---- a join that allocates nothing --------------------------------------- */
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code that runs while someone else is
+ * capturing a CUDA graph, plug-ins whose host process owns every device
+ * allocation (a fixed budget or a custom pool), and callers that cannot
+ * afford an allocation's latency or implicit synchronisation.
+ *
+ * Same result as sj_join_into (two-pass, exact), but every scratch buffer is
+ * carved from one fixed device array of 20 MiB inside this library.  Every
+ * GPU on which the library is used holds that array until the process
+ * exits.  No cudaMalloc, cudaFree or allocating library call is made.
+ *   d_R, d_S  : device rectangles as for sj_join (16-byte aligned)
+ *   g         : the grid; nx * ny <= 65536
+ *   d_out/cap : caller-owned device buffer of cap pairs
+ *   npairs    : host; receives the number of pairs (also on SJ_EOVERFLOW)
+ *   cuda_stream : the stream to use (cudaStream_t, NULL = legacy default)
+ * Limits: nR, nS <= 65536 and at most 131072 replicated entries per side;
+ * beyond them SJ_EINVAL (sizes are checked first, the entry count on the
+ * device, in which case nothing is written).  If cap is too small, *npairs
+ * gets the required count and SJ_EOVERFLOW is returned.
+ * Uses the current device.  The first call on a device resolves the array's
+ * address (cudaGetSymbolAddress) and the launch parameters: make that first
+ * call before any stream capture.  Calls share the array: two calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race and corrupt each other; serialise them.  Each call clears the
+ * counters it needs, so stale contents of an earlier call do no harm.
+ * Synchronises the stream once (after counting); the pairs are written
+ * asynchronously afterwards.  Status codes only (no sj_last_error). */
+int sj_join_noalloc(const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+                    const sj_grid *g, sj_pair *d_out, int64_t cap, int64_t *npairs,
+                    void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

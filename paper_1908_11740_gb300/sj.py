@@ -81,6 +81,7 @@ SIGNATURES = [
     ("sj_timing_enable", I32, [P, I32]),
     ("sj_timing_read", I32, [P, ctypes.POINTER(sj_timing)]),
     ("sj_timing_phase_name", ctypes.c_char_p, [I32]),
+    ("sj_join_noalloc", I32, [P, I64, P, I64, ctypes.POINTER(sj_grid), P, I64, ctypes.POINTER(I64), P]),
 ]
 
 
