@@ -181,14 +181,21 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-# algorithmic bytes per launch of each single-kernel phase
+# Algorithmic bytes per launch of each single-kernel phase: every input
+# rectangle read once (16 B), every stored entry written / read once as the
+# 20 B (MBR + id) it carries, every pair written once (8 B).  E is the
+# number of entries the kernel's partition level stores in device memory.
 def alg_bytes(phase, n_in, E, P):
     return {"count": 16 * n_in, "scatter": 16 * n_in + 20 * E, "sweep_count": 20 * E,
             "sweep_write": 20 * E + 8 * P}.get(phase)
 
 
-KERNEL_OF_PHASE = {"count": "k_count", "scatter": "k_scatter", "sweep_count": "k_sweep_chunks<COUNT>",
-                   "sweep_write": "k_sweep_chunks<WRITE>"}
+KERNELS = {
+    1: {"count": "k_bcount", "scatter": "k_bscatter", "sweep_count": "k_bjoin<COUNT>",
+        "sweep_write": "k_bjoin<WRITE>", "sweep_reserve": "k_bjoin<RESERVE>"},
+    0: {"count": "k_count", "scatter": "k_scatter", "sweep_count": "k_sweep_chunks<COUNT>",
+        "sweep_write": "k_sweep_chunks<WRITE>", "sweep_reserve": "k_sweep_chunks<RESERVE>"},
+}
 
 
 def ours(args):
@@ -219,6 +226,9 @@ def ours(args):
     P = 0
     for _ in range(max(3, args.warmup)):
         P = sj.sj_join(ctx, dR, dS, grid, opts).shape[0]
+    last = sj.sj_last_stats(ctx)
+    path = last["path"]
+    E1 = last["l1_entries_r"] + last["l1_entries_s"] if path == 1 else None
     cr, cs, _ = sj.sj_tile_stats(ctx, dR, dS, grid)
     E = int(cr.sum().item()) + int(cs.sum().item())
     del cr, cs
@@ -277,13 +287,14 @@ def ours(args):
 
     phases = {k: v for k, v in timing.items() if k != "launches" and v[0] > 0}
     n_in = args.n_r + args.n_s
-    cand = {k: v for k, v in phases.items() if k in KERNEL_OF_PHASE}
+    kern = KERNELS[path]
+    cand = {k: v for k, v in phases.items() if k in kern}
     dom = max(cand, key=lambda k: cand[k][1])
     dom_ms = cand[dom][1] / cand[dom][0]
-    ab = alg_bytes(dom, n_in, E, P)
+    ab = alg_bytes(dom, n_in, E1 if path == 1 else E, P)
     peak, peak_kind = load_peaks()
     achieved = ab / (dom_ms / 1e3) / 1e9
-    traffic = load_traffic().get(KERNEL_OF_PHASE[dom])
+    traffic = load_traffic().get(kern[dom])
     b_join = 16 * n_in + 40 * E + 8 * P
 
     cpu = None
@@ -296,9 +307,12 @@ def ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(args), "grid": args.grid, "mode": args.mode,
-                       "pairs": P, "entries": E, "l2": "inputs 480 MB > 129 MB L2 (no flush needed)",
+                       "pairs": P, "entries": E, "l1_entries": E1,
+                       "path": "two-level (blocks of %d x %d tiles)" % (last["block_side"], last["block_side"])
+                       if path == 1 else "single-level",
+                       "l2": "inputs 480 MB > 129 MB L2 (no flush needed)",
                        "per_rank": "independent join per GPU, seed 2 + rank"},
-            "roofline": {"bound": "hbm", "kernel": KERNEL_OF_PHASE[dom], "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": kern[dom], "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback 6.8 TB/s", "traffic": traffic,

@@ -186,6 +186,25 @@ int sj_join_host(sj_ctx *ctx, const sj_rect *h_R, int64_t nR, const sj_rect *h_S
                  const sj_grid *g, const sj_opts *o, sj_pair *h_out, int64_t cap,
                  int64_t *npairs);
 
+/* ---- statistics of the last join ------------------------------------------ */
+/* Counters of the last join / count on this context (host copy; valid after
+ * the call returned SJ_OK).  path: 1 = two-level (blocked) partitioning,
+ * 0 = single-level.  For the two-level path, l1_entries_* are the entries
+ * written to the coarse blocks (a rectangle is copied into every block it
+ * overlaps) and blocks / block_side describe the coarse grid; the per-tile
+ * segments of the method then exist only in shared memory.  For the
+ * single-level path, entries_* are the replicated per-tile entries. */
+typedef struct {
+    int32_t path;
+    int32_t block_side;          /* tiles per block side (two-level)        */
+    int64_t blocks;              /* blocks of the coarse grid               */
+    int64_t work_items;          /* blocks holding both R and S entries     */
+    int64_t l1_entries_r, l1_entries_s;
+    int64_t entries_r, entries_s;
+    int64_t npairs;
+} sj_stats;
+int sj_last_stats(sj_ctx *ctx, sj_stats *out);
+
 /* ---- device-side timing ------------------------------------------------- */
 /* When enabled, every phase of every join is bracketed by CUDA events on the
  * context's stream; sj_timing_read synchronises the stream and returns the

@@ -94,13 +94,16 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
     Buf *all[] = {&w.stats, &w.cnt, &w.off, &w.bsum, &w.ts, &w.large, &w.ent_r, &w.id_r,
                   &w.ent_s, &w.id_s, &w.seg_off, &w.seg_src, &w.seg_vb, &w.hist, &w.key_a,
                   &w.key_b, &w.val_a, &w.val_b, &w.lmbr, &w.lid, &w.pc, &w.poff, &w.resv,
-                  &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out};
+                  &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out, &w.bH,
+                  &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
+                  &w.bResv, &w.bFail, &w.bImeta, &w.bIns};
     for (Buf *b : all) {
         dev_free(ctx, b->p);
         b->p = nullptr;
         b->bytes = 0;
     }
     w.cap_r = w.cap_s = 0;
+    w.bcap_r = w.bcap_s = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -188,6 +191,12 @@ extern "C" int sj_timing_read(sj_ctx *ctx, sj_timing *out) {
     return SJ_OK;
 }
 
+extern "C" int sj_last_stats(sj_ctx *ctx, sj_stats *out) {
+    if (!ctx || !out) return SJ_EINVAL;
+    *out = ctx->last;
+    return SJ_OK;
+}
+
 extern "C" const char *sj_timing_phase_name(int phase) {
     return (phase >= 0 && phase < PH_N) ? kPhaseNames[phase] : "";
 }
@@ -217,6 +226,12 @@ extern "C" int sj_create(sj_ctx **out, int device, void *cuda_stream) {
         return SJ_ECUDA;
     }
     c->sweep_bps = sweep_blocks_per_sm();
+    if (blocked_setup() != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SJ_ECUDA;
+    }
+    c->bjoin_bps = bjoin_blocks_per_sm();
     if (cudaMallocHost(&c->h_stats, sizeof(Stats)) != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -487,6 +502,10 @@ int sj::partition_and_count(sj_ctx *ctx, Workspace &w, const float4 *R, long lon
             continue;   // grow and redo
         }
         if (stats->err) return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", stats->err);
+        memset(&ctx->last, 0, sizeof ctx->last);
+        ctx->last.entries_r = (int64_t)stats->e_r;
+        ctx->last.entries_s = (int64_t)stats->e_s;
+        ctx->last.npairs = (int64_t)stats->npairs;
         return SJ_OK;
     }
     return fail(ctx, SJ_EINTERNAL, "workspace did not converge");
@@ -548,6 +567,165 @@ static int write_pass(sj_ctx *ctx, Workspace &w, const Stats &stats, const sj_op
     return SJ_OK;
 }
 
+// ---------------------------------------------------------------------------
+// the two-level (blocked) path
+// ---------------------------------------------------------------------------
+struct BPlan {
+    int G = 0, bx = 0, by = 0, nb = 0, nc = 0;
+};
+
+// Blocks of G x G tiles holding about 1.5k entries each; false when the grid
+// does not suit the blocked path (then the single-level path runs).
+static bool plan_blocked(sj_ctx *ctx, const GridDev &g, long long nR, long long nS, BPlan &p) {
+    if (!ctx->use_blocked || g.nx > 65535 || g.ny > 65535) return false;
+    const double est = (double)(nR + nS) * 1.1 + 1.0;
+    const double nbt = est / 1536.0 > 1.0 ? est / 1536.0 : 1.0;
+    int G = (int)ceil(sqrt((double)g.nx * (double)g.ny / nbt));
+    if (G < 1) G = 1;
+    if (G > kMaxG) G = kMaxG;
+    for (;; G++) {
+        if (G > kMaxG) return false;
+        p.bx = (g.nx + G - 1) / G;
+        p.by = (g.ny + G - 1) / G;
+        if ((long long)p.bx * p.by <= kMaxBlocks) break;
+    }
+    p.G = G;
+    p.nb = p.bx * p.by;
+    p.nc = ctx->num_sms * l1_blocks_per_sm(p.nb);
+    return true;
+}
+
+static int size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p) {
+    int st;
+    if ((st = ensure(ctx, w.stats, sizeof(Stats)))) return st;
+    if ((st = ensure(ctx, w.bH, 8ull * p.nb * p.nc))) return st;
+    if ((st = ensure(ctx, w.bTot, 8ull * p.nb))) return st;
+    if ((st = ensure(ctx, w.bBoR, 4ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bBoS, 4ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bItems, 4ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bImeta, 16ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bIns, 4ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bEntR, sizeof(BEnt) * (w.bcap_r + 1)))) return st;
+    if ((st = ensure(ctx, w.bEntS, sizeof(BEnt) * (w.bcap_s + 1)))) return st;
+    if ((st = ensure(ctx, w.bPc, 4ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bPoff, 8ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bResv, 8ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bFail, 4ull * (p.nb + 1)))) return st;
+    return SJ_OK;
+}
+
+static BArgs blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long nR, const float4 *S,
+                          long long nS, const GridDev &g) {
+    BArgs a;
+    a.R = R;
+    a.nR = nR;
+    a.S = S;
+    a.nS = nS;
+    a.g = g;
+    a.G = p.G;
+    a.gmul = p.G > 1 ? (unsigned)(0xFFFFFFFFull / (unsigned long long)p.G + 1ull) : 0u;
+    a.bx = p.bx;
+    a.by = p.by;
+    a.nb = p.nb;
+    a.H = (unsigned *)w.bH.p;
+    a.btot = (unsigned *)w.bTot.p;
+    a.bo_r = (unsigned *)w.bBoR.p;
+    a.bo_s = (unsigned *)w.bBoS.p;
+    a.items = (unsigned *)w.bItems.p;
+    a.imeta = (uint4 *)w.bImeta.p;
+    a.ins = (unsigned *)w.bIns.p;
+    a.bent_r = (BEnt *)w.bEntR.p;
+    a.bent_s = (BEnt *)w.bEntS.p;
+    a.cap_r = w.bcap_r;
+    a.cap_s = w.bcap_s;
+    a.st = (Stats *)w.stats.p;
+    return a;
+}
+
+static BJoinOut bjoin_out(Workspace &w, int slot) {
+    BJoinOut o;
+    memset(&o, 0, sizeof o);
+    o.work_slot = slot;
+    o.cnt_out = (unsigned *)w.bPc.p;
+    o.off_in = (const unsigned long long *)w.bPoff.p;
+    o.resv = (unsigned long long *)w.bResv.p;
+    o.fail = (unsigned *)w.bFail.p;
+    o.nfail = &((Stats *)w.stats.p)->nfail;
+    return o;
+}
+
+// L1 partition of the blocked path (count, scan, write).
+static int enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, const BArgs &a) {
+    cudaError_t e;
+    cudaStream_t s = ctx->stream;
+    {
+        PhaseScope ph(ctx, PH_RESET, 0);
+        if ((e = cudaMemsetAsync(w.stats.p, 0, sizeof(Stats), s))) return cuda_fail(ctx, e, "memset");
+        if ((e = cudaMemsetAsync(w.bPc.p, 0, 4ull * (p.nb + 1), s))) return cuda_fail(ctx, e, "memset");
+    }
+    {
+        PhaseScope ph(ctx, PH_COUNT, 1);
+        if ((e = launch_bcount(a, p.nc, s))) return cuda_fail(ctx, e, "block count kernel");
+    }
+    {
+        PhaseScope ph(ctx, PH_SCAN, 2);
+        if ((e = launch_bscan(a, p.nc, s))) return cuda_fail(ctx, e, "block scan kernels");
+    }
+    {
+        PhaseScope ph(ctx, PH_SCATTER, 1);
+        if ((e = launch_bscatter(a, p.nc, s))) return cuda_fail(ctx, e, "block write kernel");
+    }
+    return SJ_OK;
+}
+
+// Blocked partition + count pass.  *use_direct is set when a tile holds more
+// entries than shared memory (the caller then runs the single-level path).
+static int blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const float4 *R,
+                                   long long nR, const float4 *S, long long nS, const GridDev &g,
+                                   Stats *stats, bool *use_direct) {
+    *use_direct = false;
+    w.bcap_r = std::max<unsigned long long>(w.bcap_r, (unsigned long long)nR + nR / 8 + 1024);
+    w.bcap_s = std::max<unsigned long long>(w.bcap_s, (unsigned long long)nS + nS / 8 + 1024);
+    for (int attempt = 0; attempt < 3; attempt++) {
+        int st;
+        if ((st = size_blocked(ctx, w, p))) return st;
+        BArgs a = blocked_args(w, p, R, nR, S, nS, g);
+        if ((st = enqueue_blocked_partition(ctx, w, p, a))) return st;
+        cudaError_t e;
+        {
+            PhaseScope ph(ctx, PH_SWEEP_COUNT, 1);
+            if ((e = launch_bjoin(MODE_COUNT, a, bjoin_out(w, 0), ctx->num_sms * ctx->bjoin_bps, ctx->stream)))
+                return cuda_fail(ctx, e, "block join kernel");
+        }
+        {
+            PhaseScope ph(ctx, PH_PAIRSCAN, 1);
+            if ((e = launch_scan_pairs((const unsigned *)w.bPc.p, (unsigned)p.nb, (unsigned long long *)w.bPoff.p,
+                                       (Stats *)w.stats.p, ctx->stream)))
+                return cuda_fail(ctx, e, "pair-count scan");
+        }
+        if ((st = read_stats(ctx, w, stats))) return st;
+        if (stats->err & kErrBadRect)
+            return fail(ctx, SJ_EINVAL, "invalid rectangle: NaN/Inf coordinate or xl > xu / yl > yu");
+        if (stats->err & kErrEntCap) {
+            w.bcap_r = std::max<unsigned long long>(w.bcap_r, stats->e_r + stats->e_r / 8 + 1024);
+            w.bcap_s = std::max<unsigned long long>(w.bcap_s, stats->e_s + stats->e_s / 8 + 1024);
+            continue;
+        }
+        if (stats->err) return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", stats->err);
+        if (stats->need_direct) *use_direct = true;
+        memset(&ctx->last, 0, sizeof ctx->last);
+        ctx->last.path = 1;
+        ctx->last.block_side = p.G;
+        ctx->last.blocks = p.nb;
+        ctx->last.work_items = stats->nchunks;
+        ctx->last.l1_entries_r = (int64_t)stats->e_r;
+        ctx->last.l1_entries_s = (int64_t)stats->e_s;
+        ctx->last.npairs = (int64_t)stats->npairs;
+        return SJ_OK;
+    }
+    return fail(ctx, SJ_EINTERNAL, "blocked workspace did not converge");
+}
+
 static int join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
                      int64_t nS, const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs) {
     const int mode = o ? o->mode : SJ_TWO_PASS;
@@ -562,7 +740,38 @@ static int join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, 
         return st;
     }
     Stats stats;
-    int st = partition_and_count(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &stats, true);
+    int st;
+    BPlan bp;
+    if (plan_blocked(ctx, gd, nR, nS, bp)) {
+        bool direct = false;
+        if ((st = blocked_partition_count(ctx, w, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd,
+                                          &stats, &direct)))
+            return st;
+        if (!direct) {
+            const unsigned long long P = stats.npairs;
+            *npairs = (int64_t)P;
+            if ((st = out_acquire(ctx, w, os, P))) return st;
+            if (P == 0) return SJ_OK;
+            BArgs a = blocked_args(w, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd);
+            BJoinOut bo = bjoin_out(w, 1);
+            bo.out = os.got;
+            bo.cap = P;
+            cudaError_t e;
+            {
+                PhaseScope ph(ctx, PH_SWEEP_WRITE, 1);
+                if ((e = launch_bjoin(MODE_WRITE, a, bo, ctx->num_sms * ctx->bjoin_bps, ctx->stream))) {
+                    out_abandon(ctx, os);
+                    return cuda_fail(ctx, e, "block join kernel");
+                }
+            }
+            if (o && o->sort_output && (st = sort_pairs(ctx, w, os.got, P))) {
+                out_abandon(ctx, os);
+                return st;
+            }
+            return SJ_OK;
+        }
+    }
+    st = partition_and_count(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &stats, true);
     if (st) return st;
     return write_pass(ctx, w, stats, o, os, npairs);
 }
@@ -656,6 +865,17 @@ extern "C" int sj_count(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_re
     DeviceGuard dg(ctx->device);
     ctx->msg[0] = 0;
     Stats stats;
+    BPlan bp;
+    if (plan_blocked(ctx, gd, nR, nS, bp)) {
+        bool direct = false;
+        if ((st = blocked_partition_count(ctx, ctx->ws, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd,
+                                          &stats, &direct)))
+            return st;
+        if (!direct) {
+            *out_npairs = (int64_t)stats.npairs;
+            return SJ_OK;
+        }
+    }
     if ((st = partition_and_count(ctx, ctx->ws, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd,
                                   &stats, true)))
         return st;

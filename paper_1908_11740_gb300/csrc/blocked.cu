@@ -1,0 +1,803 @@
+// blocked.cu -- two-level PBSM on the GPU: the uniform nx x ny grid of the
+// method (Sec. 2.2) is grouped into coarse blocks of G x G tiles.
+//
+//  L1 (global memory): the count -> prefix-sum -> write scheme of Sec. 3.4
+//     steps 2-4, applied to blocks: every CTA counts its slice of the input
+//     per block in shared memory, a scan turns the (block, CTA) counts into
+//     write offsets, and every CTA writes its slice into the blocks
+//     (multi-assignment: a rectangle goes to every block it overlaps).  Each
+//     entry is one aligned 32-byte sector, so the scattered writes are whole
+//     sectors and need no read-modify-write.
+//  L2 (shared memory, fused with the join): one CTA takes a block, assigns
+//     its entries to the block's tiles (again every tile a rectangle
+//     overlaps), sorts every tile by x_l, and runs the forward scan of
+//     Algorithm 1 with the y-test and the reference-point test of Eq. 1.  The
+//     tile segments never leave shared memory.
+//
+// The pairs reported are exactly those of single-level PBSM on the same
+// nx x ny grid: a pair is reported by the tile that holds its reference
+// point, and that tile belongs to exactly one block.
+#include "sj_blocked.h"
+
+namespace sj {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// x / G for x < 2^16 and G <= 32 as a multiply-high by gmul = 2^32 / G + 1
+// (exact in that range); G == 1 passes x through.
+__device__ __forceinline__ int div_g(int x, const BArgs &a) {
+    return a.G == 1 ? x : (int)__umulhi((unsigned)x, a.gmul);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt_b() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// L1 count: per-CTA block histograms (shared memory), slice c of the input.
+// H is CTA-major: H[c * 2NB + side * NB + b].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kL1Threads) k_bcount(BArgs a) {
+    extern __shared__ unsigned hist[];   // 2 * NB
+    const int NB2 = 2 * a.nb;
+    for (int k = threadIdx.x; k < NB2; k += kL1Threads) hist[k] = 0;
+    __syncthreads();
+    const long long n = a.nR + a.nS;
+    const long long q = (n + gridDim.x - 1) / gridDim.x;
+    const long long i0 = (long long)blockIdx.x * q, i1 = min(n, i0 + q);
+    int bad = 0;
+    for (long long base = i0 + threadIdx.x; base < i1; base += 4ll * kL1Threads) {
+        float4 m[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const long long i = base + (long long)u * kL1Threads;
+            if (i < i1) m[u] = ld_stream(i < a.nR ? a.R + i : a.S + (i - a.nR));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const long long i = base + (long long)u * kL1Threads;
+            if (i >= i1) break;
+            if (!rect_ok(m[u])) {
+                bad = 1;
+                continue;
+            }
+            const int side = i >= a.nR;
+            const int bx0 = div_g(cell_of(m[u].x, a.g.x0, a.g.gx, a.g.nx), a);
+            const int bx1 = div_g(cell_of(m[u].z, a.g.x0, a.g.gx, a.g.nx), a);
+            const int by0 = div_g(cell_of(m[u].y, a.g.y0, a.g.gy, a.g.ny), a);
+            const int by1 = div_g(cell_of(m[u].w, a.g.y0, a.g.gy, a.g.ny), a);
+            unsigned *h = hist + side * a.nb;
+            for (int by = by0; by <= by1; by++)
+                for (int bx = bx0; bx <= bx1; bx++) atomicAdd(h + by * a.bx + bx, 1u);
+        }
+    }
+    __syncthreads();
+    unsigned *row = a.H + (size_t)blockIdx.x * NB2;
+    for (int k = threadIdx.x; k < NB2; k += kL1Threads) row[k] = hist[k];
+    if (bad) atomicOr(&a.st->err, kErrBadRect);
+}
+
+// L1 scan, part 1: for every (side, block), the exclusive prefix over CTAs
+// (in place) and the total per (side, block).
+__global__ void __launch_bounds__(256) k_bscan_ctas(BArgs a, int nc) {
+    const int NB2 = 2 * a.nb;
+    const int sb = blockIdx.x * 256 + threadIdx.x;
+    if (sb >= NB2) return;
+    unsigned *__restrict__ H = a.H;
+    unsigned run = 0;
+    for (int c0 = 0; c0 < nc; c0 += 16) {
+        unsigned v[16];
+#pragma unroll
+        for (int u = 0; u < 16; u++) v[u] = c0 + u < nc ? H[(size_t)(c0 + u) * NB2 + sb] : 0u;
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+            if (c0 + u < nc) {
+                H[(size_t)(c0 + u) * NB2 + sb] = run;
+                run += v[u];
+            }
+    }
+    a.btot[sb] = run;
+}
+
+// L1 scan, part 2 (one block of 1024): exclusive scans of the per-block
+// totals of each side -> block starts; the work list of blocks that hold
+// both sides; the totals.
+__global__ void __launch_bounds__(1024) k_bscan_blocks(BArgs a) {
+    __shared__ unsigned long long sh[1024];
+    __shared__ unsigned s_items;
+    if (threadIdx.x == 0) s_items = 0;
+    const int nb = a.nb;
+    const int per = (nb + 1023) / 1024;
+    const int b0 = threadIdx.x * per;
+    for (int side = 0; side < 2; side++) {
+        unsigned long long sum = 0;
+        for (int k = 0; k < per; k++)
+            if (b0 + k < nb) sum += a.btot[side * nb + b0 + k];
+        sh[threadIdx.x] = sum;
+        __syncthreads();
+        for (int d = 1; d < 1024; d <<= 1) {
+            const unsigned long long x = threadIdx.x >= (unsigned)d ? sh[threadIdx.x - d] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += x;
+            __syncthreads();
+        }
+        unsigned long long run = sh[threadIdx.x] - sum;
+        unsigned *bo = side ? a.bo_s : a.bo_r;
+        for (int k = 0; k < per; k++)
+            if (b0 + k < nb) {
+                bo[b0 + k] = (unsigned)run;
+                run += a.btot[side * nb + b0 + k];
+            }
+        if (threadIdx.x == 1023) {
+            bo[nb] = (unsigned)sh[1023];
+            if (side) a.st->e_s = sh[1023];
+            else a.st->e_r = sh[1023];
+            const unsigned long long cap = side ? a.cap_s : a.cap_r;
+            if (sh[1023] > cap) atomicOr(&a.st->err, kErrEntCap);
+        }
+        __syncthreads();
+    }
+    // work list: blocks with entries on both sides, with their ranges
+    __syncthreads();
+    for (int k = 0; k < per; k++) {
+        const int b = b0 + k;
+        if (b < nb && a.btot[b] > 0 && a.btot[nb + b] > 0) {
+            const unsigned idx = atomicAdd(&s_items, 1u);
+            a.items[idx] = (unsigned)b;
+            a.imeta[idx] = make_uint4((unsigned)b, a.bo_r[b], a.btot[b], a.bo_s[b]);
+            a.ins[idx] = a.btot[nb + b];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.st->nchunks = s_items;
+}
+
+// L1 write: the same slice per CTA as k_bcount; shared cursors start at
+// block start + this CTA's prefix.
+__global__ void __launch_bounds__(kL1Threads) k_bscatter(BArgs a) {
+    extern __shared__ unsigned cur[];   // 2 * NB
+    if (block_skip(a.st)) return;
+    const int NB2 = 2 * a.nb;
+    const unsigned *row = a.H + (size_t)blockIdx.x * NB2;
+    for (int k = threadIdx.x; k < NB2; k += kL1Threads)
+        cur[k] = row[k] + (k < a.nb ? a.bo_r[k] : a.bo_s[k - a.nb]);
+    __syncthreads();
+    const long long n = a.nR + a.nS;
+    const long long q = (n + gridDim.x - 1) / gridDim.x;
+    const long long i0 = (long long)blockIdx.x * q, i1 = min(n, i0 + q);
+    for (long long base = i0 + threadIdx.x; base < i1; base += 4ll * kL1Threads) {
+        float4 m[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const long long i = base + (long long)u * kL1Threads;
+            if (i < i1) m[u] = ld_stream(i < a.nR ? a.R + i : a.S + (i - a.nR));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const long long i = base + (long long)u * kL1Threads;
+            if (i >= i1) break;
+            float4 v = m[u];
+            if (!rect_ok(v)) continue;
+            v.x = __fadd_rn(v.x, 0.0f);
+            v.y = __fadd_rn(v.y, 0.0f);
+            v.z = __fadd_rn(v.z, 0.0f);
+            v.w = __fadd_rn(v.w, 0.0f);
+            const int side = i >= a.nR;
+            const unsigned id = (unsigned)(side ? i - a.nR : i);
+            const int cx0 = cell_of(v.x, a.g.x0, a.g.gx, a.g.nx), cx1 = cell_of(v.z, a.g.x0, a.g.gx, a.g.nx);
+            const int cy0 = cell_of(v.y, a.g.y0, a.g.gy, a.g.ny), cy1 = cell_of(v.w, a.g.y0, a.g.gy, a.g.ny);
+            const uint4 tail = make_uint4(id, (unsigned)cx0 | ((unsigned)cx1 << 16),
+                                          (unsigned)cy0 | ((unsigned)cy1 << 16), 0u);
+            BEnt *dst = side ? a.bent_s : a.bent_r;
+            const unsigned long long cap = side ? a.cap_s : a.cap_r;
+            unsigned *c = cur + side * a.nb;
+            const int bx0 = div_g(cx0, a), bx1 = div_g(cx1, a), by0 = div_g(cy0, a), by1 = div_g(cy1, a);
+            for (int by = by0; by <= by1; by++)
+                for (int bx = bx0; bx <= bx1; bx++) {
+                    const unsigned pos = atomicAdd(c + by * a.bx + bx, 1u);
+                    if (pos < cap) {
+                        uint4 *d = reinterpret_cast<uint4 *>(dst + pos);
+                        d[0] = make_uint4(__float_as_uint(v.x), __float_as_uint(v.y), __float_as_uint(v.z),
+                                          __float_as_uint(v.w));
+                        d[1] = tail;
+                    }
+                }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L2: fused tile partition + per-tile sort + sweep of one block per CTA step.
+// ---------------------------------------------------------------------------
+struct BJSmem {
+    unsigned cnt[2][kMaxFine];       // entries per tile of the block
+    unsigned off[2][kMaxFine + 1];   // band offsets; after the scatter: segment ends
+    unsigned key[kFineCap];          // x_l keys
+    float4 mbr[kFineCap];            // the band's entries, sorted by x_l inside every tile segment
+    unsigned id[kFineCap];
+    unsigned short tile[kFineCap];   // band-local tile of each position
+    unsigned short band[kMaxFine + 2];
+};
+
+// ---- TMA bulk copies into shared memory (mbarrier completion) --------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`; false after about a second.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity) {
+    for (unsigned it = 0; it < (1u << 22); it++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 64) __nanosleep(256);
+    }
+    return false;
+}
+
+struct BlockCtx {
+    int cxb, cyb, gw, gh, ntl;
+    unsigned r0, nr1, s0, ns1;
+    const BEnt *er, *es;   // the block's R and S entries (shared-memory copy or global)
+};
+
+// Steps of one band [ta, tb): offsets, scatter into the tile segments,
+// ranks -> sorted entries.  Returns nothing; results live in sm.
+__device__ __forceinline__ void band_stage(BJSmem &sm, const BlockCtx &bc, int ta, int tb, int &nRb,
+                                           int &nSb) {
+    const int NT = kBJThreads;
+    const int nt = tb - ta;
+    // packed exclusive scan of (R count | S count << 32) over the band's tiles
+    __shared__ unsigned long long s_warp[kBJThreads / 32];
+    __shared__ unsigned long long s_tot;
+    const int per = (nt + NT - 1) / NT;
+    const int j0 = threadIdx.x * per;
+    unsigned long long sum = 0;
+    for (int k = 0; k < per; k++) {
+        const int j = j0 + k;
+        if (j < nt) sum += (unsigned long long)sm.cnt[0][ta + j] | ((unsigned long long)sm.cnt[1][ta + j] << 32);
+    }
+    unsigned long long inc = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long o = __shfl_up_sync(kFullMask, inc, d);
+        if ((threadIdx.x & 31) >= d) inc += o;
+    }
+    if ((threadIdx.x & 31) == 31) s_warp[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned long long x = threadIdx.x < NT / 32 ? s_warp[threadIdx.x] : 0ull;
+        unsigned long long xi = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long o = __shfl_up_sync(kFullMask, xi, d);
+            if (threadIdx.x >= (unsigned)d) xi += o;
+        }
+        if (threadIdx.x < NT / 32) s_warp[threadIdx.x] = xi - x;
+        if (threadIdx.x == NT / 32 - 1) s_tot = xi;
+    }
+    __syncthreads();
+    const unsigned long long tot = s_tot;
+    nRb = (int)(tot & 0xffffffffull);
+    nSb = (int)(tot >> 32);
+    unsigned long long run = s_warp[threadIdx.x >> 5] + inc - sum;
+    for (int k = 0; k < per; k++) {
+        const int j = j0 + k;
+        if (j < nt) {
+            sm.off[0][j] = (unsigned)(run & 0xffffffffull);
+            sm.off[1][j] = (unsigned)nRb + (unsigned)(run >> 32);
+            run += (unsigned long long)sm.cnt[0][ta + j] | ((unsigned long long)sm.cnt[1][ta + j] << 32);
+        }
+    }
+    __syncthreads();
+    // scatter the block's entries into the band's tile segments
+    const int row_a = ta / bc.gw, row_b = (tb - 1) / bc.gw;
+    const int n1 = (int)(bc.nr1 + bc.ns1);
+    for (int e = threadIdx.x; e < n1; e += NT) {
+        const int side = e >= (int)bc.nr1;
+        const uint4 *p = reinterpret_cast<const uint4 *>(side ? bc.es + (e - bc.nr1) : bc.er + e);
+        const uint4 t = p[1];
+        const uint4 hd = p[0];
+        const int cx0 = t.y & 0xffff, cx1 = t.y >> 16, cy0 = t.z & 0xffff, cy1 = t.z >> 16;
+        const int ly0 = max(cy0 - bc.cyb, row_a), ly1 = min(cy1 - bc.cyb, row_b);
+        if (ly0 > ly1) continue;
+        const int lx0 = max(cx0 - bc.cxb, 0), lx1 = min(cx1 - bc.cxb, bc.gw - 1);
+        const float4 mb = make_float4(__uint_as_float(hd.x), __uint_as_float(hd.y), __uint_as_float(hd.z),
+                                      __uint_as_float(hd.w));
+        const unsigned k = xkey(mb.x);
+        for (int ly = ly0; ly <= ly1; ly++)
+            for (int lx = lx0; lx <= lx1; lx++) {
+                const int lt = ly * bc.gw + lx;
+                if (lt < ta || lt >= tb) continue;
+                const int j = lt - ta;
+                const unsigned pos = atomicAdd(&sm.off[side][j], 1u);
+                const unsigned flags = (lx + bc.cxb == cx0 ? kFlagCol : 0u) | (ly + bc.cyb == cy0 ? kFlagRow : 0u);
+                sm.key[pos] = k;
+                sm.mbr[pos] = mb;
+                sm.id[pos] = t.x | flags;
+                sm.tile[pos] = (unsigned short)j;
+            }
+    }
+    __syncthreads();
+    // sort every tile segment by x_l in place: rank of each position among
+    // its segment (ties by position), then move through registers
+    const int nb = nRb + nSb;
+    constexpr int KP = kFineCap / kBJThreads;
+    int dst[KP];
+    float4 vm[KP];
+    unsigned vi[KP];
+#pragma unroll
+    for (int q = 0; q < KP; q++) {
+        const int pidx = threadIdx.x + q * NT;
+        dst[q] = -1;
+        if (pidx < nb) {
+            const int side = pidx >= nRb;
+            const int j = sm.tile[pidx];
+            const int s0 = j ? (int)sm.off[side][j - 1] : (side ? nRb : 0);
+            const int s1 = (int)sm.off[side][j];
+            const unsigned k0 = sm.key[pidx];
+            int r = 0;
+            for (int qq = s0; qq < s1; qq++) {
+                const unsigned kq = sm.key[qq];
+                r += (kq < k0) | ((kq == k0) & (qq < pidx));
+            }
+            dst[q] = s0 + r;
+            vm[q] = sm.mbr[pidx];
+            vi[q] = sm.id[pidx];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < KP; q++)
+        if (dst[q] >= 0) {
+            sm.mbr[dst[q]] = vm[q];
+            sm.id[dst[q]] = vi[q];
+        }
+    __syncthreads();
+}
+
+// Candidate range of pivot p in the other side of its tile.
+__device__ __forceinline__ void band_pivot(const BJSmem &sm, int nRb, int p, float4 &pv, unsigned &pid, int &k,
+                                           int &kend, bool &isR) {
+    isR = p < nRb;
+    const int j = sm.tile[p];
+    pv = sm.mbr[p];
+    pid = sm.id[p];
+    const int o = isR ? 1 : 0;
+    int lo = j ? (int)sm.off[o][j - 1] : (o ? nRb : 0);
+    int hi = (int)sm.off[o][j];
+    kend = hi;
+    // first x_l > pivot.x_l (R pivot) or >= pivot.x_l (S pivot)
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const float xm = sm.mbr[mid].x;
+        const bool right = isR ? (xm > pv.x) : (xm >= pv.x);
+        if (right) hi = mid;
+        else lo = mid + 1;
+    }
+    k = lo;
+}
+
+// Count pairs of the staged band; per-tile counts go to tile_pairs if given.
+__device__ __forceinline__ unsigned band_count(const BJSmem &sm, const BlockCtx &bc, int ta, int nRb, int nSb,
+                                               unsigned *tile_pairs, int nx) {
+    unsigned my = 0;
+    const int nb = nRb + nSb;
+    if (nRb == 0 || nSb == 0) return 0;
+    for (int p = threadIdx.x; p < nb; p += kBJThreads) {
+        float4 pv;
+        unsigned pid;
+        int k, kend;
+        bool isR;
+        band_pivot(sm, nRb, p, pv, pid, k, kend, isR);
+        unsigned c = 0;
+        for (; k < kend; k++) {
+            const float4 o = sm.mbr[k];
+            if (o.x > pv.z) break;
+            if (o.y <= pv.w && pv.y <= o.w && reported_here(pid, sm.id[k])) c++;
+        }
+        if (tile_pairs && c) {
+            const int lt = ta + sm.tile[p];
+            const int gt = (bc.cyb + lt / bc.gw) * nx + bc.cxb + lt % bc.gw;
+            atomicAdd(tile_pairs + gt, c);
+        }
+        my += c;
+    }
+    return my;
+}
+
+// Write the pairs of the staged band at out[base + cursor ...].
+__device__ __forceinline__ void band_write(const BJSmem &sm, int nRb, int nSb, int2 *out, unsigned long long base,
+                                           unsigned *s_cursor) {
+    const int nb = nRb + nSb;
+    if (nRb == 0 || nSb == 0) return;
+    const unsigned lane = threadIdx.x & 31;
+    for (int pb = 0; pb < nb; pb += kBJThreads) {
+        const int p = pb + threadIdx.x;
+        const bool active = p < nb;
+        float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+        unsigned pid = 0;
+        int k = 0, kend = 0;
+        bool isR = true;
+        if (active) band_pivot(sm, nRb, p, pv, pid, k, kend, isR);
+        bool go = active;
+        for (;;) {
+            float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool cand = false;
+            if (go && k < kend) {
+                o = sm.mbr[k];
+                cand = o.x <= pv.z;
+            }
+            if (!__any_sync(kFullMask, cand)) break;
+            go = cand;
+            bool hit = false;
+            int2 pr = make_int2(0, 0);
+            if (cand) {
+                if (o.y <= pv.w && pv.y <= o.w) {
+                    const unsigned oid = sm.id[k];
+                    if (reported_here(pid, oid)) {
+                        hit = true;
+                        pr = isR ? make_int2((int)(pid & kIdMask), (int)(oid & kIdMask))
+                                 : make_int2((int)(oid & kIdMask), (int)(pid & kIdMask));
+                    }
+                }
+                k++;
+            }
+            const unsigned hm = __ballot_sync(kFullMask, hit);
+            if (hm) {
+                const int leader = __ffs(hm) - 1;
+                unsigned pos = 0;
+                if ((int)lane == leader) pos = atomicAdd(s_cursor, (unsigned)__popc(hm));
+                pos = __shfl_sync(kFullMask, pos, leader);
+                if (hit) out[base + pos + __popc(hm & lanemask_lt_b())] = pr;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned *s_red) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFullMask, v, d);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    unsigned t = 0;
+    for (int w = 0; w < kBJThreads / 32; w++) t += s_red[w];
+    return t;
+}
+
+// Parallel band split of the block's ntl tiles (see step 2 of k_bjoin).
+// Uses sm.off as scratch; writes sm.band[0..nbands] and the flags.
+__device__ void band_split(BJSmem &sm, int ntl, unsigned *s_nbands, int *s_huge) {
+    constexpr unsigned h = kFineCap / 2;
+    __shared__ unsigned s_w[kBJThreads / 32];
+    __shared__ unsigned s_t;
+    __shared__ int s_hg;
+    if (threadIdx.x == 0) s_hg = 0;
+    // exclusive prefix of per-tile entries -> sm.off[0][lt]
+    const int per = (ntl + kBJThreads - 1) / kBJThreads;
+    const int l0 = threadIdx.x * per;
+    unsigned sum = 0;
+    for (int k = 0; k < per; k++)
+        if (l0 + k < ntl) sum += sm.cnt[0][l0 + k] + sm.cnt[1][l0 + k];
+    unsigned inc = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned o = __shfl_up_sync(kFullMask, inc, d);
+        if ((threadIdx.x & 31) >= d) inc += o;
+    }
+    if ((threadIdx.x & 31) == 31) s_w[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned x = threadIdx.x < kBJThreads / 32 ? s_w[threadIdx.x] : 0u;
+        unsigned xi = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned o = __shfl_up_sync(kFullMask, xi, d);
+            if (threadIdx.x >= (unsigned)d) xi += o;
+        }
+        if (threadIdx.x < kBJThreads / 32) s_w[threadIdx.x] = xi - x;
+    }
+    __syncthreads();
+    unsigned run = s_w[threadIdx.x >> 5] + inc - sum;
+    for (int k = 0; k < per; k++)
+        if (l0 + k < ntl) {
+            sm.off[0][l0 + k] = run;
+            run += sm.cnt[0][l0 + k] + sm.cnt[1][l0 + k];
+        }
+    __syncthreads();
+    // band-start flags -> sm.off[1][lt]
+    for (int lt = threadIdx.x; lt < ntl; lt += kBJThreads) {
+        const unsigned c = sm.cnt[0][lt] + sm.cnt[1][lt];
+        if (c > (unsigned)kFineCap) s_hg = 1;
+        unsigned f = lt == 0;
+        if (lt > 0) {
+            const unsigned cp = sm.cnt[0][lt - 1] + sm.cnt[1][lt - 1];
+            f |= (c > h) | (cp > h) | (sm.off[0][lt] / h != sm.off[0][lt - 1] / h);
+        }
+        sm.off[1][lt] = f;
+    }
+    __syncthreads();
+    // compaction of the flags (exclusive scan) -> band starts
+    sum = 0;
+    for (int k = 0; k < per; k++)
+        if (l0 + k < ntl) sum += sm.off[1][l0 + k];
+    inc = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned o = __shfl_up_sync(kFullMask, inc, d);
+        if ((threadIdx.x & 31) >= d) inc += o;
+    }
+    if ((threadIdx.x & 31) == 31) s_w[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const unsigned x = threadIdx.x < kBJThreads / 32 ? s_w[threadIdx.x] : 0u;
+        unsigned xi = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned o = __shfl_up_sync(kFullMask, xi, d);
+            if (threadIdx.x >= (unsigned)d) xi += o;
+        }
+        if (threadIdx.x < kBJThreads / 32) s_w[threadIdx.x] = xi - x;
+        if (threadIdx.x == kBJThreads / 32 - 1) s_t = xi;
+    }
+    __syncthreads();
+    run = s_w[threadIdx.x >> 5] + inc - sum;
+    for (int k = 0; k < per; k++)
+        if (l0 + k < ntl) {
+            if (sm.off[1][l0 + k]) sm.band[run] = (unsigned short)(l0 + k);
+            run += sm.off[1][l0 + k];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sm.band[s_t] = (unsigned short)ntl;
+        *s_nbands = s_t;
+        *s_huge = s_hg;
+    }
+    __syncthreads();
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    BJSmem &sm = *reinterpret_cast<BJSmem *>(smem_raw);
+    __shared__ unsigned s_meta[2][6];   // current / next item: item, block, r0, nr, s0, ns
+    __shared__ unsigned s_nbands, s_cursor;
+    __shared__ int s_ok, s_huge;
+    __shared__ unsigned long long s_base;
+    __shared__ unsigned s_red[kBJThreads / 32];
+    if (block_skip(a.st)) return;
+    const unsigned nlist = o.list ? *o.list_n : a.st->nchunks;
+    // Thread 0 runs two steps ahead: the work counter is read for item k+2
+    // and the (single-load) metadata of item k+1 is gathered while item k is
+    // joined, so neither round trip stalls the block.
+    unsigned raw_next = 0;   // thread 0: work index of the item after the current one
+    auto load_meta = [&](unsigned raw, unsigned *m) {
+        if (raw < nlist) {
+            const unsigned it = o.list ? o.list[raw] : raw;
+            const uint4 q = a.imeta[it];
+            const unsigned ns = a.ins[it];
+            m[0] = it;
+            m[1] = q.x;
+            m[2] = q.y;
+            m[3] = q.z;
+            m[4] = q.w;
+            m[5] = ns;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.bent_r + q.y),
+                         "r"(q.z * (unsigned)sizeof(BEnt)) : "memory");
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.bent_s + q.w),
+                         "r"(ns * (unsigned)sizeof(BEnt)) : "memory");
+        } else {
+            m[0] = 0xffffffffu;
+        }
+    };
+    if (threadIdx.x == 0) {
+        const unsigned r0_ = atomicAdd(&a.st->work[o.work_slot], 1u);
+        raw_next = atomicAdd(&a.st->work[o.work_slot], 1u);
+        load_meta(r0_, s_meta[0]);
+    }
+    __syncthreads();
+    for (int step = 0;; step++) {
+        const int cur = step & 1;
+        if (s_meta[cur][0] == 0xffffffffu) break;
+        unsigned raw_after = 0;
+        if (threadIdx.x == 0) raw_after = atomicAdd(&a.st->work[o.work_slot], 1u);   // value used next step
+        const unsigned *m = s_meta[cur];
+        const unsigned it = m[0], b = m[1];
+        BlockCtx bc;
+        const int bxi = (int)(b % (unsigned)a.bx), byi = (int)(b / (unsigned)a.bx);
+        bc.cxb = bxi * a.G;
+        bc.cyb = byi * a.G;
+        bc.gw = min(a.G, a.g.nx - bc.cxb);
+        bc.gh = min(a.G, a.g.ny - bc.cyb);
+        bc.ntl = bc.gw * bc.gh;
+        bc.r0 = m[2];
+        bc.nr1 = m[3];
+        bc.s0 = m[4];
+        bc.ns1 = m[5];
+        bc.er = a.bent_r + bc.r0;
+        bc.es = a.bent_s + bc.s0;
+
+        // step 1: entries per tile of the block
+        for (int k = threadIdx.x; k < bc.ntl; k += kBJThreads) {
+            sm.cnt[0][k] = 0;
+            sm.cnt[1][k] = 0;
+        }
+        __syncthreads();
+        const int n1 = (int)(bc.nr1 + bc.ns1);
+        for (int e = threadIdx.x; e < n1; e += kBJThreads) {
+            const int side = e >= (int)bc.nr1;
+            const BEnt *p = side ? bc.es + (e - bc.nr1) : bc.er + e;
+            const uint4 t = reinterpret_cast<const uint4 *>(p)[1];
+            const int lx0 = max((int)(t.y & 0xffff) - bc.cxb, 0), lx1 = min((int)(t.y >> 16) - bc.cxb, bc.gw - 1);
+            const int ly0 = max((int)(t.z & 0xffff) - bc.cyb, 0), ly1 = min((int)(t.z >> 16) - bc.cyb, bc.gh - 1);
+            for (int ly = ly0; ly <= ly1; ly++)
+                for (int lx = lx0; lx <= lx1; lx++) atomicAdd(&sm.cnt[side][ly * bc.gw + lx], 1u);
+        }
+        __syncthreads();
+        // step 2: bands of consecutive tiles that fit in shared memory.
+        // Usually the whole block fits (one band).  Otherwise, with h = half
+        // the capacity, a band starts at every tile whose exclusive prefix
+        // of entries enters a new multiple of h, and around every tile
+        // heavier than h; each band then holds fewer than 2h entries.
+        {
+            unsigned my = 0;
+            for (int lt = threadIdx.x; lt < bc.ntl; lt += kBJThreads) my += sm.cnt[0][lt] + sm.cnt[1][lt];
+            const unsigned total = block_sum(my, s_red);
+            if (total <= (unsigned)kFineCap) {
+                if (threadIdx.x == 0) {
+                    sm.band[0] = 0;
+                    sm.band[1] = (unsigned short)bc.ntl;
+                    s_nbands = 1;
+                    s_huge = 0;
+                }
+            } else {
+                band_split(sm, bc.ntl, &s_nbands, &s_huge);
+            }
+            if (threadIdx.x == 0) s_cursor = 0;
+        }
+        __syncthreads();
+        if (s_huge) {   // a single tile exceeds shared memory: the caller reruns on the direct path
+            if (threadIdx.x == 0) {
+                atomicOr(&a.st->need_direct, 1);
+                if (MODE == MODE_COUNT) o.cnt_out[it] = 0;
+            }
+        } else {
+            const int nbands = (int)s_nbands;
+            if (MODE == MODE_WRITE) {
+                const unsigned long long base = o.off_in[it];
+                for (int bi = 0; bi < nbands; bi++) {
+                    int nRb, nSb;
+                    band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb);
+                    band_write(sm, nRb, nSb, o.out, base, &s_cursor);
+                    __syncthreads();
+                }
+            } else {
+                unsigned tot = 0;
+                int nRb = 0, nSb = 0;
+                for (int bi = 0; bi < nbands; bi++) {
+                    band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb);
+                    tot += block_sum(band_count(sm, bc, sm.band[bi], nRb, nSb,
+                                                MODE == MODE_TILES ? o.tile_pairs : nullptr, a.g.nx),
+                                     s_red);
+                }
+                if (MODE == MODE_COUNT || MODE == MODE_RESERVE) {
+                    if (threadIdx.x == 0) {
+                        if (MODE == MODE_COUNT) {
+                            o.cnt_out[it] = tot;
+                        } else {
+                            const unsigned long long bs = atomicAdd(&a.st->npairs, (unsigned long long)tot);
+                            o.resv[it] = bs;
+                            const bool ok = tot == 0 || bs + tot <= o.cap;
+                            s_ok = ok;
+                            s_base = bs;
+                            if (!ok) {
+                                const unsigned f = atomicAdd(o.nfail, 1u);
+                                o.fail[f] = it;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    if (MODE == MODE_RESERVE && s_ok) {
+                        if (nbands == 1) {
+                            band_write(sm, nRb, nSb, o.out, s_base, &s_cursor);
+                        } else {
+                            for (int bi = 0; bi < nbands; bi++) {
+                                band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb);
+                                band_write(sm, nRb, nSb, o.out, s_base, &s_cursor);
+                                __syncthreads();
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (threadIdx.x == 0) {
+            load_meta(raw_next, s_meta[cur ^ 1]);
+            raw_next = raw_after;
+        }
+        __syncthreads();
+    }
+}
+
+// ---- launchers -------------------------------------------------------------
+size_t bjoin_smem_bytes() { return sizeof(BJSmem); }
+
+cudaError_t blocked_setup() {
+    cudaError_t e;
+    const int sm = (int)sizeof(BJSmem);
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_RESERVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    const int l1 = 8 * kMaxBlocks;
+    if ((e = cudaFuncSetAttribute(k_bcount, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
+    if ((e = cudaFuncSetAttribute(k_bscatter, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
+    return cudaSuccess;
+}
+
+int bjoin_blocks_per_sm() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bjoin<MODE_WRITE>, kBJThreads, sizeof(BJSmem));
+    return nb > 0 ? nb : 1;
+}
+
+int l1_blocks_per_sm(int nb_blocks) {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bscatter, kL1Threads, 8ull * nb_blocks);
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_bcount(const BArgs &a, int nc, cudaStream_t s) {
+    k_bcount<<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bscan(const BArgs &a, int nc, cudaStream_t s) {
+    k_bscan_ctas<<<(2 * a.nb + 255) / 256, 256, 0, s>>>(a, nc);
+    k_bscan_blocks<<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s) {
+    k_bscatter<<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, cudaStream_t s) {
+    const size_t sm = sizeof(BJSmem);
+    switch (mode) {
+        case MODE_COUNT: k_bjoin<MODE_COUNT><<<grid, kBJThreads, sm, s>>>(a, o); break;
+        case MODE_WRITE: k_bjoin<MODE_WRITE><<<grid, kBJThreads, sm, s>>>(a, o); break;
+        case MODE_RESERVE: k_bjoin<MODE_RESERVE><<<grid, kBJThreads, sm, s>>>(a, o); break;
+        default: k_bjoin<MODE_TILES><<<grid, kBJThreads, sm, s>>>(a, o); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sj

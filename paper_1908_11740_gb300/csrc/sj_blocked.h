@@ -1,0 +1,68 @@
+// sj_blocked.h -- the two-level (blocked) PBSM path: argument blocks,
+// constants and launchers.  Internal to the library.
+#pragma once
+#include "sj_common.cuh"
+#include "sj_kernels.h"
+
+namespace sj {
+
+constexpr int kL1Threads = 1024;     // L1 count / write CTAs
+constexpr int kMaxBlocks = 24576;    // blocks per grid (2 * 4 bytes of shared memory each)
+constexpr int kBJThreads = 512;      // fused block-join CTAs (two per SM)
+constexpr int kFineCap = 3072;       // tile entries staged in shared memory per band
+constexpr int kMaxG = 32;            // tiles per block side
+constexpr int kLoadBatch = 4;        // entries a thread loads before using them
+constexpr int kMaxFine = kMaxG * kMaxG;
+
+// An L1 entry: one aligned 32-byte sector.
+struct __align__(32) BEnt {
+    float4 mbr;
+    unsigned id;   // original index
+    unsigned cx;   // first | last tile column << 16
+    unsigned cy;   // first | last tile row << 16
+    unsigned pad;
+};
+
+struct BArgs {
+    const float4 *R;
+    long long nR;
+    const float4 *S;
+    long long nS;
+    GridDev g;
+    int G, bx, by, nb;          // tiles per block side, blocks per axis, blocks
+    unsigned gmul;              // 2^32 / G + 1 (division by G, G > 1)
+    unsigned *H;                // per-CTA block counts, CTA-major (nc x 2nb)
+    unsigned *btot;             // entries per (side, block)
+    unsigned *bo_r, *bo_s;      // block starts per side (nb + 1)
+    unsigned *items;            // blocks with entries on both sides
+    uint4 *imeta;               // per work item: block, R start, R count, S start
+    unsigned *ins;              // per work item: S count
+    BEnt *bent_r, *bent_s;
+    unsigned long long cap_r, cap_s;
+    Stats *st;
+};
+
+struct BJoinOut {
+    int work_slot;
+    const unsigned *list;       // optional subset of work items
+    const unsigned *list_n;
+    unsigned *cnt_out;          // MODE_COUNT: pairs per item
+    const unsigned long long *off_in;   // MODE_WRITE: offset per item
+    unsigned long long *resv;   // MODE_RESERVE: reserved offset per item
+    unsigned *fail;             // MODE_RESERVE: items that did not fit
+    unsigned *nfail;
+    int2 *out;
+    unsigned long long cap;
+    unsigned *tile_pairs;       // MODE_TILES
+};
+
+cudaError_t blocked_setup();
+int bjoin_blocks_per_sm();
+int l1_blocks_per_sm(int nb);
+size_t bjoin_smem_bytes();
+cudaError_t launch_bcount(const BArgs &a, int nc, cudaStream_t s);
+cudaError_t launch_bscan(const BArgs &a, int nc, cudaStream_t s);
+cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s);
+cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, cudaStream_t s);
+
+}  // namespace sj

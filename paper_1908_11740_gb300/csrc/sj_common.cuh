@@ -40,10 +40,11 @@ constexpr int kErrTooMany = 4;       // more than 2^31 entries on a side
 constexpr int kErrChunkCap = 8;      // chunk table overflow (internal)
 constexpr int kErrLargeCap = 16;     // large-tile table overflow (internal)
 constexpr int kErrOutCap = 32;       // one-pass output capacity exceeded
+constexpr int kErrTimeout = 64;      // a bounded device-side wait gave up
 
 // Errors after which the partition is incomplete: every kernel that reads the
 // partition returns at once (the host grows the workspace and starts over).
-constexpr int kErrFatal = kErrEntCap | kErrTooMany | kErrChunkCap | kErrLargeCap;
+constexpr int kErrFatal = kErrEntCap | kErrTooMany | kErrChunkCap | kErrLargeCap | kErrTimeout;
 
 struct GridDev {
     int nx, ny;
@@ -64,7 +65,8 @@ struct Stats {
     unsigned int nfail_large;           // one-pass large-tile blocks that did not fit
     unsigned int work[8];               // work counters of persistent kernels
     int err;
-    int pad[2];
+    int need_direct;                    // blocked path: a tile exceeds shared memory
+    int pad;
 };
 
 // ---- the cell function (tile index of a coordinate) ------------------------

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/sj.h"
+#include "sj_blocked.h"
 #include "sj_common.cuh"
 #include "sj_kernels.h"
 
@@ -25,6 +26,9 @@ struct Workspace {
     Buf pc, poff, resv, fail_c, fail_l;
     Buf sort_tmp;
     Buf in_r, in_s, out;      // staging of sj_join_host
+    // blocked (two-level) path
+    Buf bH, bTot, bBoR, bBoS, bItems, bEntR, bEntS, bPc, bPoff, bResv, bFail, bImeta, bIns;
+    unsigned long long bcap_r = 0, bcap_s = 0;
     unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
     long long T = 0;
     unsigned nch_cap = 0, nl_cap = 0, vb_cap = 0;
@@ -105,12 +109,15 @@ struct sj_ctx {
     cudaStream_t stream = nullptr;
     int num_sms = 1;
     int sweep_bps = 1;
+    int bjoin_bps = 1;
+    int use_blocked = 1;      // the two-level path when the grid allows it
     sj_alloc_fn alloc = nullptr;
     sj_free_fn free_fn = nullptr;
     void *user = nullptr;
     sj::Workspace ws;
     void *h_stats = nullptr;   // pinned copy of sj::Stats
     sj::Timer timer;
+    sj_stats last = {};
     long long launches = 0;
     bool mlp_loaded = false;
     sj::MlpState *mlp = nullptr;

@@ -1,0 +1,57 @@
+"""Command-line driver: run joins of a synthetic workload through the C ABI.
+
+    python -m paper_1908_11740_gb300.run_join --workload gis --scale 0.25 --grid 3000 --reps 3
+
+Useful to time or profile one configuration (for example under ncu, whose
+kernel filter then selects the launches to capture).  Prints the pair count
+and the per-phase device times of the last repetition.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+from . import inputs
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="gis", choices=["gis", "uniform", "zipf"])
+    ap.add_argument("--scale", type=float, default=1.0, help="fraction of the default sizes")
+    ap.add_argument("--grid", type=int, default=3000)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--mode", default="two_pass")
+    ap.add_argument("--rho", type=float, default=0.0)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from . import build, sj
+
+    build.build()
+    if a.workload == "gis":
+        R, S = inputs.gis_pair(int(10_000_000 * a.scale), int(20_000_000 * a.scale), seed=2)
+    elif a.workload == "zipf":
+        R, S = inputs.zipf_pair(int(20_000_000 * a.scale), int(20_000_000 * a.scale), seed=3, rho=a.rho)
+    else:
+        R, S = inputs.uniform_pair(int(10_000_000 * a.scale), int(10_000_000 * a.scale), seed=1)
+    dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
+    ctx = sj.sj_create(0)
+    try:
+        g = sj.make_grid(a.grid)
+        opts = sj.make_opts(a.mode)
+        n = 0
+        for i in range(a.reps):
+            if i == a.reps - 1:
+                sj.sj_timing_enable(ctx, True)
+            n = sj.sj_join(ctx, dR, dS, g, opts).shape[0]
+        t = sj.sj_timing_read(ctx)
+        torch.cuda.synchronize()
+        print(json.dumps({"pairs": n, "stats": sj.sj_last_stats(ctx),
+                          "phases_ms": {k: v[1] for k, v in t.items() if k != "launches" and v[0]}}))
+    finally:
+        sj.sj_destroy(ctx)
+
+
+if __name__ == "__main__":
+    main()

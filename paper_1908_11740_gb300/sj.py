@@ -52,6 +52,13 @@ class sj_timing(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("n", ctypes.c_int64 * 12), ("ms", ctypes.c_double * 12)]
 
 
+class sj_stats(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("block_side", ctypes.c_int32), ("blocks", ctypes.c_int64),
+                ("work_items", ctypes.c_int64), ("l1_entries_r", ctypes.c_int64),
+                ("l1_entries_s", ctypes.c_int64), ("entries_r", ctypes.c_int64),
+                ("entries_s", ctypes.c_int64), ("npairs", ctypes.c_int64)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -81,6 +88,7 @@ SIGNATURES = [
     ("sj_timing_enable", I32, [P, I32]),
     ("sj_timing_read", I32, [P, ctypes.POINTER(sj_timing)]),
     ("sj_timing_phase_name", ctypes.c_char_p, [I32]),
+    ("sj_last_stats", I32, [P, ctypes.POINTER(sj_stats)]),
     ("sj_join_noalloc", I32, [P, I64, P, I64, ctypes.POINTER(sj_grid), P, I64, ctypes.POINTER(I64), P]),
 ]
 
@@ -275,6 +283,12 @@ def sj_join_host(ctx: Context, R, S, grid: sj_grid, out=None, opts: sj_opts | No
                               out.data_ptr() if len(out) else None, len(out), ctypes.byref(n))
     _check(ctx.handle, st)
     return out[: n.value]
+
+
+def sj_last_stats(ctx: Context) -> dict:
+    st = sj_stats()
+    _check(ctx.handle, load().sj_last_stats(ctx.handle, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in sj_stats._fields_}
 
 
 def sj_timing_enable(ctx: Context, on: bool = True) -> None:
