@@ -186,6 +186,55 @@ int sj_join_host(sj_ctx *ctx, const sj_rect *h_R, int64_t nR, const sj_rect *h_S
                  const sj_grid *g, const sj_opts *o, sj_pair *h_out, int64_t cap,
                  int64_t *npairs);
 
+/* ---- learned per-block result-count predictor ---------------------------- */
+/* The one-pass join (SJ_ONE_PASS) sizes its output from predicted result
+ * counts.  The unit of prediction is a block of the two-level partition
+ * (G x G tiles, about 1.5k entries; sj_last_stats().block_side).  Its 32
+ * features are the Eq. 2 histograms of Sec. 3.3 with k = 8 buckets: for R
+ * and S, the x and y projections of a sample (one rectangle of every 16 of
+ * each side, cf. the sampling of Sec. 3.3) counted per bucket of the block's
+ * extent, scaled to the block's exact entry count, then log1p.  Layout of a
+ * feature row: [R x (8) | R y (8) | S x (8) | S y (8)].
+ * The model: 32 -> 64 ReLU -> 64 ReLU -> 1 (predicted log1p of the block's
+ * pairs), bf16 weights, fp32 accumulation.  Parameter vector (fp32,
+ * SJ_MLP_PARAMS): W1[64][32], b1[64], W2[64][64], b2[64], W3[64], b3. */
+#define SJ_MLP_FEATURES 32
+#define SJ_MLP_PARAMS   6337
+typedef struct sj_mlp sj_mlp;
+
+/* Create a model on the context's device (parameters zero; set them with
+ * sj_mlp_set_params).  Release with sj_mlp_free (before its context). */
+int  sj_mlp_create(sj_ctx *ctx, sj_mlp **out);
+void sj_mlp_free(sj_mlp *m);
+/* Host fp32 parameter vector -> model (resets the Adam state). */
+int  sj_mlp_set_params(sj_ctx *ctx, sj_mlp *m, const float *h_params);
+/* Model -> host: fp32 master parameters, and (if h_inference != NULL) the
+ * values inference uses (weights rounded to bf16, as fp32).  Synchronises. */
+int  sj_mlp_get_params(sj_ctx *ctx, const sj_mlp *m, float *h_params, float *h_inference);
+/* d_y[i] = model(d_X[i]) for n rows of SJ_MLP_FEATURES floats (device). */
+int  sj_mlp_forward(sj_ctx *ctx, const sj_mlp *m, const float *d_X, int64_t n, float *d_y);
+/* Gradient of the mean squared error of the n rows (device d_X, d_Y) with
+ * respect to the parameters as inference uses them: d_grad (SJ_MLP_PARAMS
+ * floats, overwritten) and the loss in d_loss[0] (overwritten). */
+int  sj_mlp_grad(sj_ctx *ctx, const sj_mlp *m, const float *d_X, const float *d_Y, int64_t n,
+                 float *d_grad, float *d_loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on a batch;
+ * the batch loss goes to d_loss[0] when d_loss != NULL. */
+int  sj_mlp_train_step(sj_ctx *ctx, sj_mlp *m, const float *d_X, const float *d_Y, int64_t n,
+                       float lr, float *d_loss);
+/* Features and exact labels (log1p of the pairs each block reports) of every
+ * block that holds both R and S entries, for a join on grid *g: d_feat
+ * (cap x SJ_MLP_FEATURES floats), d_label (cap floats) and, if not NULL,
+ * d_block (cap int32: block index by * blocks_x + bx), all caller-owned
+ * device buffers, rows in an unspecified order.  *n_items receives the
+ * number of blocks (also on SJ_EOVERFLOW when cap is too small).  SJ_EINVAL
+ * if the grid or the data do not suit the two-level path. */
+int  sj_block_features(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+                       const sj_grid *g, float *d_feat, float *d_label, int32_t *d_block, int64_t cap,
+                       int64_t *n_items);
+/* Use model m (kept by pointer; NULL = none) for SJ_ONE_PASS / SJ_AUTO. */
+int  sj_set_model(sj_ctx *ctx, const sj_mlp *m);
+
 /* ---- statistics of the last join ------------------------------------------ */
 /* Counters of the last join / count on this context (host copy; valid after
  * the call returned SJ_OK).  path: 1 = two-level (blocked) partitioning,
@@ -202,6 +251,10 @@ typedef struct {
     int64_t l1_entries_r, l1_entries_s;
     int64_t entries_r, entries_s;
     int64_t npairs;
+    int32_t one_pass;            /* 1 if the last join ran one-pass          */
+    int32_t pad;
+    int64_t capacity;            /* one-pass: pairs the output was sized for */
+    int64_t refit_items;         /* one-pass: blocks re-run because they did not fit */
 } sj_stats;
 int sj_last_stats(sj_ctx *ctx, sj_stats *out);
 

@@ -67,6 +67,8 @@ def _load():
         lib.orc_res_free.argtypes = [P]
         lib.orc_cell.restype = I
         lib.orc_cell.argtypes = [F, F, F, I]
+        lib.orc_cells.restype = None
+        lib.orc_cells.argtypes = [P, I64, I, I, F, F, F, F, P]
         lib.orc_tile_counts.restype = None
         lib.orc_tile_counts.argtypes = [P, I64, I, I, F, F, F, F, P]
         _lib = lib
@@ -149,4 +151,14 @@ def tile_counts(A, nx: int, ny: int | None = None, x0=0.0, y0=0.0, x1=1.0, y1=1.
     A = _rects(A)
     out = np.zeros(nx * ny, np.int64)
     lib.orc_tile_counts(A.ctypes.data, len(A), nx, ny, x0, y0, x1, y1, out.ctypes.data)
+    return out
+
+
+def cells(A, nx: int, ny: int | None = None, x0=0.0, y0=0.0, x1=1.0, y1=1.0) -> np.ndarray:
+    """int32[n, 4]: (cx0, cx1, cy0, cy1) of every rectangle."""
+    lib = _load()
+    ny = nx if ny is None else ny
+    A = _rects(A)
+    out = np.zeros((len(A), 4), np.int32)
+    lib.orc_cells(A.ctypes.data, len(A), nx, ny, x0, y0, x1, y1, out.ctypes.data)
     return out

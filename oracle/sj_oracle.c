@@ -349,3 +349,16 @@ void orc_tile_counts(const orc_rect *A, int64_t n, int nx, int ny,
                 cnt[(int64_t)cy * nx + cx]++;
     }
 }
+
+/* The four cells (cx0, cx1, cy0, cy1) of every rectangle, int32[n][4]. */
+void orc_cells(const orc_rect *A, int64_t n, int nx, int ny, float x0, float y0, float x1, float y1,
+               int32_t *out)
+{
+    grid_t g = make_grid(nx, ny, x0, y0, x1, y1);
+    for (int64_t i = 0; i < n; i++) {
+        out[4 * i + 0] = cell_of(A[i].xl, g.gx0, g.ginvx, nx);
+        out[4 * i + 1] = cell_of(A[i].xu, g.gx0, g.ginvx, nx);
+        out[4 * i + 2] = cell_of(A[i].yl, g.gy0, g.ginvy, ny);
+        out[4 * i + 3] = cell_of(A[i].yu, g.gy0, g.ginvy, ny);
+    }
+}

@@ -96,7 +96,8 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
                   &w.key_b, &w.val_a, &w.val_b, &w.lmbr, &w.lid, &w.pc, &w.poff, &w.resv,
                   &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out, &w.bH,
                   &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
-                  &w.bResv, &w.bFail, &w.bImeta, &w.bIns};
+                  &w.bResv, &w.bFail, &w.bImeta, &w.bIns, &w.bFeatRaw, &w.bFeat, &w.bPred,
+                  &w.bOrder, &w.bCapTot};
     for (Buf *b : all) {
         dev_free(ctx, b->p);
         b->p = nullptr;
@@ -232,8 +233,12 @@ extern "C" int sj_create(sj_ctx **out, int device, void *cuda_stream) {
         return SJ_ECUDA;
     }
     c->bjoin_bps = bjoin_blocks_per_sm();
-    if (cudaMallocHost(&c->h_stats, sizeof(Stats)) != cudaSuccess) {
+    if (cudaMallocHost(&c->h_stats, sizeof(Stats)) != cudaSuccess ||
+        cudaMallocHost(&c->h_aux, 64) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        if (c->h_stats) cudaFreeHost(c->h_stats);
+        if (c->h_aux) cudaFreeHost(c->h_aux);
         delete c;
         return SJ_ENOMEM;
     }
@@ -251,6 +256,8 @@ extern "C" int sj_destroy(sj_ctx *ctx) {
     timing_resolve(ctx);
     for (cudaEvent_t e : ctx->timer.pool) cudaEventDestroy(e);
     cudaFreeHost(ctx->h_stats);
+    cudaFreeHost(ctx->h_aux);
+    cudaEventDestroy(ctx->ev_aux);
     delete ctx;
     return SJ_OK;
 }
@@ -349,6 +356,7 @@ int sj::size_workspace(sj_ctx *ctx, Workspace &w, long long T) {
 
 LargeArgs sj::large_args(Workspace &w) {
     LargeArgs a;
+    memset(&a, 0, sizeof a);
     a.off = (const uint2 *)w.off.p;
     a.large = (const unsigned *)w.large.p;
     a.ent_r = (const float4 *)w.ent_r.p;
@@ -514,15 +522,7 @@ int sj::partition_and_count(sj_ctx *ctx, Workspace &w, const float4 *R, long lon
 // ---------------------------------------------------------------------------
 // public joins
 // ---------------------------------------------------------------------------
-// Where the pairs of a join go once their number P is known.
-struct OutSpec {
-    enum Kind { LIB, INTO, WS } kind;
-    sj_pair *into = nullptr;   // INTO: caller buffer
-    int64_t cap = 0;           // INTO: its capacity
-    int2 *got = nullptr;       // the buffer written
-};
-
-static int out_acquire(sj_ctx *ctx, Workspace &w, OutSpec &os, unsigned long long P) {
+int sj::out_acquire(sj_ctx *ctx, Workspace &w, OutSpec &os, unsigned long long P) {
     if (os.kind == OutSpec::INTO) {
         if ((unsigned long long)os.cap < P)
             return fail(ctx, SJ_EOVERFLOW, "need %llu pairs, cap %lld", P, (long long)os.cap);
@@ -542,7 +542,7 @@ static int out_acquire(sj_ctx *ctx, Workspace &w, OutSpec &os, unsigned long lon
     return SJ_OK;
 }
 
-static void out_abandon(sj_ctx *ctx, OutSpec &os) {
+void sj::out_abandon(sj_ctx *ctx, OutSpec &os) {
     if (os.kind == OutSpec::LIB && os.got) dev_free(ctx, os.got);
     os.got = nullptr;
 }
@@ -570,13 +570,9 @@ static int write_pass(sj_ctx *ctx, Workspace &w, const Stats &stats, const sj_op
 // ---------------------------------------------------------------------------
 // the two-level (blocked) path
 // ---------------------------------------------------------------------------
-struct BPlan {
-    int G = 0, bx = 0, by = 0, nb = 0, nc = 0;
-};
-
 // Blocks of G x G tiles holding about 1.5k entries each; false when the grid
 // does not suit the blocked path (then the single-level path runs).
-static bool plan_blocked(sj_ctx *ctx, const GridDev &g, long long nR, long long nS, BPlan &p) {
+bool sj::plan_blocked(sj_ctx *ctx, const GridDev &g, long long nR, long long nS, BPlan &p) {
     if (!ctx->use_blocked || g.nx > 65535 || g.ny > 65535) return false;
     const double est = (double)(nR + nS) * 1.1 + 1.0;
     const double nbt = est / 1536.0 > 1.0 ? est / 1536.0 : 1.0;
@@ -595,7 +591,7 @@ static bool plan_blocked(sj_ctx *ctx, const GridDev &g, long long nR, long long 
     return true;
 }
 
-static int size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p) {
+int sj::size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p) {
     int st;
     if ((st = ensure(ctx, w.stats, sizeof(Stats)))) return st;
     if ((st = ensure(ctx, w.bH, 8ull * p.nb * p.nc))) return st;
@@ -614,9 +610,10 @@ static int size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p) {
     return SJ_OK;
 }
 
-static BArgs blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long nR, const float4 *S,
+BArgs sj::blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long nR, const float4 *S,
                           long long nS, const GridDev &g) {
     BArgs a;
+    memset(&a, 0, sizeof a);   // optional fields (feature sampling) stay off
     a.R = R;
     a.nR = nR;
     a.S = S;
@@ -642,7 +639,7 @@ static BArgs blocked_args(Workspace &w, const BPlan &p, const float4 *R, long lo
     return a;
 }
 
-static BJoinOut bjoin_out(Workspace &w, int slot) {
+BJoinOut sj::bjoin_out(Workspace &w, int slot) {
     BJoinOut o;
     memset(&o, 0, sizeof o);
     o.work_slot = slot;
@@ -655,7 +652,7 @@ static BJoinOut bjoin_out(Workspace &w, int slot) {
 }
 
 // L1 partition of the blocked path (count, scan, write).
-static int enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, const BArgs &a) {
+int sj::enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, const BArgs &a) {
     cudaError_t e;
     cudaStream_t s = ctx->stream;
     {
@@ -680,7 +677,7 @@ static int enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, 
 
 // Blocked partition + count pass.  *use_direct is set when a tile holds more
 // entries than shared memory (the caller then runs the single-level path).
-static int blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const float4 *R,
+int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const float4 *R,
                                    long long nR, const float4 *S, long long nS, const GridDev &g,
                                    Stats *stats, bool *use_direct) {
     *use_direct = false;
@@ -732,12 +729,10 @@ static int join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, 
     const bool one_pass = (mode == SJ_ONE_PASS || mode == SJ_ONE_PASS_HEUR ||
                            (mode == SJ_AUTO && ctx->mlp_loaded));
     if (one_pass) {
-        sj_pair *lib_out = nullptr;
-        sj_pair **plib = os.kind == OutSpec::LIB ? &lib_out : nullptr;
-        int st = join_one_pass(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, o,
-                               mode == SJ_ONE_PASS_HEUR ? 1 : 0, plib, os.into, os.cap, npairs);
-        os.got = os.kind == OutSpec::LIB ? (int2 *)lib_out : (int2 *)os.into;
-        return st;
+        int st = join_one_pass_spec(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, o,
+                                    mode == SJ_ONE_PASS_HEUR ? 1 : 0, os, npairs, nullptr);
+        if (st != ONE_PASS_UNSUITED) return st;
+        os.got = nullptr;   // the grid or the data need the exact two-pass join
     }
     Stats stats;
     int st;
@@ -776,7 +771,7 @@ static int join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, 
     return write_pass(ctx, w, stats, o, os, npairs);
 }
 
-static int check_opts(sj_ctx *ctx, const sj_opts *o) {
+int sj::check_opts(sj_ctx *ctx, const sj_opts *o) {
     if (!o) return SJ_OK;
     if (o->reserved != 0) return fail(ctx, SJ_EINVAL, "sj_opts.reserved must be 0");
     if (o->mode < SJ_TWO_PASS || o->mode > SJ_AUTO) return fail(ctx, SJ_EINVAL, "unknown mode %d", o->mode);

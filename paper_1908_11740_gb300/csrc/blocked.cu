@@ -18,6 +18,7 @@
 // nx x ny grid: a pair is reported by the tile that holds its reference
 // point, and that tile belongs to exactly one block.
 #include "sj_blocked.h"
+#include "sj_learned.h"
 
 namespace sj {
 
@@ -64,13 +65,14 @@ __global__ void __launch_bounds__(kL1Threads) k_bcount(BArgs a) {
                 continue;
             }
             const int side = i >= a.nR;
-            const int bx0 = div_g(cell_of(m[u].x, a.g.x0, a.g.gx, a.g.nx), a);
-            const int bx1 = div_g(cell_of(m[u].z, a.g.x0, a.g.gx, a.g.nx), a);
-            const int by0 = div_g(cell_of(m[u].y, a.g.y0, a.g.gy, a.g.ny), a);
-            const int by1 = div_g(cell_of(m[u].w, a.g.y0, a.g.gy, a.g.ny), a);
+            const int cx0 = cell_of(m[u].x, a.g.x0, a.g.gx, a.g.nx), cx1 = cell_of(m[u].z, a.g.x0, a.g.gx, a.g.nx);
+            const int cy0 = cell_of(m[u].y, a.g.y0, a.g.gy, a.g.ny), cy1 = cell_of(m[u].w, a.g.y0, a.g.gy, a.g.ny);
+            const int bx0 = div_g(cx0, a), bx1 = div_g(cx1, a), by0 = div_g(cy0, a), by1 = div_g(cy1, a);
             unsigned *h = hist + side * a.nb;
             for (int by = by0; by <= by1; by++)
                 for (int bx = bx0; bx <= bx1; bx++) atomicAdd(h + by * a.bx + bx, 1u);
+            if (a.feat_raw && ((side ? i - a.nR : i) % kPhi) == 0)
+                feat_add(a.feat_raw, a.G, a.bx, side, cx0, cx1, cy0, cy1, bx0, bx1, by0, by1);
         }
     }
     __syncthreads();

@@ -1,0 +1,360 @@
+// learned.cu -- the learned result-count predictor of the one-pass join.
+//
+// Unit: a block of the two-level partition (G x G tiles; the unit of work
+// and of output reservation of the join).  Features of a block follow the
+// histograms of Sec. 3.3 (Eq. 2): for each side (R, S) and axis (x, y), k = 8
+// buckets over the block's extent, bucket i counting the rectangles whose
+// projection overlaps it; as in the paper, only a sample (one rectangle of
+// every kPhi of each side) feeds the histograms, and each histogram is then
+// scaled to the block's exact entry count.  The 32 inputs are log1p of those
+// scaled counts.  Buckets are ranges of tile columns (rows), so the features
+// depend only on integer tile indices.
+//
+// Model: 32 -> 64 (ReLU) -> 64 (ReLU) -> 1, weights stored as bf16, every
+// product accumulated in fp32; output = predicted log1p(pairs of the block).
+// Training (forward, backward, Adam) runs in the kernels below.
+#include <cuda_bf16.h>
+
+#include "sj_learned.h"
+
+namespace sj {
+
+// ---------------------------------------------------------------------------
+// features
+// ---------------------------------------------------------------------------
+// feat[it][32] of every work item (block with both sides), scaled to the
+// exact entry counts btot.  A block side without a sample gets its entries
+// spread evenly over the 8 buckets.
+__global__ void k_features(const unsigned *__restrict__ raw, const unsigned *__restrict__ items,
+                           const unsigned *__restrict__ btot, int nb, const Stats *__restrict__ st,
+                           float *__restrict__ feat) {
+    const unsigned n = st->nchunks;
+    for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+        const unsigned b = items[it];
+        const unsigned *r = raw + (size_t)b * kRawPerBlock;
+        float *f = feat + (size_t)it * kFeat;
+        for (int side = 0; side < 2; side++) {
+            const float nt = (float)btot[side * nb + b];
+            const unsigned samp = r[32 + side];
+            for (int q = 0; q < 16; q++) {
+                const float h = samp ? (float)r[side * 16 + q] * nt / (float)samp : nt * 0.125f;
+                f[side * 16 + q] = log1pf(h);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// MLP forward (inference): one warp per sample, bf16 weights in shared memory
+// ---------------------------------------------------------------------------
+struct MlpSmem {
+    __nv_bfloat16 w1[kH1 * kFeat];
+    __nv_bfloat16 w2[kH2 * kH1];
+    __nv_bfloat16 w3[kH2];
+    float b1[kH1], b2[kH2], b3;
+};
+
+__device__ __forceinline__ void mlp_load(MlpSmem &m, const MlpWeights &w) {
+    for (int k = threadIdx.x; k < kH1 * kFeat; k += blockDim.x) m.w1[k] = w.w1[k];
+    for (int k = threadIdx.x; k < kH2 * kH1; k += blockDim.x) m.w2[k] = w.w2[k];
+    for (int k = threadIdx.x; k < kH2; k += blockDim.x) {
+        m.w3[k] = w.w3[k];
+        m.b2[k] = w.b2[k];
+    }
+    for (int k = threadIdx.x; k < kH1; k += blockDim.x) m.b1[k] = w.b1[k];
+    if (threadIdx.x == 0) m.b3 = w.b3[0];
+    __syncthreads();
+}
+
+// lane computes hidden units lane and lane + 32 of both layers; x and h1
+// live in shared memory per warp.  Returns the output on every lane; when
+// act is given, stores z1, z2 (pre-activations) for the backward pass.
+__device__ __forceinline__ float mlp_warp_forward(const MlpSmem &m, const float *x, float *h1s, float *z1o,
+                                                  float *z2o) {
+    const int lane = threadIdx.x & 31;
+    float z1[2], z2[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int j = lane + 32 * u;
+        float acc = m.b1[j];
+#pragma unroll 8
+        for (int k = 0; k < kFeat; k++) acc = fmaf(__bfloat162float(m.w1[j * kFeat + k]), x[k], acc);
+        z1[u] = acc;
+        h1s[j] = fmaxf(acc, 0.0f);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int j = lane + 32 * u;
+        float acc = m.b2[j];
+#pragma unroll 8
+        for (int k = 0; k < kH1; k++) acc = fmaf(__bfloat162float(m.w2[j * kH1 + k]), h1s[k], acc);
+        z2[u] = acc;
+    }
+    float part = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 2; u++) part = fmaf(__bfloat162float(m.w3[lane + 32 * u]), fmaxf(z2[u], 0.0f), part);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+    if (z1o) {
+        z1o[lane] = z1[0];
+        z1o[lane + 32] = z1[1];
+        z2o[lane] = z2[0];
+        z2o[lane + 32] = z2[1];
+    }
+    __syncwarp();
+    return part + m.b3;
+}
+
+constexpr int kMlpThreads = 256;
+constexpr int kMlpWarps = kMlpThreads / 32;
+
+// y[i] = f(X[i]) for i < n (n read from *n_dev when given).
+__global__ void __launch_bounds__(kMlpThreads) k_mlp_forward(MlpWeights w, const float *__restrict__ X,
+                                                             long long n, const unsigned *n_dev,
+                                                             float *__restrict__ y) {
+    __shared__ MlpSmem m;
+    __shared__ float xs[kMlpWarps][kFeat];
+    __shared__ float hs[kMlpWarps][kH1];
+    mlp_load(m, w);
+    const long long nn = n_dev ? (long long)*n_dev : n;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (long long i = (long long)blockIdx.x * kMlpWarps + wid; i < nn; i += (long long)gridDim.x * kMlpWarps) {
+        xs[wid][lane] = X[i * kFeat + lane];
+        __syncwarp();
+        const float out = mlp_warp_forward(m, xs[wid], hs[wid], nullptr, nullptr);
+        if (lane == 0) y[i] = out;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// training: forward + backward of the mean squared error, gradients summed
+// per CTA in shared memory, then added to the global gradient buffer.
+// Parameter layout (fp32, kParams): W1[64x32], b1[64], W2[64x64], b2[64],
+// W3[64], b3[1].  The forward uses the bf16 weights (what inference uses);
+// gradients are with respect to those values.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kMlpThreads) k_mlp_grad(MlpWeights w, const float *__restrict__ X,
+                                                          const float *__restrict__ Y, long long n,
+                                                          float *__restrict__ grad, float *__restrict__ loss) {
+    __shared__ MlpSmem m;
+    __shared__ float g[kParams];
+    __shared__ float xs[kMlpWarps][kFeat];
+    __shared__ float hs[kMlpWarps][kH1];
+    __shared__ float z1s[kMlpWarps][kH1];
+    __shared__ float z2s[kMlpWarps][kH2];
+    __shared__ float d2s[kMlpWarps][kH2];
+    __shared__ float s_loss;
+    mlp_load(m, w);
+    for (int k = threadIdx.x; k < kParams; k += blockDim.x) g[k] = 0.0f;
+    if (threadIdx.x == 0) s_loss = 0.0f;
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float inv_n = 1.0f / (float)(n > 0 ? n : 1);
+    for (long long i = (long long)blockIdx.x * kMlpWarps + wid; i < n; i += (long long)gridDim.x * kMlpWarps) {
+        xs[wid][lane] = X[i * kFeat + lane];
+        __syncwarp();
+        const float out = mlp_warp_forward(m, xs[wid], hs[wid], z1s[wid], z2s[wid]);
+        const float err = out - Y[i];
+        if (lane == 0) atomicAdd(&s_loss, err * err * inv_n);
+        const float dout = 2.0f * err * inv_n;          // d loss / d out
+        // layer 3
+        float d2[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int j = lane + 32 * u;
+            const float z = z2s[wid][j];
+            atomicAdd(&g[kOffW3 + j], dout * fmaxf(z, 0.0f));
+            d2[u] = z > 0.0f ? dout * __bfloat162float(m.w3[j]) : 0.0f;   // d loss / d z2_j
+            d2s[wid][j] = d2[u];
+        }
+        if (lane == 0) atomicAdd(&g[kOffB3], dout);
+        __syncwarp();
+        // layer 2: dW2[j][k] = d2_j * h1_k ; d h1_k = sum_j d2_j W2[j][k]
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int j = lane + 32 * u;
+            atomicAdd(&g[kOffB2 + j], d2[u]);
+            if (d2[u] != 0.0f)
+                for (int kk = 0; kk < kH1; kk++) {   // rotated so the 32 lanes hit 32 banks
+                    const int k = (kk + lane) & (kH1 - 1);
+                    atomicAdd(&g[kOffW2 + j * kH1 + k], d2[u] * hs[wid][k]);
+                }
+        }
+        float d1[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int k = lane + 32 * u;
+            float acc = 0.0f;
+            for (int j = 0; j < kH2; j++) acc = fmaf(d2s[wid][j], __bfloat162float(m.w2[j * kH1 + k]), acc);
+            d1[u] = z1s[wid][k] > 0.0f ? acc : 0.0f;          // d loss / d z1_k
+        }
+        // layer 1
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int j = lane + 32 * u;
+            atomicAdd(&g[kOffB1 + j], d1[u]);
+            if (d1[u] != 0.0f)
+                for (int kk = 0; kk < kFeat; kk++) {
+                    const int k = (kk + lane) & (kFeat - 1);
+                    atomicAdd(&g[kOffW1 + j * kFeat + k], d1[u] * xs[wid][k]);
+                }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kParams; k += blockDim.x)
+        if (g[k] != 0.0f) atomicAdd(grad + k, g[k]);
+    if (threadIdx.x == 0) atomicAdd(loss, s_loss);
+}
+
+// Adam step on the fp32 master parameters, then the bf16 copies.
+__global__ void k_adam(MlpParams p, const float *__restrict__ grad, float lr, float b1, float b2, float eps,
+                       int step) {
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kParams; k += gridDim.x * blockDim.x) {
+        const float gk = grad[k];
+        const float mk = b1 * p.m[k] + (1.0f - b1) * gk;
+        const float vk = b2 * p.v[k] + (1.0f - b2) * gk * gk;
+        p.m[k] = mk;
+        p.v[k] = vk;
+        p.master[k] -= lr * (mk / c1) / (sqrtf(vk / c2) + eps);
+    }
+}
+
+// bf16 weights and fp32 biases of the inference copy from the fp32 master.
+__global__ void k_mlp_publish(MlpParams p, MlpWeights w) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kParams; k += gridDim.x * blockDim.x) {
+        const float v = p.master[k];
+        if (k < kOffB1) w.w1[k - kOffW1] = __float2bfloat16_rn(v);
+        else if (k < kOffW2) w.b1[k - kOffB1] = v;
+        else if (k < kOffB2) w.w2[k - kOffW2] = __float2bfloat16_rn(v);
+        else if (k < kOffW3) w.b2[k - kOffB2] = v;
+        else if (k < kOffB3) w.w3[k - kOffW3] = __float2bfloat16_rn(v);
+        else w.b3[0] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one-pass plan: capacity of every work item from the predicted log1p(pairs),
+// the total, and a heaviest-first order of the items (LPT).
+// ---------------------------------------------------------------------------
+// The non-learned estimate from the same histograms (Eq. 2): I_x = sum_i
+// H_R^x[i] H_S^x[i] estimates the pairs that share an x bucket, I_y alike;
+// assuming x and y independent, pairs ~ I_x I_y / (n_R n_S).
+__global__ void k_heur_pred(const float *__restrict__ feat, const unsigned *__restrict__ items,
+                            const unsigned *__restrict__ btot, int nb, const Stats *__restrict__ st,
+                            float *__restrict__ pred) {
+    const unsigned n = st->nchunks;
+    for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+        const float *f = feat + (size_t)it * kFeat;
+        double ix = 0.0, iy = 0.0;
+        for (int q = 0; q < 8; q++) {
+            ix += (double)expm1f(f[q]) * (double)expm1f(f[16 + q]);
+            iy += (double)expm1f(f[8 + q]) * (double)expm1f(f[24 + q]);
+        }
+        const unsigned b = items[it];
+        const double nn = (double)btot[b] * (double)btot[nb + b];
+        const double p = nn > 0.0 ? ix * iy / nn : 0.0;
+        pred[it] = (float)log1p(p);
+    }
+}
+
+// One CTA of 1024 threads: cap[it] = ceil(expm1(pred) * (1 + margin)) + slack
+// (at least 0); total -> *cap_total; order = items sorted by predicted cost
+// (L1 entries + predicted pairs) into 32 log2 classes, heaviest first.
+__global__ void __launch_bounds__(1024) k_plan(const float *__restrict__ pred, const uint4 *__restrict__ imeta,
+                                               const unsigned *__restrict__ ins, const Stats *__restrict__ st,
+                                               float margin, unsigned slack, unsigned long long *cap_total,
+                                               unsigned *__restrict__ order) {
+    __shared__ unsigned hist[32], base[32];
+    __shared__ unsigned long long s_tot;
+    const unsigned n = st->nchunks;
+    if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_tot = 0;
+    __syncthreads();
+    unsigned long long my = 0;
+    for (unsigned it = threadIdx.x; it < n; it += blockDim.x) {
+        const float e = expm1f(fmaxf(pred[it], 0.0f));
+        const double c = ceil((double)e * (1.0 + (double)margin)) + (double)slack;
+        my += (unsigned long long)(c < 4e9 ? c : 4e9);
+        const double cost = (double)imeta[it].z + (double)ins[it] + (double)e;
+        const int cls = cost >= 1.0 ? min(31, (int)log2(cost)) : 0;
+        atomicAdd(&hist[31 - cls], 1u);
+    }
+    atomicAdd(&s_tot, my);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned acc = 0;
+        for (int q = 0; q < 32; q++) {
+            base[q] = acc;
+            acc += hist[q];
+        }
+        *cap_total = s_tot;
+    }
+    __syncthreads();
+    for (unsigned it = threadIdx.x; it < n; it += blockDim.x) {
+        const float e = expm1f(fmaxf(pred[it], 0.0f));
+        const double cost = (double)imeta[it].z + (double)ins[it] + (double)e;
+        const int cls = cost >= 1.0 ? min(31, (int)log2(cost)) : 0;
+        const unsigned pos = atomicAdd(&base[31 - cls], 1u);
+        order[pos] = it;
+    }
+}
+
+// label[it] = log1p(pairs of work item it) from the count pass.
+__global__ void k_labels(const unsigned *__restrict__ cnt, const Stats *__restrict__ st, float *__restrict__ label) {
+    const unsigned n = st->nchunks;
+    for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x)
+        label[it] = log1pf((float)cnt[it]);
+}
+
+// ---- launchers -------------------------------------------------------------
+cudaError_t launch_labels(const unsigned *cnt, const Stats *st, float *label, int grid, cudaStream_t s) {
+    k_labels<<<grid, 256, 0, s>>>(cnt, st, label);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features(const unsigned *raw, const unsigned *items, const unsigned *btot, int nb,
+                            const Stats *st, float *feat, int grid, cudaStream_t s) {
+    k_features<<<grid, 256, 0, s>>>(raw, items, btot, nb, st, feat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_forward(const MlpWeights &w, const float *X, long long n, const unsigned *n_dev, float *y,
+                               int grid, cudaStream_t s) {
+    k_mlp_forward<<<grid, kMlpThreads, 0, s>>>(w, X, n, n_dev, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_grad(const MlpWeights &w, const float *X, const float *Y, long long n, float *grad,
+                            float *loss, int grid, cudaStream_t s) {
+    k_mlp_grad<<<grid, kMlpThreads, 0, s>>>(w, X, Y, n, grad, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(const MlpParams &p, const float *grad, float lr, float b1, float b2, float eps, int step,
+                        cudaStream_t s) {
+    k_adam<<<(kParams + 255) / 256, 256, 0, s>>>(p, grad, lr, b1, b2, eps, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_publish(const MlpParams &p, const MlpWeights &w, cudaStream_t s) {
+    k_mlp_publish<<<(kParams + 255) / 256, 256, 0, s>>>(p, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_heur_pred(const float *feat, const unsigned *items, const unsigned *btot, int nb,
+                             const Stats *st, float *pred, int grid, cudaStream_t s) {
+    k_heur_pred<<<grid, 256, 0, s>>>(feat, items, btot, nb, st, pred);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const float *pred, const uint4 *imeta, const unsigned *ins, const Stats *st, float margin,
+                        unsigned slack, unsigned long long *cap_total, unsigned *order, cudaStream_t s) {
+    k_plan<<<1, 1024, 0, s>>>(pred, imeta, ins, st, margin, slack, cap_total, order);
+    return cudaGetLastError();
+}
+
+}  // namespace sj

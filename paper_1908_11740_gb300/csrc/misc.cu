@@ -38,14 +38,14 @@ cudaError_t launch_reset_counters(Stats *st, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Not yet available: filled in by the one-pass / sorting / model sources.
-int join_one_pass(sj_ctx *ctx, Workspace &, const float4 *, long long, const float4 *, long long,
-                  const GridDev &, const sj_opts *, int, sj_pair **, sj_pair *, int64_t, int64_t *) {
-    return fail(ctx, SJ_EINVAL, "one-pass mode is not available in this build");
-}
+// Not yet available: filled in by the sorting source.
 int sort_pairs(sj_ctx *ctx, Workspace &, int2 *, unsigned long long) {
     return fail(ctx, SJ_EINVAL, "sort_output is not available in this build");
 }
-void mlp_release(sj_ctx *) {}
+// Models belong to their creator (sj_mlp_free); the context only forgets its reference.
+void mlp_release(sj_ctx *ctx) {
+    ctx->model = nullptr;
+    ctx->mlp_loaded = false;
+}
 
 }  // namespace sj

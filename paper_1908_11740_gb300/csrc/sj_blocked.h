@@ -39,6 +39,7 @@ struct BArgs {
     unsigned *ins;              // per work item: S count
     BEnt *bent_r, *bent_s;
     unsigned long long cap_r, cap_s;
+    unsigned *feat_raw;         // optional: sampled bucket counts per block (learned sizing)
     Stats *st;
 };
 

@@ -28,6 +28,7 @@ struct Workspace {
     Buf in_r, in_s, out;      // staging of sj_join_host
     // blocked (two-level) path
     Buf bH, bTot, bBoR, bBoS, bItems, bEntR, bEntS, bPc, bPoff, bResv, bFail, bImeta, bIns;
+    Buf bFeatRaw, bFeat, bPred, bOrder, bCapTot;   // learned one-pass sizing
     unsigned long long bcap_r = 0, bcap_s = 0;
     unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
     long long T = 0;
@@ -81,11 +82,39 @@ int enqueue_sweep(sj_ctx *ctx, Workspace &w, int mode, int2 *out, unsigned long 
 int read_stats(sj_ctx *ctx, Workspace &w, Stats *out);
 int partition_and_count(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S,
                         long long nS, const GridDev &g, Stats *stats, bool count_pass);
-int join_one_pass(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S,
-                  long long nS, const GridDev &g, const sj_opts *o, int heuristic, sj_pair **lib_out,
-                  sj_pair *into, int64_t cap, int64_t *npairs);
+struct OutSpec;
+// returned by join_one_pass_spec when the grid or the data do not suit the
+// two-level path; the caller then runs the exact two-pass join
+constexpr int ONE_PASS_UNSUITED = -1;
+int join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S, long long nS,
+                       const GridDev &gd, const sj_opts *o, int heuristic, OutSpec &os, int64_t *npairs,
+                       sj_pair **lib_out);
 int sort_pairs(sj_ctx *ctx, Workspace &w, int2 *pairs, unsigned long long n);
 void mlp_release(sj_ctx *ctx);
+
+// Where the pairs of a join go once their number P is known.
+struct OutSpec {
+    enum Kind { LIB, INTO, WS } kind;
+    sj_pair *into = nullptr;   // INTO: caller buffer
+    int64_t cap = 0;           // INTO: its capacity
+    int2 *got = nullptr;       // the buffer written
+};
+
+struct BPlan {
+    int G = 0, bx = 0, by = 0, nb = 0, nc = 0;
+};
+
+int out_acquire(sj_ctx *ctx, Workspace &w, OutSpec &os, unsigned long long P);
+void out_abandon(sj_ctx *ctx, OutSpec &os);
+bool plan_blocked(sj_ctx *ctx, const GridDev &g, long long nR, long long nS, BPlan &p);
+int size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p);
+BArgs blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long nR, const float4 *S, long long nS,
+                   const GridDev &g);
+BJoinOut bjoin_out(Workspace &w, int slot);
+int enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, const BArgs &a);
+int blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const float4 *R, long long nR,
+                            const float4 *S, long long nS, const GridDev &g, Stats *stats, bool *use_direct);
+int check_opts(sj_ctx *ctx, const sj_opts *o);
 
 // misc.cu
 cudaError_t launch_tile_counts(const uint2 *off, long long T, unsigned *cnt_r, unsigned *cnt_s,
@@ -120,7 +149,9 @@ struct sj_ctx {
     sj_stats last = {};
     long long launches = 0;
     bool mlp_loaded = false;
-    sj::MlpState *mlp = nullptr;
+    const sj_mlp *model = nullptr;      // predictor of SJ_ONE_PASS (not owned)
+    void *h_aux = nullptr;              // pinned: one-pass capacity
+    cudaEvent_t ev_aux = nullptr;
     char msg[512];
 };
 

@@ -56,7 +56,12 @@ class sj_stats(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("block_side", ctypes.c_int32), ("blocks", ctypes.c_int64),
                 ("work_items", ctypes.c_int64), ("l1_entries_r", ctypes.c_int64),
                 ("l1_entries_s", ctypes.c_int64), ("entries_r", ctypes.c_int64),
-                ("entries_s", ctypes.c_int64), ("npairs", ctypes.c_int64)]
+                ("entries_s", ctypes.c_int64), ("npairs", ctypes.c_int64), ("one_pass", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("capacity", ctypes.c_int64), ("refit_items", ctypes.c_int64)]
+
+
+SJ_MLP_FEATURES = 32
+SJ_MLP_PARAMS = 6337
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -89,6 +94,15 @@ SIGNATURES = [
     ("sj_timing_read", I32, [P, ctypes.POINTER(sj_timing)]),
     ("sj_timing_phase_name", ctypes.c_char_p, [I32]),
     ("sj_last_stats", I32, [P, ctypes.POINTER(sj_stats)]),
+    ("sj_mlp_create", I32, [P, ctypes.POINTER(P)]),
+    ("sj_mlp_free", None, [P]),
+    ("sj_mlp_set_params", I32, [P, P, P]),
+    ("sj_mlp_get_params", I32, [P, P, P, P]),
+    ("sj_mlp_forward", I32, [P, P, P, I64, P]),
+    ("sj_mlp_grad", I32, [P, P, P, P, I64, P, P]),
+    ("sj_mlp_train_step", I32, [P, P, P, P, I64, ctypes.c_float, P]),
+    ("sj_block_features", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), P, P, P, I64, ctypes.POINTER(I64)]),
+    ("sj_set_model", I32, [P, P]),
     ("sj_join_noalloc", I32, [P, I64, P, I64, ctypes.POINTER(sj_grid), P, I64, ctypes.POINTER(I64), P]),
 ]
 
@@ -363,3 +377,84 @@ def device_view(ptr: int, shape, dtype: torch.dtype) -> torch.Tensor:
     if n == 0:
         return torch.empty(tuple(shape), dtype=dtype, device="cuda")
     return torch.as_tensor(_CudaArray(ptr, shape, typestr), device="cuda")
+
+
+# ---- learned per-block result-count predictor --------------------------------
+class Model:
+    """An sj_mlp on a context (32 -> 64 -> 64 -> 1, bf16 weights)."""
+
+    def __init__(self, ctx: Context, params=None):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(ctx.handle, lib.sj_mlp_create(ctx.handle, ctypes.byref(h)))
+        self.ctx, self.handle = ctx, h.value
+        self.loss_buf = torch.zeros(1, dtype=torch.float32, device=ctx.device)
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, np.float32)
+        if p.shape != (SJ_MLP_PARAMS,):
+            raise ValueError(f"expected {SJ_MLP_PARAMS} parameters")
+        _check(self.ctx.handle, load().sj_mlp_set_params(self.ctx.handle, self.handle, p.ctypes.data))
+
+    def get_params(self, inference: bool = False):
+        import numpy as np
+        master = np.empty(SJ_MLP_PARAMS, np.float32)
+        inf = np.empty(SJ_MLP_PARAMS, np.float32) if inference else None
+        _check(self.ctx.handle, load().sj_mlp_get_params(self.ctx.handle, self.handle, master.ctypes.data,
+                                                         inf.ctypes.data if inf is not None else None))
+        return (master, inf) if inference else master
+
+    def forward(self, X: torch.Tensor) -> torch.Tensor:
+        X = X.contiguous()
+        y = torch.empty(X.shape[0], dtype=torch.float32, device=self.ctx.device)
+        _check(self.ctx.handle, load().sj_mlp_forward(self.ctx.handle, self.handle, X.data_ptr(), X.shape[0],
+                                                      y.data_ptr()))
+        return y
+
+    def grad(self, X: torch.Tensor, Y: torch.Tensor):
+        g = torch.empty(SJ_MLP_PARAMS, dtype=torch.float32, device=self.ctx.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.ctx.device)
+        X, Y = X.contiguous(), Y.contiguous()
+        _check(self.ctx.handle, load().sj_mlp_grad(self.ctx.handle, self.handle, X.data_ptr(), Y.data_ptr(),
+                                                   X.shape[0], g.data_ptr(), loss.data_ptr()))
+        return g, loss
+
+    def train_step(self, X: torch.Tensor, Y: torch.Tensor, lr: float) -> torch.Tensor:
+        """One Adam step; returns the batch loss as a device scalar (no sync)."""
+        _check(self.ctx.handle, load().sj_mlp_train_step(self.ctx.handle, self.handle, X.data_ptr(),
+                                                         Y.data_ptr(), X.shape[0], float(lr),
+                                                         self.loss_buf.data_ptr()))
+        return self.loss_buf
+
+    def free(self):
+        if self.handle:
+            load().sj_mlp_free(self.handle)
+            self.handle = 0
+
+
+def sj_set_model(ctx: Context, model: "Model | None") -> None:
+    _check(ctx.handle, load().sj_set_model(ctx.handle, model.handle if model is not None else None))
+
+
+def sj_block_features(ctx: Context, R, S, grid: sj_grid, with_blocks: bool = False):
+    """(features float32[n, 32], labels float32[n][, block ids int32[n]]) of
+    the blocks of a join: labels = log1p(exact pairs each block reports)."""
+    lib = load()
+    pr, nr = _rects(R, ctx.device)
+    ps, ns = _rects(S, ctx.device)
+    n = ctypes.c_int64()
+    st = lib.sj_block_features(ctx.handle, pr, nr, ps, ns, ctypes.byref(grid), None, None, None, 0,
+                               ctypes.byref(n))
+    if st not in (SJ_OK, SJ_EOVERFLOW):
+        _check(ctx.handle, st)
+    m = max(n.value, 1)
+    X = torch.empty((m, SJ_MLP_FEATURES), dtype=torch.float32, device=ctx.device)
+    Y = torch.empty(m, dtype=torch.float32, device=ctx.device)
+    B = torch.empty(m, dtype=torch.int32, device=ctx.device)
+    _check(ctx.handle, lib.sj_block_features(ctx.handle, pr, nr, ps, ns, ctypes.byref(grid), X.data_ptr(),
+                                             Y.data_ptr(), B.data_ptr(), m, ctypes.byref(n)))
+    k = n.value
+    return (X[:k], Y[:k], B[:k]) if with_blocks else (X[:k], Y[:k])
