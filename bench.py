@@ -43,7 +43,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=3000)
-    ap.add_argument("--mode", default="two_pass")
+    ap.add_argument("--mode", default="one_pass",
+                    help="one_pass (learned sizing, the headline), two_pass or one_pass_heur")
+    ap.add_argument("--model", default=None, help="trained predictor (.npz); default: the packaged one")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other join modes")
     ap.add_argument("--n-r", type=int, default=10_000_000)
     ap.add_argument("--n-s", type=int, default=20_000_000)
     ap.add_argument("--seed", type=int, default=2)
@@ -220,15 +223,43 @@ def ours(args):
     dR, dS = hR.cuda(), hS.cuda()
     ctx = sj.sj_create(local)
     grid = sj.make_grid(args.grid)
+    model = model_header = None
+    if args.mode in ("one_pass", "auto"):
+        from paper_1908_11740_gb300 import learn
+        model, model_header = learn.load(ctx, args.model or learn.DEFAULT_MODEL)
+        sj.sj_set_model(ctx, model)
     opts = sj.make_opts(args.mode)
     stream = torch.cuda.current_stream()
 
-    P = 0
-    for _ in range(max(3, args.warmup)):
-        P = sj.sj_join(ctx, dR, dS, grid, opts).shape[0]
-    last = sj.sj_last_stats(ctx)
-    path = last["path"]
-    E1 = last["l1_entries_r"] + last["l1_entries_s"] if path == 1 else None
+    def timed(o, steps):
+        """ms per join over `steps` joins (CUDA events on the stream), phases."""
+        for _ in range(max(3, args.warmup)):
+            sj.sj_join(ctx, dR, dS, grid, o)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sj.sj_timing_enable(ctx, True)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        npairs = 0
+        for _ in range(steps):
+            out = sj.sj_join(ctx, dR, dS, grid, o)
+            npairs = out.shape[0]
+            del out
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        tm = sj.sj_timing_read(ctx)
+        sj.sj_timing_enable(ctx, False)
+        return ev0.elapsed_time(ev1) / steps, tm, npairs
+
+    P = sj.sj_join(ctx, dR, dS, grid, sj.make_opts("two_pass")).shape[0]
+    last2 = sj.sj_last_stats(ctx)
+    path = last2["path"]
+    E1 = last2["l1_entries_r"] + last2["l1_entries_s"] if path == 1 else None
     cr, cs, _ = sj.sj_tile_stats(ctx, dR, dS, grid)
     E = int(cr.sum().item()) + int(cs.sum().item())
     del cr, cs
@@ -237,24 +268,20 @@ def ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sj.sj_timing_enable(ctx, True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        out = sj.sj_join(ctx, dR, dS, grid, opts)
-        del out
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    timing = sj.sj_timing_read(ctx)
-    sj.sj_timing_enable(ctx, False)
+    ms, timing, P_main = timed(opts, args.steps)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    assert P_main == P, (P_main, P)
+    last = sj.sj_last_stats(ctx)
+    compare = {}
+    if not args.no_compare:
+        for name in ("two_pass", "one_pass_heur"):
+            if name == args.mode:
+                continue
+            cms, ctm, cP = timed(sj.make_opts(name), max(3, args.steps // 2))
+            cl = sj.sj_last_stats(ctx)
+            compare[name] = {"ms_per_step": cms, "value": cP / (cms / 1e3), "pairs": cP,
+                             "capacity": cl["capacity"] if cl["one_pass"] else None,
+                             "refit_blocks": cl["refit_items"] if cl["one_pass"] else None}
     if dist:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -287,8 +314,10 @@ def ours(args):
 
     phases = {k: v for k, v in timing.items() if k != "launches" and v[0] > 0}
     n_in = args.n_r + args.n_s
-    kern = KERNELS[path]
-    cand = {k: v for k, v in phases.items() if k in kern}
+    kern = dict(KERNELS[path])
+    if args.mode.startswith("one_pass"):
+        kern["sweep_write"] = kern["sweep_reserve"]
+    cand = {k: v for k, v in phases.items() if k in kern and k != "sweep_reserve"}
     dom = max(cand, key=lambda k: cand[k][1])
     dom_ms = cand[dom][1] / cand[dom][0]
     ab = alg_bytes(dom, n_in, E1 if path == 1 else E, P)
@@ -307,6 +336,9 @@ def ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(args), "grid": args.grid, "mode": args.mode,
+                       "model": (model_header or {}).get("features") if model_header else None,
+                       "one_pass_capacity": last["capacity"] if last["one_pass"] else None,
+                       "one_pass_refit_blocks": last["refit_items"] if last["one_pass"] else None,
                        "pairs": P, "entries": E, "l1_entries": E1,
                        "path": "two-level (blocks of %d x %d tiles)" % (last["block_side"], last["block_side"])
                        if path == 1 else "single-level",
@@ -320,6 +352,7 @@ def ours(args):
             "join_roofline": {"alg_bytes": b_join, "achieved_gbs": b_join / (ms / 1e3) / 1e9,
                               "frac": b_join / (ms / 1e3) / 1e9 / peak},
             "phases_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in phases.items()},
+            "compare": compare,
             "cpu_baseline": cpu,
             "e2e": {"value": p_all / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": 16 * n_in, "d2h_bytes_per_step": 8 * P,
@@ -328,6 +361,9 @@ def ours(args):
             "gpu_launches": timing["launches"],
         }
         print(json.dumps(line), flush=True)
+    sj.sj_set_model(ctx, None)
+    if model is not None:
+        model.free()
     sj.sj_destroy(ctx)
     if dist:
         dist.destroy_process_group()

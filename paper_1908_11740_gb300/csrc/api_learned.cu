@@ -243,7 +243,8 @@ extern "C" int sj_block_features(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, co
             return cuda_fail(ctx, e, "memset");
         if ((st = enqueue_blocked_partition(ctx, w, p, a))) return st;
         {
-            PhaseScope ph(ctx, PH_MODEL, 1);
+            PhaseScope ph(ctx, PH_MODEL, 2);
+            if ((e = launch_bfeat_sample(a, ctx->num_sms * 4, ctx->stream))) return cuda_fail(ctx, e, "sampling");
             if ((e = launch_features((const unsigned *)w.bFeatRaw.p, a.items, a.btot, p.nb, a.st,
                                      (float *)w.bFeat.p, ctx->num_sms * 2, ctx->stream)))
                 return cuda_fail(ctx, e, "features");
@@ -306,7 +307,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
     BPlan p;
     if (!plan_blocked(ctx, gd, nR, nS, p)) return ONE_PASS_UNSUITED;
     const float margin = o ? o->margin : 0.25f;
-    const unsigned slack = 16;
+    const unsigned slack = 2;
     w.bcap_r = std::max<unsigned long long>(w.bcap_r, (unsigned long long)nR + nR / 8 + 1024);
     w.bcap_s = std::max<unsigned long long>(w.bcap_s, (unsigned long long)nS + nS / 8 + 1024);
     cudaStream_t s = ctx->stream;
@@ -332,7 +333,8 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         }
         unsigned long long *d_cap = (unsigned long long *)w.bCapTot.p;
         {
-            PhaseScope ph(ctx, PH_MODEL, 3);
+            PhaseScope ph(ctx, PH_MODEL, 4);
+            if ((e = launch_bfeat_sample(a, ctx->num_sms * 4, s))) return cuda_fail(ctx, e, "sampling");
             if ((e = launch_features((const unsigned *)w.bFeatRaw.p, a.items, a.btot, p.nb, a.st, (float *)w.bFeat.p,
                                      ctx->num_sms * 2, s)))
                 return cuda_fail(ctx, e, "features");

@@ -65,14 +65,14 @@ __global__ void __launch_bounds__(kL1Threads) k_bcount(BArgs a) {
                 continue;
             }
             const int side = i >= a.nR;
-            const int cx0 = cell_of(m[u].x, a.g.x0, a.g.gx, a.g.nx), cx1 = cell_of(m[u].z, a.g.x0, a.g.gx, a.g.nx);
-            const int cy0 = cell_of(m[u].y, a.g.y0, a.g.gy, a.g.ny), cy1 = cell_of(m[u].w, a.g.y0, a.g.gy, a.g.ny);
-            const int bx0 = div_g(cx0, a), bx1 = div_g(cx1, a), by0 = div_g(cy0, a), by1 = div_g(cy1, a);
+            const int bx0 = div_g(cell_of(m[u].x, a.g.x0, a.g.gx, a.g.nx), a);
+            const int bx1 = div_g(cell_of(m[u].z, a.g.x0, a.g.gx, a.g.nx), a);
+            const int by0 = div_g(cell_of(m[u].y, a.g.y0, a.g.gy, a.g.ny), a);
+            const int by1 = div_g(cell_of(m[u].w, a.g.y0, a.g.gy, a.g.ny), a);
             unsigned *h = hist + side * a.nb;
             for (int by = by0; by <= by1; by++)
                 for (int bx = bx0; bx <= bx1; bx++) atomicAdd(h + by * a.bx + bx, 1u);
-            if (a.feat_raw && ((side ? i - a.nR : i) % kPhi) == 0)
-                feat_add(a.feat_raw, a.G, a.bx, side, cx0, cx1, cy0, cy1, bx0, bx1, by0, by1);
+
         }
     }
     __syncthreads();
@@ -747,7 +747,28 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
     }
 }
 
+// Feature sampling for the learned sizing: rectangles 0, kPhi, 2 kPhi, ... of
+// each side add their bucket ranges to every block they overlap.
+__global__ void __launch_bounds__(256) k_bfeat_sample(BArgs a) {
+    const long long mr = (a.nR + kPhi - 1) / kPhi, ms = (a.nS + kPhi - 1) / kPhi;
+    for (long long k = blockIdx.x * 256ll + threadIdx.x; k < mr + ms; k += 256ll * gridDim.x) {
+        const int side = k >= mr;
+        const long long i = (side ? k - mr : k) * kPhi;
+        const float4 v = ld_stream(side ? a.S + i : a.R + i);
+        if (!rect_ok(v)) continue;
+        const int cx0 = cell_of(v.x, a.g.x0, a.g.gx, a.g.nx), cx1 = cell_of(v.z, a.g.x0, a.g.gx, a.g.nx);
+        const int cy0 = cell_of(v.y, a.g.y0, a.g.gy, a.g.ny), cy1 = cell_of(v.w, a.g.y0, a.g.gy, a.g.ny);
+        feat_add(a.feat_raw, a.G, a.bx, side, cx0, cx1, cy0, cy1, div_g(cx0, a), div_g(cx1, a), div_g(cy0, a),
+                 div_g(cy1, a));
+    }
+}
+
 // ---- launchers -------------------------------------------------------------
+cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s) {
+    k_bfeat_sample<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 size_t bjoin_smem_bytes() { return sizeof(BJSmem); }
 
 cudaError_t blocked_setup() {

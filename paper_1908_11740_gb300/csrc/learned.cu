@@ -249,21 +249,25 @@ __global__ void k_heur_pred(const float *__restrict__ feat, const unsigned *__re
     const unsigned n = st->nchunks;
     for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
         const float *f = feat + (size_t)it * kFeat;
-        double ix = 0.0, iy = 0.0;
+        float ix = 0.0f, iy = 0.0f;
         for (int q = 0; q < 8; q++) {
-            ix += (double)expm1f(f[q]) * (double)expm1f(f[16 + q]);
-            iy += (double)expm1f(f[8 + q]) * (double)expm1f(f[24 + q]);
+            ix = fmaf(expm1f(f[q]), expm1f(f[16 + q]), ix);
+            iy = fmaf(expm1f(f[8 + q]), expm1f(f[24 + q]), iy);
         }
         const unsigned b = items[it];
-        const double nn = (double)btot[b] * (double)btot[nb + b];
-        const double p = nn > 0.0 ? ix * iy / nn : 0.0;
-        pred[it] = (float)log1p(p);
+        const float nn = (float)btot[b] * (float)btot[nb + b];
+        // log1p(ix * iy / nn) computed as log(ix) + log(iy) - log(nn) to stay in range
+        pred[it] = nn > 0.0f && ix > 0.0f && iy > 0.0f ? log1pf(expf(logf(ix) + logf(iy) - logf(nn))) : 0.0f;
     }
 }
 
 // One CTA of 1024 threads: cap[it] = ceil(expm1(pred) * (1 + margin)) + slack
 // (at least 0); total -> *cap_total; order = items sorted by predicted cost
 // (L1 entries + predicted pairs) into 32 log2 classes, heaviest first.
+__device__ __forceinline__ int cost_class(float cost) {
+    return cost >= 1.0f ? min(31, (int)log2f(cost)) : 0;
+}
+
 __global__ void __launch_bounds__(1024) k_plan(const float *__restrict__ pred, const uint4 *__restrict__ imeta,
                                                const unsigned *__restrict__ ins, const Stats *__restrict__ st,
                                                float margin, unsigned slack, unsigned long long *cap_total,
@@ -276,12 +280,10 @@ __global__ void __launch_bounds__(1024) k_plan(const float *__restrict__ pred, c
     __syncthreads();
     unsigned long long my = 0;
     for (unsigned it = threadIdx.x; it < n; it += blockDim.x) {
-        const float e = expm1f(fmaxf(pred[it], 0.0f));
-        const double c = ceil((double)e * (1.0 + (double)margin)) + (double)slack;
-        my += (unsigned long long)(c < 4e9 ? c : 4e9);
-        const double cost = (double)imeta[it].z + (double)ins[it] + (double)e;
-        const int cls = cost >= 1.0 ? min(31, (int)log2(cost)) : 0;
-        atomicAdd(&hist[31 - cls], 1u);
+        const float e = expm1f(fminf(fmaxf(pred[it], 0.0f), 21.0f));   // at most ~1.3e9 pairs a block
+        my += (unsigned long long)ceilf(e * (1.0f + margin)) + slack;
+        const float cost = (float)imeta[it].z + (float)ins[it] + e;
+        atomicAdd(&hist[31 - cost_class(cost)], 1u);
     }
     atomicAdd(&s_tot, my);
     __syncthreads();
@@ -295,10 +297,9 @@ __global__ void __launch_bounds__(1024) k_plan(const float *__restrict__ pred, c
     }
     __syncthreads();
     for (unsigned it = threadIdx.x; it < n; it += blockDim.x) {
-        const float e = expm1f(fmaxf(pred[it], 0.0f));
-        const double cost = (double)imeta[it].z + (double)ins[it] + (double)e;
-        const int cls = cost >= 1.0 ? min(31, (int)log2(cost)) : 0;
-        const unsigned pos = atomicAdd(&base[31 - cls], 1u);
+        const float e = expm1f(fminf(fmaxf(pred[it], 0.0f), 21.0f));
+        const float cost = (float)imeta[it].z + (float)ins[it] + e;
+        const unsigned pos = atomicAdd(&base[31 - cost_class(cost)], 1u);
         order[pos] = it;
     }
 }

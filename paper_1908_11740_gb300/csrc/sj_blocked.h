@@ -64,6 +64,7 @@ size_t bjoin_smem_bytes();
 cudaError_t launch_bcount(const BArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_bscan(const BArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s);
+cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, cudaStream_t s);
 
 }  // namespace sj
