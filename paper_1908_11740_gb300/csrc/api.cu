@@ -97,7 +97,7 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
                   &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out, &w.bH,
                   &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
                   &w.bResv, &w.bFail, &w.bImeta, &w.bIns, &w.bFeatRaw, &w.bFeat, &w.bPred,
-                  &w.bOrder, &w.bCapTot};
+                  &w.bOrder, &w.bCapTot, &w.bCur};
     for (Buf *b : all) {
         dev_free(ctx, b->p);
         b->p = nullptr;
@@ -233,6 +233,12 @@ extern "C" int sj_create(sj_ctx **out, int device, void *cuda_stream) {
         return SJ_ECUDA;
     }
     c->bjoin_bps = bjoin_blocks_per_sm();
+    {
+        const char *e = getenv("SJ_L1_WRITE");   // "private": per-CTA write ranges (tuning / comparison)
+        if (e && strcmp(e, "private") == 0) c->shared_cursors = 0;
+        const char *t = getenv("SJ_BLOCK_TARGET");   // entries per block of the two-level plan
+        if (t && atoi(t) >= 64) c->block_target = atoi(t);
+    }
     if (cudaMallocHost(&c->h_stats, sizeof(Stats)) != cudaSuccess ||
         cudaMallocHost(&c->h_aux, 64) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming) != cudaSuccess) {
@@ -575,7 +581,8 @@ static int write_pass(sj_ctx *ctx, Workspace &w, const Stats &stats, const sj_op
 bool sj::plan_blocked(sj_ctx *ctx, const GridDev &g, long long nR, long long nS, BPlan &p) {
     if (!ctx->use_blocked || g.nx > 65535 || g.ny > 65535) return false;
     const double est = (double)(nR + nS) * 1.1 + 1.0;
-    const double nbt = est / 1536.0 > 1.0 ? est / 1536.0 : 1.0;
+    const double tgt = (double)ctx->block_target;
+    const double nbt = est / tgt > 1.0 ? est / tgt : 1.0;
     int G = (int)ceil(sqrt((double)g.nx * (double)g.ny / nbt));
     if (G < 1) G = 1;
     if (G > kMaxG) G = kMaxG;
@@ -607,6 +614,7 @@ int sj::size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p) {
     if ((st = ensure(ctx, w.bPoff, 8ull * (p.nb + 1)))) return st;
     if ((st = ensure(ctx, w.bResv, 8ull * (p.nb + 1)))) return st;
     if ((st = ensure(ctx, w.bFail, 4ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bCur, 8ull * (p.nb + 1)))) return st;
     return SJ_OK;
 }
 
@@ -635,6 +643,7 @@ BArgs sj::blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long 
     a.bent_s = (BEnt *)w.bEntS.p;
     a.cap_r = w.bcap_r;
     a.cap_s = w.bcap_s;
+    a.cur = nullptr;
     a.st = (Stats *)w.stats.p;
     return a;
 }
@@ -687,6 +696,7 @@ int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const
         int st;
         if ((st = size_blocked(ctx, w, p))) return st;
         BArgs a = blocked_args(w, p, R, nR, S, nS, g);
+        if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
         if ((st = enqueue_blocked_partition(ctx, w, p, a))) return st;
         cudaError_t e;
         {
@@ -748,6 +758,7 @@ static int join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, 
             if ((st = out_acquire(ctx, w, os, P))) return st;
             if (P == 0) return SJ_OK;
             BArgs a = blocked_args(w, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd);
+            if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
             BJoinOut bo = bjoin_out(w, 1);
             bo.out = os.got;
             bo.cap = P;

@@ -238,6 +238,7 @@ extern "C" int sj_block_features(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, co
         if ((st = size_blocked(ctx, w, p)) || (st = size_learned(ctx, w, p))) return st;
         BArgs a = blocked_args(w, p, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd);
         a.feat_raw = (unsigned *)w.bFeatRaw.p;
+        if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
         cudaError_t e;
         if ((e = cudaMemsetAsync(w.bFeatRaw.p, 0, 4ull * kRawPerBlock * p.nb, ctx->stream)))
             return cuda_fail(ctx, e, "memset");
@@ -316,6 +317,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         if ((st = size_blocked(ctx, w, p)) || (st = size_learned(ctx, w, p))) return st;
         BArgs a = blocked_args(w, p, R, nR, S, nS, gd);
         a.feat_raw = (unsigned *)w.bFeatRaw.p;
+        if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
         cudaError_t e;
         {
             PhaseScope ph(ctx, PH_RESET, 0);

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(1024) k_bscan_blocks(BArgs a) {
         for (int k = 0; k < per; k++)
             if (b0 + k < nb) {
                 bo[b0 + k] = (unsigned)run;
+                if (a.cur) a.cur[side * nb + b0 + k] = (unsigned)run;
                 run += a.btot[side * nb + b0 + k];
             }
         if (threadIdx.x == 1023) {
@@ -199,11 +200,78 @@ __global__ void __launch_bounds__(kL1Threads) k_bscatter(BArgs a) {
             for (int by = by0; by <= by1; by++)
                 for (int bx = bx0; bx <= bx1; bx++) {
                     const unsigned pos = atomicAdd(c + by * a.bx + bx, 1u);
-                    if (pos < cap) {
-                        uint4 *d = reinterpret_cast<uint4 *>(dst + pos);
-                        d[0] = make_uint4(__float_as_uint(v.x), __float_as_uint(v.y), __float_as_uint(v.z),
+                    if (pos < cap)
+                        store_bent(dst + pos,
+                                   make_uint4(__float_as_uint(v.x), __float_as_uint(v.y), __float_as_uint(v.z),
+                                              __float_as_uint(v.w)),
+                                   tail);
+                }
+        }
+    }
+}
+
+// L1 write, shared cursors: every CTA appends to one run per block through a
+// global cursor (lanes of a warp that hit the same block take their slots
+// with one atomic), so each block's run is filled front to back by all CTAs
+// together and L2 merges the 32-byte entries into whole lines before they
+// reach DRAM.
+__global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
+    if (block_skip(a.st)) return;
+    const long long n = a.nR + a.nS;
+    const unsigned lane = threadIdx.x & 31;
+    for (long long base = blockIdx.x * 256ll * 4 + threadIdx.x; base - threadIdx.x < n;
+         base += 256ll * 4 * gridDim.x) {
+        float4 m[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const long long i = base + u * 256;
+            if (i < n) m[u] = ld_stream(i < a.nR ? a.R + i : a.S + (i - a.nR));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const long long i = base + u * 256;
+            bool valid = i < n;
+            float4 v = valid ? m[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid && !rect_ok(v)) valid = false;
+            v.x = __fadd_rn(v.x, 0.0f);
+            v.y = __fadd_rn(v.y, 0.0f);
+            v.z = __fadd_rn(v.z, 0.0f);
+            v.w = __fadd_rn(v.w, 0.0f);
+            const int side = i >= a.nR;
+            const unsigned id = (unsigned)(side ? i - a.nR : i);
+            int cx0 = 0, cx1 = -1, cy0 = 0, cy1 = -1;
+            if (valid) {
+                cx0 = cell_of(v.x, a.g.x0, a.g.gx, a.g.nx);
+                cx1 = cell_of(v.z, a.g.x0, a.g.gx, a.g.nx);
+                cy0 = cell_of(v.y, a.g.y0, a.g.gy, a.g.ny);
+                cy1 = cell_of(v.w, a.g.y0, a.g.gy, a.g.ny);
+            }
+            const uint4 head = make_uint4(__float_as_uint(v.x), __float_as_uint(v.y), __float_as_uint(v.z),
                                           __float_as_uint(v.w));
-                        d[1] = tail;
+            const uint4 tail = make_uint4(id, (unsigned)cx0 | ((unsigned)cx1 << 16),
+                                          (unsigned)cy0 | ((unsigned)cy1 << 16), 0u);
+            BEnt *dst = side ? a.bent_s : a.bent_r;
+            const unsigned long long cap = side ? a.cap_s : a.cap_r;
+            const int bx0 = valid ? div_g(cx0, a) : 0, bx1 = valid ? div_g(cx1, a) : -1;
+            const int by0 = valid ? div_g(cy0, a) : 0, by1 = valid ? div_g(cy1, a) : -1;
+            // first block: warp-aggregated slot; further blocks (replicas) one atomic each
+            const unsigned key = valid ? (unsigned)(side * a.nb + by0 * a.bx + bx0) : 0xffffffffu;
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            const int leader = __ffs(peers) - 1;
+            unsigned pos0 = 0;
+            if (valid && (int)lane == leader) pos0 = atomicAdd(a.cur + key, (unsigned)__popc(peers));
+            pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+            if (!valid) continue;
+            pos0 += __popc(peers & ((1u << lane) - 1u));
+            for (int by = by0; by <= by1; by++)
+                for (int bx = bx0; bx <= bx1; bx++) {
+                    const unsigned pos = (by == by0 && bx == bx0)
+                                             ? pos0
+                                             : atomicAdd(a.cur + side * a.nb + by * a.bx + bx, 1u);
+                    if (pos < cap) {
+                        store_bent(dst + pos, head, tail);
+                    } else {
+                        atomicOr(&a.st->err, kErrEntCap);
                     }
                 }
         }
@@ -808,7 +876,8 @@ cudaError_t launch_bscan(const BArgs &a, int nc, cudaStream_t s) {
 }
 
 cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s) {
-    k_bscatter<<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
+    if (a.cur) k_bscatter_shared<<<nc * 8, 256, 0, s>>>(a);
+    else k_bscatter<<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,13 @@ struct __align__(32) BEnt {
     unsigned pad;
 };
 
+// One 32-byte store of an L1 entry (a whole sector in one instruction).
+__device__ __forceinline__ void store_bent(BEnt *dst, uint4 h, uint4 t) {
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "r"(h.x), "r"(h.y), "r"(h.z),
+                 "r"(h.w), "r"(t.x), "r"(t.y), "r"(t.z), "r"(t.w)
+                 : "memory");
+}
+
 struct BArgs {
     const float4 *R;
     long long nR;
@@ -40,6 +47,7 @@ struct BArgs {
     BEnt *bent_r, *bent_s;
     unsigned long long cap_r, cap_s;
     unsigned *feat_raw;         // optional: sampled bucket counts per block (learned sizing)
+    unsigned *cur;              // optional: shared per-block write cursors (2 nb)
     Stats *st;
 };
 

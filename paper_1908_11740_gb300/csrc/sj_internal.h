@@ -29,6 +29,7 @@ struct Workspace {
     // blocked (two-level) path
     Buf bH, bTot, bBoR, bBoS, bItems, bEntR, bEntS, bPc, bPoff, bResv, bFail, bImeta, bIns;
     Buf bFeatRaw, bFeat, bPred, bOrder, bCapTot;   // learned one-pass sizing
+    Buf bCur;                                      // shared L1 write cursors
     unsigned long long bcap_r = 0, bcap_s = 0;
     unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
     long long T = 0;
@@ -140,6 +141,8 @@ struct sj_ctx {
     int sweep_bps = 1;
     int bjoin_bps = 1;
     int use_blocked = 1;      // the two-level path when the grid allows it
+    int shared_cursors = 1;   // L1 write through shared per-block cursors
+    int block_target = 1536;  // L1 entries a block should hold (two-level plan)
     sj_alloc_fn alloc = nullptr;
     sj_free_fn free_fn = nullptr;
     void *user = nullptr;
