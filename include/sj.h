@@ -186,6 +186,26 @@ int sj_join_host(sj_ctx *ctx, const sj_rect *h_R, int64_t nR, const sj_rect *h_S
                  const sj_grid *g, const sj_opts *o, sj_pair *h_out, int64_t cap,
                  int64_t *npairs);
 
+/* ---- batches of independent joins ---------------------------------------- */
+/* nj independent joins (R_j join S_j on grid g[j]) in one pass of the
+ * two-level kernels: one count, one scan, one write and one persistent
+ * block-join launch over the blocks of all joins (each join keeps its own
+ * grid and blocks), captured into CUDA graphs that are replayed while the
+ * arguments do not change (work runs on an internal stream ordered after the
+ * context's stream; the context's stream waits for the result).
+ *   d_R[j], d_S[j], nR[j], nS[j] : device inputs as for sj_join (1 <= nj <= 4096)
+ *   g : nj grids, or NULL = per join, tiles about ten times the average
+ *       rectangle extent (the rule of Sec. 4.3) over the unit square
+ *   d_out, cap : caller-owned device buffer of cap pairs; the pairs of join j
+ *       are d_out[h_offsets[j] .. h_offsets[j+1]) (ids local to the join)
+ *   h_offsets : host, nj + 1 values (also filled on SJ_EOVERFLOW, which is
+ *       returned when cap < h_offsets[nj]; nothing is written then)
+ * Exact two-pass join (o->mode is ignored); synchronises once after counting.
+ * Joins whose tiles exceed shared memory fall back to sj_join_into each. */
+int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const int64_t *nR,
+                  const sj_rect *const *d_S, const int64_t *nS, const sj_grid *g, const sj_opts *o,
+                  sj_pair *d_out, int64_t cap, int64_t *h_offsets);
+
 /* ---- learned per-block result-count predictor ---------------------------- */
 /* The one-pass join (SJ_ONE_PASS) sizes its output from predicted result
  * counts.  The unit of prediction is a block of the two-level partition

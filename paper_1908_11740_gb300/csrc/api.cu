@@ -97,7 +97,7 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
                   &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out, &w.bH,
                   &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
                   &w.bResv, &w.bFail, &w.bImeta, &w.bIns, &w.bFeatRaw, &w.bFeat, &w.bPred,
-                  &w.bOrder, &w.bCapTot, &w.bCur};
+                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff};
     for (Buf *b : all) {
         dev_free(ctx, b->p);
         b->p = nullptr;
@@ -241,10 +241,14 @@ extern "C" int sj_create(sj_ctx **out, int device, void *cuda_stream) {
     }
     if (cudaMallocHost(&c->h_stats, sizeof(Stats)) != cudaSuccess ||
         cudaMallocHost(&c->h_aux, 64) != cudaSuccess ||
+        cudaMallocHost(&c->h_jd, sizeof(JoinDesc) * kMaxJoins) != cudaSuccess ||
+        cudaMallocHost(&c->h_joff, 8ull * (kMaxJoins + 1)) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (c->h_stats) cudaFreeHost(c->h_stats);
         if (c->h_aux) cudaFreeHost(c->h_aux);
+        if (c->h_jd) cudaFreeHost(c->h_jd);
+        if (c->h_joff) cudaFreeHost(c->h_joff);
         delete c;
         return SJ_ENOMEM;
     }
@@ -256,6 +260,7 @@ extern "C" int sj_create(sj_ctx **out, int device, void *cuda_stream) {
 extern "C" int sj_destroy(sj_ctx *ctx) {
     if (!ctx) return SJ_EINVAL;
     DeviceGuard g(ctx->device);
+    batch_release(ctx);
     release(ctx, ctx->ws);
     mlp_release(ctx);
     cudaStreamSynchronize(ctx->stream);
@@ -263,6 +268,8 @@ extern "C" int sj_destroy(sj_ctx *ctx) {
     for (cudaEvent_t e : ctx->timer.pool) cudaEventDestroy(e);
     cudaFreeHost(ctx->h_stats);
     cudaFreeHost(ctx->h_aux);
+    cudaFreeHost(ctx->h_jd);
+    cudaFreeHost(ctx->h_joff);
     cudaEventDestroy(ctx->ev_aux);
     delete ctx;
     return SJ_OK;
@@ -273,6 +280,7 @@ extern "C" int sj_set_allocator(sj_ctx *ctx, sj_alloc_fn alloc, sj_free_fn free_
     if ((alloc == nullptr) != (free_fn == nullptr))
         return fail(ctx, SJ_EINVAL, "allocator needs both alloc and free (or neither)");
     DeviceGuard g(ctx->device);
+    batch_release(ctx);   // cached graphs point into the workspace
     release(ctx, ctx->ws);
     mlp_release(ctx);
     ctx->alloc = alloc;
@@ -615,6 +623,7 @@ int sj::size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p) {
     if ((st = ensure(ctx, w.bResv, 8ull * (p.nb + 1)))) return st;
     if ((st = ensure(ctx, w.bFail, 4ull * (p.nb + 1)))) return st;
     if ((st = ensure(ctx, w.bCur, 8ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bJd, sizeof(JoinDesc) * 2))) return st;
     return SJ_OK;
 }
 
@@ -644,6 +653,9 @@ BArgs sj::blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long 
     a.cap_r = w.bcap_r;
     a.cap_s = w.bcap_s;
     a.cur = nullptr;
+    a.jd = (const JoinDesc *)w.bJd.p;   // filled by enqueue_blocked_partition
+    a.nj = 1;
+    a.nbt = p.nb;
     a.st = (Stats *)w.stats.p;
     return a;
 }
@@ -661,9 +673,39 @@ BJoinOut sj::bjoin_out(Workspace &w, int slot) {
 }
 
 // L1 partition of the blocked path (count, scan, write).
+int sj::upload_joins(sj_ctx *ctx, Workspace &w, const JoinDesc *h, int nj) {
+    int st = ensure(ctx, w.bJd, sizeof(JoinDesc) * (nj + 1));
+    if (st) return st;
+    memcpy(ctx->h_jd, h, sizeof(JoinDesc) * nj);
+    cudaError_t e = cudaMemcpyAsync(w.bJd.p, ctx->h_jd, sizeof(JoinDesc) * nj, cudaMemcpyHostToDevice, ctx->stream);
+    return e ? cuda_fail(ctx, e, "join table copy") : SJ_OK;
+}
+
+// The descriptor of a single join (the kernels read joins from a table).
+int sj::upload_single_join(sj_ctx *ctx, Workspace &w, const BArgs &a) {
+    JoinDesc d;
+    memset(&d, 0, sizeof d);
+    d.R = a.R;
+    d.S = a.S;
+    d.nR = a.nR;
+    d.nS = a.nS;
+    d.in_off = 0;
+    d.g = a.g;
+    d.G = a.G;
+    d.gmul = a.gmul;
+    d.bx = a.bx;
+    d.by = a.by;
+    d.boff = 0;
+    return upload_joins(ctx, w, &d, 1);
+}
+
 int sj::enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, const BArgs &a) {
     cudaError_t e;
     cudaStream_t s = ctx->stream;
+    {
+        int st = upload_single_join(ctx, w, a);
+        if (st) return st;
+    }
     {
         PhaseScope ph(ctx, PH_RESET, 0);
         if ((e = cudaMemsetAsync(w.stats.p, 0, sizeof(Stats), s))) return cuda_fail(ctx, e, "memset");

@@ -1,0 +1,337 @@
+// api_batch.cu -- many independent joins in one pass of the two-level
+// kernels (sj_join_batch): every join keeps its own grid and blocks; all
+// blocks share one index space, so one count, one scan, one write and one
+// persistent block-join launch serve the whole batch.  Each phase is
+// captured once into a CUDA graph on the context's internal stream and
+// replayed while the arguments do not change.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "sj_internal.h"
+
+using namespace sj;
+
+namespace {
+
+struct GraphCache {
+    unsigned long long key = 0;
+    cudaGraphExec_t exec = nullptr;
+};
+
+unsigned long long fnv(unsigned long long h, const void *p, size_t n) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < n; i++) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+}  // namespace
+
+struct sj_batch_state {
+    cudaStream_t gs = nullptr;          // internal stream (capturable)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    GraphCache g1, g2;
+};
+
+static int batch_state(sj_ctx *ctx, sj_batch_state **out) {
+    if (!ctx->batch) {
+        sj_batch_state *b = new (std::nothrow) sj_batch_state();
+        if (!b) return fail(ctx, SJ_ENOMEM, "host allocation");
+        if (cudaStreamCreateWithFlags(&b->gs, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return fail(ctx, SJ_ECUDA, "stream / event creation");
+        }
+        ctx->batch = b;
+    }
+    *out = ctx->batch;
+    return SJ_OK;
+}
+
+void sj::batch_release(sj_ctx *ctx) {
+    sj_batch_state *b = ctx->batch;
+    if (!b) return;
+    cudaStreamSynchronize(b->gs);
+    if (b->g1.exec) cudaGraphExecDestroy(b->g1.exec);
+    if (b->g2.exec) cudaGraphExecDestroy(b->g2.exec);
+    cudaEventDestroy(b->ev_in);
+    cudaEventDestroy(b->ev_out);
+    cudaStreamDestroy(b->gs);
+    delete b;
+    ctx->batch = nullptr;
+}
+
+// Run `body` on the internal stream as a graph cached under `key`.
+template <typename F>
+static int run_graph(sj_ctx *ctx, sj_batch_state *b, GraphCache &gc, unsigned long long key, F body) {
+    cudaError_t e;
+    if (!(gc.exec && gc.key == key)) {
+        if (gc.exec) {
+            cudaGraphExecDestroy(gc.exec);
+            gc.exec = nullptr;
+        }
+        cudaStream_t user = ctx->stream;
+        const bool timer = ctx->timer.on;
+        ctx->stream = b->gs;
+        ctx->timer.on = false;   // no timing events inside a captured graph
+        if ((e = cudaStreamBeginCapture(b->gs, cudaStreamCaptureModeThreadLocal))) {
+            ctx->stream = user;
+            ctx->timer.on = timer;
+            return cuda_fail(ctx, e, "graph capture");
+        }
+        int st = body();
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(b->gs, &graph);
+        ctx->stream = user;
+        ctx->timer.on = timer;
+        if (st) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e) return cuda_fail(ctx, e, "graph capture");
+        e = cudaGraphInstantiate(&gc.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e) {
+            gc.exec = nullptr;
+            return cuda_fail(ctx, e, "graph instantiate");
+        }
+        gc.key = key;
+    }
+    // order after the caller's stream, run, and make the caller's stream wait
+    if ((e = cudaEventRecord(b->ev_in, ctx->stream)) || (e = cudaStreamWaitEvent(b->gs, b->ev_in, 0)) ||
+        (e = cudaGraphLaunch(gc.exec, b->gs)) || (e = cudaEventRecord(b->ev_out, b->gs)) ||
+        (e = cudaStreamWaitEvent(ctx->stream, b->ev_out, 0)))
+        return cuda_fail(ctx, e, "graph launch");
+    return SJ_OK;
+}
+
+// Grid of every join by the rule of Sec. 4.3 (tile extent about ten times
+// the average rectangle extent) over the unit square.
+static int rule_grids(sj_ctx *ctx, Workspace &w, std::vector<JoinDesc> &jd, std::vector<sj_grid> &grids) {
+    const int nj = (int)jd.size();
+    int st;
+    if ((st = upload_joins(ctx, w, jd.data(), nj))) return st;
+    if ((st = ensure(ctx, w.bJoff, 32ull * (nj + 1)))) return st;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.bJoff.p, 0, 32ull * nj, ctx->stream))) return cuda_fail(ctx, e, "memset");
+    BArgs a;
+    memset(&a, 0, sizeof a);
+    a.jd = (const JoinDesc *)w.bJd.p;
+    a.nj = nj;
+    {
+        PhaseScope ph(ctx, PH_OTHER, 1);
+        if ((e = launch_extent_stats(a, (double *)w.bJoff.p, ctx->num_sms * 8, ctx->stream)))
+            return cuda_fail(ctx, e, "extent statistics");
+    }
+    std::vector<double> sums(4ull * nj);
+    if ((e = cudaMemcpyAsync(sums.data(), w.bJoff.p, 32ull * nj, cudaMemcpyDeviceToHost, ctx->stream)) ||
+        (e = cudaStreamSynchronize(ctx->stream)))
+        return cuda_fail(ctx, e, "extent statistics copy");
+    for (int j = 0; j < nj; j++) {
+        const double n = 2.0 * (double)(jd[j].nR + jd[j].nS);
+        const double mean = n > 0 ? (sums[4 * j] + sums[4 * j + 1] + sums[4 * j + 2] + sums[4 * j + 3]) / n : 1e-3;
+        double k = mean > 0 ? 1.0 / (10.0 * mean) : 4096.0;
+        k = std::min(4096.0, std::max(1.0, floor(k + 0.5)));
+        grids[j] = sj_grid{(int32_t)k, (int32_t)k, 0.0f, 0.0f, 1.0f, 1.0f};
+    }
+    return SJ_OK;
+}
+
+extern "C" int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const int64_t *nR,
+                             const sj_rect *const *d_S, const int64_t *nS, const sj_grid *g_in,
+                             const sj_opts *o, sj_pair *d_out, int64_t cap, int64_t *h_offsets) {
+    if (!ctx) return SJ_EINVAL;
+    if (nj < 1 || nj > kMaxJoins) return fail(ctx, SJ_EINVAL, "1 <= joins <= %d", kMaxJoins);
+    if (!d_R || !nR || !d_S || !nS || !h_offsets || cap < 0) return fail(ctx, SJ_EINVAL, "null argument");
+    int st = check_opts(ctx, o);
+    if (st) return st;
+    DeviceGuard dg(ctx->device);
+    ctx->msg[0] = 0;
+    Workspace &w = ctx->ws;
+    sj_batch_state *bs = nullptr;
+    if ((st = batch_state(ctx, &bs))) return st;
+
+    // per-join descriptors: inputs, grids, block plans, offsets
+    std::vector<JoinDesc> jd(nj);
+    std::vector<sj_grid> grids(nj);
+    long long in_off = 0, tot_r = 0, tot_s = 0;
+    for (int j = 0; j < nj; j++) {
+        memset(&jd[j], 0, sizeof(JoinDesc));
+        jd[j].R = (const float4 *)d_R[j];
+        jd[j].S = (const float4 *)d_S[j];
+        jd[j].nR = nR[j];
+        jd[j].nS = nS[j];
+        jd[j].in_off = in_off;
+        if (nR[j] < 0 || nS[j] < 0 || nR[j] >= SJ_MAX_N || nS[j] >= SJ_MAX_N)
+            return fail(ctx, SJ_EINVAL, "join %d: bad sizes", j);
+        in_off += nR[j] + nS[j];
+        tot_r += nR[j];
+        tot_s += nS[j];
+    }
+    if (g_in) {
+        for (int j = 0; j < nj; j++) grids[j] = g_in[j];
+    } else if ((st = rule_grids(ctx, w, jd, grids))) {
+        return st;
+    }
+    int nbt = 0;
+    for (int j = 0; j < nj; j++) {
+        GridDev gd;
+        if ((st = check_inputs(ctx, d_R[j], nR[j], d_S[j], nS[j], &grids[j], &gd))) return st;
+        if (gd.nx > 65535 || gd.ny > 65535) return fail(ctx, SJ_EINVAL, "join %d: grid too large for batches", j);
+        const double est = (double)(nR[j] + nS[j]) * 1.1 + 1.0;
+        const double nbtj = std::max(1.0, est / (double)ctx->block_target);
+        int G = (int)ceil(sqrt((double)gd.nx * (double)gd.ny / nbtj));
+        G = std::max(1, std::min(kMaxG, G));
+        jd[j].g = gd;
+        jd[j].G = G;
+        jd[j].gmul = G > 1 ? (unsigned)(0xFFFFFFFFull / (unsigned long long)G + 1ull) : 0u;
+        jd[j].bx = (gd.nx + G - 1) / G;
+        jd[j].by = (gd.ny + G - 1) / G;
+        jd[j].boff = nbt;
+        if ((long long)nbt + (long long)jd[j].bx * jd[j].by > (1ll << 30)) return fail(ctx, SJ_EINVAL, "too many blocks");
+        nbt += jd[j].bx * jd[j].by;
+    }
+
+    w.bcap_r = std::max<unsigned long long>(w.bcap_r, (unsigned long long)tot_r + tot_r / 8 + 1024);
+    w.bcap_s = std::max<unsigned long long>(w.bcap_s, (unsigned long long)tot_s + tot_s / 8 + 1024);
+    cudaError_t e;
+    for (int attempt = 0; attempt < 3; attempt++) {
+        BPlan p;
+        p.nb = nbt;
+        p.nc = 1;
+        p.G = 1;
+        p.bx = nbt;
+        p.by = 1;
+        if ((st = size_blocked(ctx, w, p)) || (st = upload_joins(ctx, w, jd.data(), nj)) ||
+            (st = ensure(ctx, w.bIjoin, 4ull * (nbt + 1))) || (st = ensure(ctx, w.bJfirst, 4ull * (nj + 1))) ||
+            (st = ensure(ctx, w.bJoff, 32ull * (nj + 1))))
+            return st;
+        BArgs a;
+        memset(&a, 0, sizeof a);
+        a.nb = nbt;
+        a.nbt = nbt;
+        a.nj = nj;
+        a.jd = (const JoinDesc *)w.bJd.p;
+        a.btot = (unsigned *)w.bTot.p;
+        a.bo_r = (unsigned *)w.bBoR.p;
+        a.bo_s = (unsigned *)w.bBoS.p;
+        a.items = (unsigned *)w.bItems.p;
+        a.imeta = (uint4 *)w.bImeta.p;
+        a.ins = (unsigned *)w.bIns.p;
+        a.ijoin = (unsigned *)w.bIjoin.p;
+        a.jfirst = (unsigned *)w.bJfirst.p;
+        a.bent_r = (BEnt *)w.bEntR.p;
+        a.bent_s = (BEnt *)w.bEntS.p;
+        a.cap_r = w.bcap_r;
+        a.cap_s = w.bcap_s;
+        a.cur = (unsigned *)w.bCur.p;
+        a.st = (Stats *)w.stats.p;
+        // the arguments that shape the captured work
+        unsigned long long key = 1469598103934665603ull;
+        key = fnv(key, jd.data(), sizeof(JoinDesc) * nj);
+        key = fnv(key, &a, sizeof a);
+        key = fnv(key, &nj, sizeof nj);
+        const int grid_l1 = ctx->num_sms * 8;
+        const int grid_bj = ctx->num_sms * ctx->bjoin_bps;
+        unsigned long long *d_joff = (unsigned long long *)w.bJoff.p;
+        st = run_graph(ctx, bs, bs->g1, key, [&]() -> int {
+            cudaStream_t s = ctx->stream;
+            cudaError_t e2;
+            if ((e2 = cudaMemsetAsync(w.stats.p, 0, sizeof(Stats), s)) ||
+                (e2 = cudaMemsetAsync(w.bTot.p, 0, 8ull * nbt, s)) ||
+                (e2 = cudaMemsetAsync(w.bPc.p, 0, 4ull * (nbt + 1), s)))
+                return cuda_fail(ctx, e2, "memset");
+            {
+                PhaseScope ph(ctx, PH_COUNT, 1);
+                if ((e2 = launch_bcount_global(a, grid_l1, s))) return cuda_fail(ctx, e2, "batch count");
+            }
+            {
+                PhaseScope ph(ctx, PH_SCAN, 1);
+                if ((e2 = launch_bscan_blocks_only(a, s))) return cuda_fail(ctx, e2, "batch scan");
+            }
+            {
+                PhaseScope ph(ctx, PH_SCATTER, 1);
+                if ((e2 = launch_bscatter(a, ctx->num_sms, s))) return cuda_fail(ctx, e2, "batch write");
+            }
+            {
+                PhaseScope ph(ctx, PH_SWEEP_COUNT, 1);
+                if ((e2 = launch_bjoin(MODE_COUNT, a, bjoin_out(w, 0), grid_bj, s))) return cuda_fail(ctx, e2, "batch join");
+            }
+            {
+                PhaseScope ph(ctx, PH_PAIRSCAN, 2);
+                if ((e2 = launch_scan_pairs((const unsigned *)w.bPc.p, (unsigned)nbt, (unsigned long long *)w.bPoff.p,
+                                            (Stats *)w.stats.p, s)))
+                    return cuda_fail(ctx, e2, "pair scan");
+                if ((e2 = launch_join_offsets(a, (const unsigned long long *)w.bPoff.p, d_joff, s)))
+                    return cuda_fail(ctx, e2, "join offsets");
+            }
+            if ((e2 = cudaMemcpyAsync(ctx->h_stats, w.stats.p, sizeof(Stats), cudaMemcpyDeviceToHost, s)) ||
+                (e2 = cudaMemcpyAsync(ctx->h_joff, d_joff, 8ull * (nj + 1), cudaMemcpyDeviceToHost, s)))
+                return cuda_fail(ctx, e2, "copy");
+            return SJ_OK;
+        });
+        if (st) return st;
+        if ((e = cudaStreamSynchronize(ctx->stream))) return cuda_fail(ctx, e, "stream sync");
+        Stats stats;
+        memcpy(&stats, ctx->h_stats, sizeof stats);
+        if (stats.err & kErrBadRect) return fail(ctx, SJ_EINVAL, "invalid rectangle in the batch");
+        if (stats.err & kErrEntCap) {
+            w.bcap_r = std::max<unsigned long long>(w.bcap_r, stats.e_r + stats.e_r / 8 + 1024);
+            w.bcap_s = std::max<unsigned long long>(w.bcap_s, stats.e_s + stats.e_s / 8 + 1024);
+            continue;
+        }
+        if (stats.err) return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", stats.err);
+        const unsigned long long *joff = (const unsigned long long *)ctx->h_joff;
+        for (int j = 0; j <= nj; j++) h_offsets[j] = (int64_t)joff[j];
+        const unsigned long long P = stats.npairs;
+        memset(&ctx->last, 0, sizeof ctx->last);
+        ctx->last.path = 1;
+        ctx->last.blocks = nbt;
+        ctx->last.work_items = stats.nchunks;
+        ctx->last.l1_entries_r = (int64_t)stats.e_r;
+        ctx->last.l1_entries_s = (int64_t)stats.e_s;
+        ctx->last.npairs = (int64_t)P;
+        if (stats.need_direct) {
+            // a tile of some join exceeds shared memory: count and join each one
+            // exactly on its own (the blocked counts skipped that join's block)
+            h_offsets[0] = 0;
+            for (int j = 0; j < nj; j++) {
+                int64_t n = 0;
+                if ((st = sj_count(ctx, d_R[j], nR[j], d_S[j], nS[j], &grids[j], &n))) return st;
+                h_offsets[j + 1] = h_offsets[j] + n;
+            }
+            if (cap < h_offsets[nj])
+                return fail(ctx, SJ_EOVERFLOW, "need %lld pairs, cap %lld", (long long)h_offsets[nj], (long long)cap);
+            for (int j = 0; j < nj; j++) {
+                int64_t n = 0;
+                if (h_offsets[j + 1] == h_offsets[j]) continue;
+                if ((st = sj_join_into(ctx, d_R[j], nR[j], d_S[j], nS[j], &grids[j], nullptr, d_out + h_offsets[j],
+                                       h_offsets[j + 1] - h_offsets[j], &n)))
+                    return st;
+            }
+            ctx->last.npairs = h_offsets[nj];
+            return SJ_OK;
+        }
+        if ((unsigned long long)cap < P) return fail(ctx, SJ_EOVERFLOW, "need %llu pairs, cap %lld", P, (long long)cap);
+        if (P == 0) return SJ_OK;
+        if (!d_out) return fail(ctx, SJ_EINVAL, "null output buffer");
+        unsigned long long key2 = fnv(key, &d_out, sizeof d_out);
+        key2 = fnv(key2, &P, sizeof P);
+        return run_graph(ctx, bs, bs->g2, key2, [&]() -> int {
+            BJoinOut bo = bjoin_out(w, 1);
+            bo.out = (int2 *)d_out;
+            bo.cap = P;
+            PhaseScope ph(ctx, PH_SWEEP_WRITE, 1);
+            cudaError_t e2 = launch_bjoin(MODE_WRITE, a, bo, grid_bj, ctx->stream);
+            return e2 ? cuda_fail(ctx, e2, "batch join") : SJ_OK;
+        });
+    }
+    return fail(ctx, SJ_EINTERNAL, "batch workspace did not converge");
+}

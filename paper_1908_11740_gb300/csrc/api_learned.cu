@@ -325,6 +325,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
                 (e = cudaMemsetAsync(w.bFeatRaw.p, 0, 4ull * kRawPerBlock * p.nb, s)))
                 return cuda_fail(ctx, e, "memset");
         }
+        if ((st = upload_single_join(ctx, w, a))) return st;
         {
             PhaseScope ph(ctx, PH_COUNT, 1);
             if ((e = launch_bcount(a, p.nc, s))) return cuda_fail(ctx, e, "block count kernel");

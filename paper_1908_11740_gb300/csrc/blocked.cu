@@ -104,15 +104,17 @@ __global__ void __launch_bounds__(256) k_bscan_ctas(BArgs a, int nc) {
 }
 
 // L1 scan, part 2 (one block of 1024): exclusive scans of the per-block
-// totals of each side -> block starts; the work list of blocks that hold
-// both sides; the totals.
+// totals of each side -> block starts (and the shared write cursors); the
+// work list of blocks that hold both sides, in block order (so the items of
+// each join are consecutive), with their ranges, join and each join's first
+// item; the totals.
 __global__ void __launch_bounds__(1024) k_bscan_blocks(BArgs a) {
     __shared__ unsigned long long sh[1024];
-    __shared__ unsigned s_items;
-    if (threadIdx.x == 0) s_items = 0;
-    const int nb = a.nb;
+    __shared__ int s_boff[kMaxJoins + 1];
+    const int nb = a.nbt;
     const int per = (nb + 1023) / 1024;
     const int b0 = threadIdx.x * per;
+    for (int j = threadIdx.x; j < a.nj; j += 1024) s_boff[j] = a.jd[j].boff;
     for (int side = 0; side < 2; side++) {
         unsigned long long sum = 0;
         for (int k = 0; k < per; k++)
@@ -142,19 +144,55 @@ __global__ void __launch_bounds__(1024) k_bscan_blocks(BArgs a) {
         }
         __syncthreads();
     }
-    // work list: blocks with entries on both sides, with their ranges
-    __syncthreads();
+    // work list in block order: exclusive scan of the "both sides" flags
+    unsigned cntf = 0;
     for (int k = 0; k < per; k++) {
         const int b = b0 + k;
-        if (b < nb && a.btot[b] > 0 && a.btot[nb + b] > 0) {
-            const unsigned idx = atomicAdd(&s_items, 1u);
+        cntf += (b < nb && a.btot[b] > 0 && a.btot[nb + b] > 0);
+    }
+    sh[threadIdx.x] = cntf;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const unsigned long long x = threadIdx.x >= (unsigned)d ? sh[threadIdx.x - d] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += x;
+        __syncthreads();
+    }
+    unsigned idx = (unsigned)(sh[threadIdx.x] - cntf);
+    for (int k = 0; k < per; k++) {
+        const int b = b0 + k;
+        if (b >= nb) break;
+        // join of block b: the last join whose first block is <= b
+        int lo = 0, hi = a.nj;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_boff[mid] <= b) lo = mid;
+            else hi = mid;
+        }
+        if (a.jfirst && s_boff[lo] == b) a.jfirst[lo] = idx;
+        if (a.btot[b] > 0 && a.btot[nb + b] > 0) {
             a.items[idx] = (unsigned)b;
             a.imeta[idx] = make_uint4((unsigned)b, a.bo_r[b], a.btot[b], a.bo_s[b]);
             a.ins[idx] = a.btot[nb + b];
+            if (a.ijoin) a.ijoin[idx] = (unsigned)lo;
+            idx++;
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) a.st->nchunks = s_items;
+    if (threadIdx.x == 1023) {
+        a.st->nchunks = (unsigned)sh[1023];
+        if (a.jfirst) a.jfirst[a.nj] = (unsigned)sh[1023];
+    }
+}
+
+// Pairs before every join's first item (two-pass offsets), nj + 1 values.
+__global__ void k_join_offsets(BArgs a, const unsigned long long *__restrict__ poff,
+                               unsigned long long *__restrict__ joff) {
+    const unsigned n = a.st->nchunks;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= a.nj; j += gridDim.x * blockDim.x) {
+        const unsigned f = a.jfirst[j];
+        joff[j] = f < n ? poff[f] : a.st->npairs;
+    }
 }
 
 // L1 write: the same slice per CTA as k_bcount; shared cursors start at
@@ -215,36 +253,54 @@ __global__ void __launch_bounds__(kL1Threads) k_bscatter(BArgs a) {
 // with one atomic), so each block's run is filled front to back by all CTAs
 // together and L2 merges the 32-byte entries into whole lines before they
 // reach DRAM.
+// Join of global input index i (binary search over the joins' first
+// indices, kept in shared memory).
+__device__ __forceinline__ int join_of(const long long *jin, int nj, long long i) {
+    int lo = 0, hi = nj;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (jin[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int div_gj(int x, const JoinDesc &d) {
+    return d.G == 1 ? x : (int)__umulhi((unsigned)x, d.gmul);
+}
+
 __global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
+    extern __shared__ long long s_jin[];   // nj + 1
     if (block_skip(a.st)) return;
-    const long long n = a.nR + a.nS;
+    for (int j = threadIdx.x; j < a.nj; j += 256) s_jin[j] = a.jd[j].in_off;
+    if (threadIdx.x == 0) s_jin[a.nj] = a.jd[a.nj - 1].in_off + a.jd[a.nj - 1].nR + a.jd[a.nj - 1].nS;
+    __syncthreads();
+    const long long n = s_jin[a.nj];
     const unsigned lane = threadIdx.x & 31;
     for (long long base = blockIdx.x * 256ll * 4 + threadIdx.x; base - threadIdx.x < n;
          base += 256ll * 4 * gridDim.x) {
-        float4 m[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const long long i = base + u * 256;
-            if (i < n) m[u] = ld_stream(i < a.nR ? a.R + i : a.S + (i - a.nR));
-        }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const long long i = base + u * 256;
             bool valid = i < n;
-            float4 v = valid ? m[u] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int j = valid ? (a.nj == 1 ? 0 : join_of(s_jin, a.nj, i)) : 0;
+            const JoinDesc &d = a.jd[j];
+            const long long li = i - s_jin[j];
+            const int side = li >= d.nR;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (valid) v = ld_stream(side ? d.S + (li - d.nR) : d.R + li);
             if (valid && !rect_ok(v)) valid = false;
             v.x = __fadd_rn(v.x, 0.0f);
             v.y = __fadd_rn(v.y, 0.0f);
             v.z = __fadd_rn(v.z, 0.0f);
             v.w = __fadd_rn(v.w, 0.0f);
-            const int side = i >= a.nR;
-            const unsigned id = (unsigned)(side ? i - a.nR : i);
+            const unsigned id = (unsigned)(side ? li - d.nR : li);
             int cx0 = 0, cx1 = -1, cy0 = 0, cy1 = -1;
             if (valid) {
-                cx0 = cell_of(v.x, a.g.x0, a.g.gx, a.g.nx);
-                cx1 = cell_of(v.z, a.g.x0, a.g.gx, a.g.nx);
-                cy0 = cell_of(v.y, a.g.y0, a.g.gy, a.g.ny);
-                cy1 = cell_of(v.w, a.g.y0, a.g.gy, a.g.ny);
+                cx0 = cell_of(v.x, d.g.x0, d.g.gx, d.g.nx);
+                cx1 = cell_of(v.z, d.g.x0, d.g.gx, d.g.nx);
+                cy0 = cell_of(v.y, d.g.y0, d.g.gy, d.g.ny);
+                cy1 = cell_of(v.w, d.g.y0, d.g.gy, d.g.ny);
             }
             const uint4 head = make_uint4(__float_as_uint(v.x), __float_as_uint(v.y), __float_as_uint(v.z),
                                           __float_as_uint(v.w));
@@ -252,10 +308,11 @@ __global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
                                           (unsigned)cy0 | ((unsigned)cy1 << 16), 0u);
             BEnt *dst = side ? a.bent_s : a.bent_r;
             const unsigned long long cap = side ? a.cap_s : a.cap_r;
-            const int bx0 = valid ? div_g(cx0, a) : 0, bx1 = valid ? div_g(cx1, a) : -1;
-            const int by0 = valid ? div_g(cy0, a) : 0, by1 = valid ? div_g(cy1, a) : -1;
+            const int bx0 = valid ? div_gj(cx0, d) : 0, bx1 = valid ? div_gj(cx1, d) : -1;
+            const int by0 = valid ? div_gj(cy0, d) : 0, by1 = valid ? div_gj(cy1, d) : -1;
+            const unsigned cb = (unsigned)side * (unsigned)a.nbt + (unsigned)d.boff;
             // first block: warp-aggregated slot; further blocks (replicas) one atomic each
-            const unsigned key = valid ? (unsigned)(side * a.nb + by0 * a.bx + bx0) : 0xffffffffu;
+            const unsigned key = valid ? cb + (unsigned)(by0 * d.bx + bx0) : 0xffffffffu;
             const unsigned peers = __match_any_sync(0xffffffffu, key);
             const int leader = __ffs(peers) - 1;
             unsigned pos0 = 0;
@@ -265,17 +322,53 @@ __global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
             pos0 += __popc(peers & ((1u << lane) - 1u));
             for (int by = by0; by <= by1; by++)
                 for (int bx = bx0; bx <= bx1; bx++) {
-                    const unsigned pos = (by == by0 && bx == bx0)
-                                             ? pos0
-                                             : atomicAdd(a.cur + side * a.nb + by * a.bx + bx, 1u);
-                    if (pos < cap) {
-                        store_bent(dst + pos, head, tail);
-                    } else {
-                        atomicOr(&a.st->err, kErrEntCap);
-                    }
+                    const unsigned pos = (by == by0 && bx == bx0) ? pos0 : atomicAdd(a.cur + cb + by * d.bx + bx, 1u);
+                    if (pos < cap) store_bent(dst + pos, head, tail);
+                    else atomicOr(&a.st->err, kErrEntCap);
                 }
         }
     }
+}
+
+// L1 count with global per-block totals (any number of blocks; batches):
+// lanes of a warp that hit the same block add with one atomic.
+__global__ void __launch_bounds__(256) k_bcount_global(BArgs a) {
+    extern __shared__ long long s_jin[];   // nj + 1
+    for (int j = threadIdx.x; j < a.nj; j += 256) s_jin[j] = a.jd[j].in_off;
+    if (threadIdx.x == 0) s_jin[a.nj] = a.jd[a.nj - 1].in_off + a.jd[a.nj - 1].nR + a.jd[a.nj - 1].nS;
+    __syncthreads();
+    const long long n = s_jin[a.nj];
+    int bad = 0;
+    for (long long base = blockIdx.x * 256ll + threadIdx.x; base - threadIdx.x < n; base += 256ll * gridDim.x) {
+        const long long i = base;
+        bool valid = i < n;
+        const int j = valid ? (a.nj == 1 ? 0 : join_of(s_jin, a.nj, i)) : 0;
+        const JoinDesc &d = a.jd[j];
+        const long long li = i - s_jin[j];
+        const int side = li >= d.nR;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) v = ld_stream(side ? d.S + (li - d.nR) : d.R + li);
+        if (valid && !rect_ok(v)) {
+            valid = false;
+            bad = 1;
+        }
+        int bx0 = 0, bx1 = -1, by0 = 0, by1 = -1;
+        if (valid) {
+            bx0 = div_gj(cell_of(v.x, d.g.x0, d.g.gx, d.g.nx), d);
+            bx1 = div_gj(cell_of(v.z, d.g.x0, d.g.gx, d.g.nx), d);
+            by0 = div_gj(cell_of(v.y, d.g.y0, d.g.gy, d.g.ny), d);
+            by1 = div_gj(cell_of(v.w, d.g.y0, d.g.gy, d.g.ny), d);
+        }
+        const unsigned cb = (unsigned)side * (unsigned)a.nbt + (unsigned)d.boff;
+        const unsigned key = valid ? cb + (unsigned)(by0 * d.bx + bx0) : 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.btot + key, (unsigned)__popc(peers));
+        if (!valid) continue;
+        for (int by = by0; by <= by1; by++)
+            for (int bx = bx0; bx <= bx1; bx++)
+                if (by != by0 || bx != bx0) atomicAdd(a.btot + cb + by * d.bx + bx, 1u);
+    }
+    if (bad) atomicOr(&a.st->err, kErrBadRect);
 }
 
 // ---------------------------------------------------------------------------
@@ -656,7 +749,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BJSmem &sm = *reinterpret_cast<BJSmem *>(smem_raw);
-    __shared__ unsigned s_meta[2][6];   // current / next item: item, block, r0, nr, s0, ns
+    __shared__ unsigned s_meta[2][12];  // current / next item: item, block, r0, nr, s0, ns, join geometry
     __shared__ unsigned s_nbands, s_cursor;
     __shared__ int s_ok, s_huge;
     __shared__ unsigned long long s_base;
@@ -672,12 +765,17 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
             const unsigned it = o.list ? o.list[raw] : raw;
             const uint4 q = a.imeta[it];
             const unsigned ns = a.ins[it];
+            const JoinDesc &d = a.jd[a.nj == 1 ? 0 : a.ijoin[it]];
             m[0] = it;
-            m[1] = q.x;
+            m[1] = q.x - (unsigned)d.boff;   // block inside its join
             m[2] = q.y;
             m[3] = q.z;
             m[4] = q.w;
             m[5] = ns;
+            m[6] = (unsigned)d.G;
+            m[7] = (unsigned)d.bx;
+            m[8] = (unsigned)d.g.nx;
+            m[9] = (unsigned)d.g.ny;
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.bent_r + q.y),
                          "r"(q.z * (unsigned)sizeof(BEnt)) : "memory");
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.bent_s + q.w),
@@ -699,12 +797,13 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
         if (threadIdx.x == 0) raw_after = atomicAdd(&a.st->work[o.work_slot], 1u);   // value used next step
         const unsigned *m = s_meta[cur];
         const unsigned it = m[0], b = m[1];
+        const int jG = (int)m[6], jbx = (int)m[7], jnx = (int)m[8], jny = (int)m[9];
         BlockCtx bc;
-        const int bxi = (int)(b % (unsigned)a.bx), byi = (int)(b / (unsigned)a.bx);
-        bc.cxb = bxi * a.G;
-        bc.cyb = byi * a.G;
-        bc.gw = min(a.G, a.g.nx - bc.cxb);
-        bc.gh = min(a.G, a.g.ny - bc.cyb);
+        const int bxi = (int)(b % (unsigned)jbx), byi = (int)(b / (unsigned)jbx);
+        bc.cxb = bxi * jG;
+        bc.cyb = byi * jG;
+        bc.gw = min(jG, jnx - bc.cxb);
+        bc.gh = min(jG, jny - bc.cyb);
         bc.ntl = bc.gw * bc.gh;
         bc.r0 = m[2];
         bc.nr1 = m[3];
@@ -831,7 +930,32 @@ __global__ void __launch_bounds__(256) k_bfeat_sample(BArgs a) {
     }
 }
 
+// Sums of widths and heights of every join's rectangles (for the grid rule),
+// out[4 j + 0..3] = sum w_R, sum h_R, sum w_S, sum h_S (float64).
+__global__ void __launch_bounds__(256) k_extent_stats(BArgs a, double *__restrict__ out) {
+    extern __shared__ long long s_jin[];
+    for (int j = threadIdx.x; j < a.nj; j += 256) s_jin[j] = a.jd[j].in_off;
+    if (threadIdx.x == 0) s_jin[a.nj] = a.jd[a.nj - 1].in_off + a.jd[a.nj - 1].nR + a.jd[a.nj - 1].nS;
+    __syncthreads();
+    const long long n = s_jin[a.nj];
+    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += 256ll * gridDim.x) {
+        const int j = a.nj == 1 ? 0 : join_of(s_jin, a.nj, i);
+        const JoinDesc &d = a.jd[j];
+        const long long li = i - s_jin[j];
+        const int side = li >= d.nR;
+        const float4 v = ld_stream(side ? d.S + (li - d.nR) : d.R + li);
+        if (!rect_ok(v)) continue;
+        atomicAdd(out + 4 * j + 2 * side, (double)(v.z - v.x));
+        atomicAdd(out + 4 * j + 2 * side + 1, (double)(v.w - v.y));
+    }
+}
+
 // ---- launchers -------------------------------------------------------------
+cudaError_t launch_extent_stats(const BArgs &a, double *out, int grid, cudaStream_t s) {
+    k_extent_stats<<<grid, 256, 8ull * (a.nj + 1), s>>>(a, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s) {
     k_bfeat_sample<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
@@ -869,14 +993,30 @@ cudaError_t launch_bcount(const BArgs &a, int nc, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_bscan_blocks_only(const BArgs &a, cudaStream_t s) {
+    k_bscan_blocks<<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bscan(const BArgs &a, int nc, cudaStream_t s) {
     k_bscan_ctas<<<(2 * a.nb + 255) / 256, 256, 0, s>>>(a, nc);
     k_bscan_blocks<<<1, 1024, 0, s>>>(a);
     return cudaGetLastError();
 }
 
+cudaError_t launch_bcount_global(const BArgs &a, int grid, cudaStream_t s) {
+    k_bcount_global<<<grid, 256, 8ull * (a.nj + 1), s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_join_offsets(const BArgs &a, const unsigned long long *poff, unsigned long long *joff,
+                                cudaStream_t s) {
+    k_join_offsets<<<(a.nj + 256) / 256, 256, 0, s>>>(a, poff, joff);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s) {
-    if (a.cur) k_bscatter_shared<<<nc * 8, 256, 0, s>>>(a);
+    if (a.cur) k_bscatter_shared<<<nc * 8, 256, 8ull * (a.nj + 1), s>>>(a);
     else k_bscatter<<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
     return cudaGetLastError();
 }

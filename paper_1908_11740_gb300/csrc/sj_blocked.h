@@ -12,6 +12,7 @@ constexpr int kBJThreads = 512;      // fused block-join CTAs (two per SM)
 constexpr int kFineCap = 3072;       // tile entries staged in shared memory per band
 constexpr int kMaxG = 32;            // tiles per block side
 constexpr int kLoadBatch = 4;        // entries a thread loads before using them
+constexpr int kMaxJoins = 4096;      // joins in one batch
 constexpr int kMaxFine = kMaxG * kMaxG;
 
 // An L1 entry: one aligned 32-byte sector.
@@ -30,6 +31,20 @@ __device__ __forceinline__ void store_bent(BEnt *dst, uint4 h, uint4 t) {
                  : "memory");
 }
 
+// One join of a (possibly batched) two-level partition: its inputs, grid,
+// block plan and place in the global input and block index spaces.
+struct JoinDesc {
+    const float4 *R, *S;
+    long long nR, nS;
+    long long in_off;       // first global input index (R of this join, then S)
+    GridDev g;
+    int G;                  // tiles per block side
+    unsigned gmul;          // 2^32 / G + 1
+    int bx, by;             // blocks per axis
+    int boff;               // first global block id
+    int pad;
+};
+
 struct BArgs {
     const float4 *R;
     long long nR;
@@ -47,7 +62,12 @@ struct BArgs {
     BEnt *bent_r, *bent_s;
     unsigned long long cap_r, cap_s;
     unsigned *feat_raw;         // optional: sampled bucket counts per block (learned sizing)
-    unsigned *cur;              // optional: shared per-block write cursors (2 nb)
+    unsigned *cur;              // optional: shared per-block write cursors (2 nbt)
+    const JoinDesc *jd;         // the joins (one for a single join)
+    int nj;                     // number of joins
+    int nbt;                    // blocks of all joins (== nb for a single join)
+    unsigned *ijoin;            // join of every work item
+    unsigned *jfirst;           // first work item of every join (nj + 1)
     Stats *st;
 };
 
@@ -70,7 +90,12 @@ int bjoin_blocks_per_sm();
 int l1_blocks_per_sm(int nb);
 size_t bjoin_smem_bytes();
 cudaError_t launch_bcount(const BArgs &a, int nc, cudaStream_t s);
+cudaError_t launch_bcount_global(const BArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_extent_stats(const BArgs &a, double *out, int grid, cudaStream_t s);
+cudaError_t launch_join_offsets(const BArgs &a, const unsigned long long *poff, unsigned long long *joff,
+                                cudaStream_t s);
 cudaError_t launch_bscan(const BArgs &a, int nc, cudaStream_t s);
+cudaError_t launch_bscan_blocks_only(const BArgs &a, cudaStream_t s);
 cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, cudaStream_t s);

@@ -30,6 +30,7 @@ struct Workspace {
     Buf bH, bTot, bBoR, bBoS, bItems, bEntR, bEntS, bPc, bPoff, bResv, bFail, bImeta, bIns;
     Buf bFeatRaw, bFeat, bPred, bOrder, bCapTot;   // learned one-pass sizing
     Buf bCur;                                      // shared L1 write cursors
+    Buf bJd, bIjoin, bJfirst, bJoff;               // join table (batches: per-join offsets)
     unsigned long long bcap_r = 0, bcap_s = 0;
     unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
     long long T = 0;
@@ -38,6 +39,7 @@ struct Workspace {
 };
 
 struct MlpState;   // learned per-tile result-count predictor (mlp.cu)
+void batch_release(sj_ctx *ctx);
 
 // Phases of a join, for the device-side timing of sj_timing_*.
 enum Phase {
@@ -116,6 +118,8 @@ int enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, const B
 int blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const float4 *R, long long nR,
                             const float4 *S, long long nS, const GridDev &g, Stats *stats, bool *use_direct);
 int check_opts(sj_ctx *ctx, const sj_opts *o);
+int upload_joins(sj_ctx *ctx, Workspace &w, const JoinDesc *h, int nj);
+int upload_single_join(sj_ctx *ctx, Workspace &w, const BArgs &a);
 
 // misc.cu
 cudaError_t launch_tile_counts(const uint2 *off, long long T, unsigned *cnt_r, unsigned *cnt_s,
@@ -133,6 +137,8 @@ struct PhaseScope {
 };
 
 }  // namespace sj
+
+struct sj_batch_state;
 
 struct sj_ctx {
     int device = 0;
@@ -154,6 +160,9 @@ struct sj_ctx {
     bool mlp_loaded = false;
     const sj_mlp *model = nullptr;      // predictor of SJ_ONE_PASS (not owned)
     void *h_aux = nullptr;              // pinned: one-pass capacity
+    void *h_jd = nullptr;               // pinned: join table staging (kMaxJoins)
+    void *h_joff = nullptr;             // pinned: per-join pair offsets of a batch
+    sj_batch_state *batch = nullptr;    // internal stream and cached graphs of sj_join_batch
     cudaEvent_t ev_aux = nullptr;
     char msg[512];
 };

@@ -103,6 +103,7 @@ SIGNATURES = [
     ("sj_mlp_train_step", I32, [P, P, P, P, I64, ctypes.c_float, P]),
     ("sj_block_features", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), P, P, P, I64, ctypes.POINTER(I64)]),
     ("sj_set_model", I32, [P, P]),
+    ("sj_join_batch", I32, [P, I32, P, P, P, P, P, ctypes.POINTER(sj_opts), P, I64, P]),
     ("sj_join_noalloc", I32, [P, I64, P, I64, ctypes.POINTER(sj_grid), P, I64, ctypes.POINTER(I64), P]),
 ]
 
@@ -458,3 +459,35 @@ def sj_block_features(ctx: Context, R, S, grid: sj_grid, with_blocks: bool = Fal
                                              Y.data_ptr(), B.data_ptr(), m, ctypes.byref(n)))
     k = n.value
     return (X[:k], Y[:k], B[:k]) if with_blocks else (X[:k], Y[:k])
+
+
+def sj_join_batch(ctx: Context, Rs, Ss, grids=None, out: torch.Tensor | None = None):
+    """Join every (Rs[j], Ss[j]) in one batched pass.  Returns (pairs
+    int32[P, 2] device tensor, offsets int64[nj + 1]); the pairs of join j
+    are pairs[offsets[j]:offsets[j+1]] (ids local to the join).  grids:
+    list of sj_grid, or None for the rule-of-thumb grid of every join."""
+    import numpy as np
+    lib = load()
+    nj = len(Rs)
+    if len(Ss) != nj or nj == 0:
+        raise ValueError("Rs and Ss must be non-empty lists of the same length")
+    pr = (ctypes.c_void_p * nj)()
+    ps = (ctypes.c_void_p * nj)()
+    nr = (ctypes.c_int64 * nj)()
+    ns = (ctypes.c_int64 * nj)()
+    for j in range(nj):
+        pr[j], nr[j] = _rects(Rs[j], ctx.device)
+        ps[j], ns[j] = _rects(Ss[j], ctx.device)
+    g = None
+    if grids is not None:
+        g = (sj_grid * nj)(*grids)
+    offs = np.zeros(nj + 1, np.int64)
+    buf = out if out is not None else torch.empty((0, 2), dtype=torch.int32, device=ctx.device)
+    st = lib.sj_join_batch(ctx.handle, nj, pr, nr, ps, ns, g, None, buf.data_ptr() if buf.numel() else None,
+                           buf.shape[0], offs.ctypes.data)
+    if st == SJ_EOVERFLOW and out is None:
+        buf = torch.empty((int(offs[-1]), 2), dtype=torch.int32, device=ctx.device)
+        st = lib.sj_join_batch(ctx.handle, nj, pr, nr, ps, ns, g, None, buf.data_ptr(), buf.shape[0],
+                               offs.ctypes.data)
+    _check(ctx.handle, st)
+    return buf[: int(offs[-1])], offs

@@ -1,0 +1,70 @@
+"""Batched joins (sj_join_batch): every join of the batch against the
+oracle, uneven sizes, explicit and rule-of-thumb grids, repeated calls that
+replay the captured graphs, a too-small output buffer."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1908_11740_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sj():
+    from paper_1908_11740_gb300 import build, sj as binding
+
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(sj):
+    c = sj.sj_create(0)
+    yield c
+    sj.sj_destroy(c)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def srt(a):
+    a = np.asarray(a, np.int32).reshape(-1, 2)
+    return a[np.lexsort((a[:, 1], a[:, 0]))]
+
+
+def _batch():
+    joins = inputs.batch_pairs(n_joins=12, seed0=4000, n_min=50, n_max=30_000, median_extent=2e-3)
+    joins.append(inputs.degenerate_pair(300, 200, seed=9))
+    joins.append((np.zeros((0, 4), np.float32), inputs.uniform_pair(10, 10, seed=1)[1]))
+    return joins
+
+
+@pytest.mark.parametrize("grids_kind", ["explicit", "rule"])
+def test_batch_matches_oracle(sj, ctx, grids_kind):
+    joins = _batch()
+    Rs = [dev(r) for r, _ in joins]
+    Ss = [dev(s) for _, s in joins]
+    grids = [sj.make_grid(k) for k in (8, 16, 33, 64, 5, 100, 3, 1, 40, 20, 7, 128, 9, 4)] \
+        if grids_kind == "explicit" else None
+    for rep in range(3):            # the second and third call replay the graphs
+        pairs, offs = sj.sj_join_batch(ctx, Rs, Ss, grids)
+        torch.cuda.synchronize()
+        got = pairs.cpu().numpy()
+        for j, (r, s) in enumerate(joins):
+            want = oracle.brute(r, s) if len(r) * len(s) < 2e7 else oracle.sweep(r, s)
+            np.testing.assert_array_equal(srt(got[offs[j]:offs[j + 1]]), want)
+
+
+def test_batch_overflow_reports_offsets(sj, ctx):
+    joins = _batch()[:4]
+    Rs = [dev(r) for r, _ in joins]
+    Ss = [dev(s) for _, s in joins]
+    small = torch.empty((1, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(sj.SJError) as e:
+        sj.sj_join_batch(ctx, Rs, Ss, None, out=small)
+    assert e.value.status == sj.SJ_EOVERFLOW
+    pairs, offs = sj.sj_join_batch(ctx, Rs, Ss, None)
+    assert offs[-1] == sum(len(oracle.sweep(r, s)) for r, s in joins)
