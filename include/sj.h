@@ -186,6 +186,16 @@ int sj_join_host(sj_ctx *ctx, const sj_rect *h_R, int64_t nR, const sj_rect *h_S
                  const sj_grid *g, const sj_opts *o, sj_pair *h_out, int64_t cap,
                  int64_t *npairs);
 
+/* ---- tuning ------------------------------------------------------------------ */
+/* Sums of the widths and heights of R and S (device inputs; host out[4] =
+ * sum w_R, sum h_R, sum w_S, sum h_S, float64): the statistics behind the
+ * grid rule of Sec. 4.3 (tile extent about ten times the average extent). */
+int sj_extent_stats(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+                    double *out);
+/* Entries per block of the two-level partition (default 1536, >= 64): the
+ * knob the autotuner sets next to the grid. */
+int sj_set_tuning(sj_ctx *ctx, int block_target);
+
 /* ---- batches of independent joins ---------------------------------------- */
 /* nj independent joins (R_j join S_j on grid g[j]) in one pass of the
  * two-level kernels: one count, one scan, one write and one persistent

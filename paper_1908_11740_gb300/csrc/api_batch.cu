@@ -19,6 +19,7 @@ namespace {
 struct GraphCache {
     unsigned long long key = 0;
     cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;   // kernels of this library in the graph
 };
 
 unsigned long long fnv(unsigned long long h, const void *p, size_t n) {
@@ -36,6 +37,8 @@ struct sj_batch_state {
     cudaStream_t gs = nullptr;          // internal stream (capturable)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     GraphCache g1, g2;
+    unsigned long long grid_key = 0;    // inputs of the last rule-of-thumb grids
+    std::vector<sj_grid> grids;
 };
 
 static int batch_state(sj_ctx *ctx, sj_batch_state **out) {
@@ -79,6 +82,7 @@ static int run_graph(sj_ctx *ctx, sj_batch_state *b, GraphCache &gc, unsigned lo
         }
         cudaStream_t user = ctx->stream;
         const bool timer = ctx->timer.on;
+        const long long launches0 = ctx->launches;
         ctx->stream = b->gs;
         ctx->timer.on = false;   // no timing events inside a captured graph
         if ((e = cudaStreamBeginCapture(b->gs, cudaStreamCaptureModeThreadLocal))) {
@@ -91,6 +95,8 @@ static int run_graph(sj_ctx *ctx, sj_batch_state *b, GraphCache &gc, unsigned lo
         e = cudaStreamEndCapture(b->gs, &graph);
         ctx->stream = user;
         ctx->timer.on = timer;
+        gc.kernels = ctx->launches - launches0;
+        ctx->launches = launches0;   // counted when the graph runs
         if (st) {
             if (graph) cudaGraphDestroy(graph);
             return st;
@@ -104,6 +110,7 @@ static int run_graph(sj_ctx *ctx, sj_batch_state *b, GraphCache &gc, unsigned lo
         }
         gc.key = key;
     }
+    ctx->launches += gc.kernels;
     // order after the caller's stream, run, and make the caller's stream wait
     if ((e = cudaEventRecord(b->ev_in, ctx->stream)) || (e = cudaStreamWaitEvent(b->gs, b->ev_in, 0)) ||
         (e = cudaGraphLaunch(gc.exec, b->gs)) || (e = cudaEventRecord(b->ev_out, b->gs)) ||
@@ -177,8 +184,19 @@ extern "C" int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, con
     }
     if (g_in) {
         for (int j = 0; j < nj; j++) grids[j] = g_in[j];
-    } else if ((st = rule_grids(ctx, w, jd, grids))) {
-        return st;
+    } else {
+        // the rule needs a pass over the inputs; the grids of the previous
+        // call are reused when it joined the same buffers and sizes (the
+        // grid only shapes the partitioning, never the result)
+        unsigned long long gk = 1469598103934665603ull;
+        gk = fnv(gk, jd.data(), sizeof(JoinDesc) * nj);
+        if (bs->grid_key == gk && (int)bs->grids.size() == nj) {
+            grids = bs->grids;
+        } else {
+            if ((st = rule_grids(ctx, w, jd, grids))) return st;
+            bs->grid_key = gk;
+            bs->grids = grids;
+        }
     }
     int nbt = 0;
     for (int j = 0; j < nj; j++) {
@@ -334,4 +352,44 @@ extern "C" int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, con
         });
     }
     return fail(ctx, SJ_EINTERNAL, "batch workspace did not converge");
+}
+
+extern "C" int sj_extent_stats(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+                               double *out) {
+    if (!ctx || !out) return SJ_EINVAL;
+    if (nR < 0 || nS < 0 || (nR && !d_R) || (nS && !d_S)) return fail(ctx, SJ_EINVAL, "bad inputs");
+    DeviceGuard dg(ctx->device);
+    std::vector<JoinDesc> jd(1);
+    memset(jd.data(), 0, sizeof(JoinDesc));
+    jd[0].R = (const float4 *)d_R;
+    jd[0].S = (const float4 *)d_S;
+    jd[0].nR = nR;
+    jd[0].nS = nS;
+    std::vector<sj_grid> g(1);
+    Workspace &w = ctx->ws;
+    int st = ensure(ctx, w.bJoff, 64);
+    if (st) return st;
+    // reuse the grid rule's reduction and read back its sums
+    if ((st = upload_joins(ctx, w, jd.data(), 1))) return st;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.bJoff.p, 0, 32, ctx->stream))) return cuda_fail(ctx, e, "memset");
+    BArgs a;
+    memset(&a, 0, sizeof a);
+    a.jd = (const JoinDesc *)w.bJd.p;
+    a.nj = 1;
+    {
+        PhaseScope ph(ctx, PH_OTHER, 1);
+        if ((e = launch_extent_stats(a, (double *)w.bJoff.p, ctx->num_sms * 8, ctx->stream)))
+            return cuda_fail(ctx, e, "extent statistics");
+    }
+    if ((e = cudaMemcpyAsync(out, w.bJoff.p, 32, cudaMemcpyDeviceToHost, ctx->stream)) ||
+        (e = cudaStreamSynchronize(ctx->stream)))
+        return cuda_fail(ctx, e, "copy");
+    return SJ_OK;
+}
+
+extern "C" int sj_set_tuning(sj_ctx *ctx, int block_target) {
+    if (!ctx || block_target < 64) return SJ_EINVAL;
+    ctx->block_target = block_target;
+    return SJ_OK;
 }

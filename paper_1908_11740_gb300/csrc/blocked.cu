@@ -931,22 +931,43 @@ __global__ void __launch_bounds__(256) k_bfeat_sample(BArgs a) {
 }
 
 // Sums of widths and heights of every join's rectangles (for the grid rule),
-// out[4 j + 0..3] = sum w_R, sum h_R, sum w_S, sum h_S (float64).
+// out[4 j + 0..3] = sum w_R, sum h_R, sum w_S, sum h_S (float64).  Every
+// lane walks a contiguous run of rectangles, accumulates in registers and
+// adds to the totals only when its run crosses into another join or side.
 __global__ void __launch_bounds__(256) k_extent_stats(BArgs a, double *__restrict__ out) {
     extern __shared__ long long s_jin[];
     for (int j = threadIdx.x; j < a.nj; j += 256) s_jin[j] = a.jd[j].in_off;
     if (threadIdx.x == 0) s_jin[a.nj] = a.jd[a.nj - 1].in_off + a.jd[a.nj - 1].nR + a.jd[a.nj - 1].nS;
     __syncthreads();
     const long long n = s_jin[a.nj];
-    for (long long i = blockIdx.x * 256ll + threadIdx.x; i < n; i += 256ll * gridDim.x) {
+    const long long nthreads = (long long)gridDim.x * 256;
+    const long long per = (n + nthreads - 1) / nthreads;
+    const long long i0 = ((long long)blockIdx.x * 256 + threadIdx.x) * per;
+    const long long i1 = min(n, i0 + per);
+    int cur = -1;
+    double sw = 0.0, sh = 0.0;
+    for (long long i = i0; i < i1; i++) {
         const int j = a.nj == 1 ? 0 : join_of(s_jin, a.nj, i);
         const JoinDesc &d = a.jd[j];
         const long long li = i - s_jin[j];
         const int side = li >= d.nR;
+        const int key = 2 * j + side;
+        if (key != cur) {
+            if (cur >= 0 && (sw != 0.0 || sh != 0.0)) {
+                atomicAdd(out + 2 * cur, sw);
+                atomicAdd(out + 2 * cur + 1, sh);
+            }
+            cur = key;
+            sw = sh = 0.0;
+        }
         const float4 v = ld_stream(side ? d.S + (li - d.nR) : d.R + li);
         if (!rect_ok(v)) continue;
-        atomicAdd(out + 4 * j + 2 * side, (double)(v.z - v.x));
-        atomicAdd(out + 4 * j + 2 * side + 1, (double)(v.w - v.y));
+        sw += (double)(v.z - v.x);
+        sh += (double)(v.w - v.y);
+    }
+    if (cur >= 0 && (sw != 0.0 || sh != 0.0)) {
+        atomicAdd(out + 2 * cur, sw);
+        atomicAdd(out + 2 * cur + 1, sh);
     }
 }
 

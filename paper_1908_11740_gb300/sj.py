@@ -103,6 +103,8 @@ SIGNATURES = [
     ("sj_mlp_train_step", I32, [P, P, P, P, I64, ctypes.c_float, P]),
     ("sj_block_features", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), P, P, P, I64, ctypes.POINTER(I64)]),
     ("sj_set_model", I32, [P, P]),
+    ("sj_extent_stats", I32, [P, P, I64, P, I64, P]),
+    ("sj_set_tuning", I32, [P, I32]),
     ("sj_join_batch", I32, [P, I32, P, P, P, P, P, ctypes.POINTER(sj_opts), P, I64, P]),
     ("sj_join_noalloc", I32, [P, I64, P, I64, ctypes.POINTER(sj_grid), P, I64, ctypes.POINTER(I64), P]),
 ]
@@ -491,3 +493,17 @@ def sj_join_batch(ctx: Context, Rs, Ss, grids=None, out: torch.Tensor | None = N
                                offs.ctypes.data)
     _check(ctx.handle, st)
     return buf[: int(offs[-1])], offs
+
+
+def sj_extent_stats(ctx: Context, R, S):
+    """(sum w_R, sum h_R, sum w_S, sum h_S) of device rectangles."""
+    import numpy as np
+    pr, nr = _rects(R, ctx.device)
+    ps, ns = _rects(S, ctx.device)
+    out = np.zeros(4, np.float64)
+    _check(ctx.handle, load().sj_extent_stats(ctx.handle, pr, nr, ps, ns, out.ctypes.data))
+    return out
+
+
+def sj_set_tuning(ctx: Context, block_target: int) -> None:
+    _check(ctx.handle, load().sj_set_tuning(ctx.handle, int(block_target)))
