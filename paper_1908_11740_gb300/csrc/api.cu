@@ -97,7 +97,7 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
                   &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out, &w.bH,
                   &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
                   &w.bResv, &w.bFail, &w.bImeta, &w.bIns, &w.bFeatRaw, &w.bFeat, &w.bPred,
-                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff};
+                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff};
     for (Buf *b : all) {
         dev_free(ctx, b->p);
         b->p = nullptr;
@@ -623,6 +623,7 @@ int sj::size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p) {
     if ((st = ensure(ctx, w.bResv, 8ull * (p.nb + 1)))) return st;
     if ((st = ensure(ctx, w.bFail, 4ull * (p.nb + 1)))) return st;
     if ((st = ensure(ctx, w.bCur, 8ull * (p.nb + 1)))) return st;
+    if ((st = ensure(ctx, w.bList, 4ull * list_pool_cap(w)))) return st;
     if ((st = ensure(ctx, w.bJd, sizeof(JoinDesc) * 2))) return st;
     return SJ_OK;
 }
@@ -653,6 +654,8 @@ BArgs sj::blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long 
     a.cap_r = w.bcap_r;
     a.cap_s = w.bcap_s;
     a.cur = nullptr;
+    a.lpool = (unsigned *)w.bList.p;
+    a.lpool_cap = list_pool_cap(w);
     a.jd = (const JoinDesc *)w.bJd.p;   // filled by enqueue_blocked_partition
     a.nj = 1;
     a.nbt = p.nb;

@@ -250,6 +250,8 @@ extern "C" int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, con
         a.cap_r = w.bcap_r;
         a.cap_s = w.bcap_s;
         a.cur = (unsigned *)w.bCur.p;
+        a.lpool = (unsigned *)w.bList.p;
+        a.lpool_cap = list_pool_cap(w);
         a.st = (Stats *)w.stats.p;
         // the arguments that shape the captured work
         unsigned long long key = 1469598103934665603ull;

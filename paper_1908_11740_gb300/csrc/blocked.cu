@@ -377,11 +377,25 @@ __global__ void __launch_bounds__(256) k_bcount_global(BArgs a) {
 struct BJSmem {
     unsigned cnt[2][kMaxFine];       // entries per tile of the block
     unsigned off[2][kMaxFine + 1];   // band offsets; after the scatter: segment ends
-    unsigned key[kFineCap];          // x_l keys
-    float4 mbr[kFineCap];            // the band's entries, sorted by x_l inside every tile segment
+    unsigned key[kFineCap];          // x_l keys; after the ranking: positions in x_l order per segment
+    float4 mbr[kFineCap];            // the band's entries, grouped by tile segment
     unsigned id[kFineCap];
     unsigned short tile[kFineCap];   // band-local tile of each position
     unsigned short band[kMaxFine + 2];
+    int2 pbuf[kPairBuf];             // one-pass: the block's pairs before its reservation
+};
+
+// Per-row entry lists of a block staged in several bands: entry e (R: e <
+// nr1, S: e - nr1) appears in the list of every tile row it covers.  Row y
+// has room for the sum of its tile counts (an upper bound on the entries
+// covering it), at off[y] of the block's pool slice; pre[] is the exclusive
+// prefix of the rows' actual lengths.
+struct RowLists {
+    unsigned off[kMaxG + 1];
+    unsigned pre[kMaxG + 1];
+    unsigned cur[kMaxG];
+    unsigned *pool;
+    int on;
 };
 
 // ---- TMA bulk copies into shared memory (mbarrier completion) --------------
@@ -429,10 +443,41 @@ struct BlockCtx {
     const BEnt *er, *es;   // the block's R and S entries (shared-memory copy or global)
 };
 
+// Write entry e of the block into every tile of [ta, tb) it overlaps (rows
+// row_a..row_b of the block).  With row >= 0 the entry comes from the list
+// of that row and is taken only there if it is its first row in the band.
+__device__ __forceinline__ void stage_entry(BJSmem &sm, const BlockCtx &bc, int e, int ta, int tb, int row_a,
+                                            int row_b, int row) {
+    const int side = e >= (int)bc.nr1;
+    const uint4 *p = reinterpret_cast<const uint4 *>(side ? bc.es + (e - bc.nr1) : bc.er + e);
+    const uint4 t = p[1];
+    const uint4 hd = p[0];
+    const int cx0 = t.y & 0xffff, cx1 = t.y >> 16, cy0 = t.z & 0xffff, cy1 = t.z >> 16;
+    const int ly0 = max(cy0 - bc.cyb, row_a), ly1 = min(cy1 - bc.cyb, row_b);
+    if (ly0 > ly1 || (row >= 0 && ly0 != row)) return;
+    const int lx0 = max(cx0 - bc.cxb, 0), lx1 = min(cx1 - bc.cxb, bc.gw - 1);
+    const float4 mb = make_float4(__uint_as_float(hd.x), __uint_as_float(hd.y), __uint_as_float(hd.z),
+                                  __uint_as_float(hd.w));
+    const unsigned k = xkey(mb.x);
+    for (int ly = ly0; ly <= ly1; ly++)
+        for (int lx = lx0; lx <= lx1; lx++) {
+            const int lt = ly * bc.gw + lx;
+            if (lt < ta || lt >= tb) continue;
+            const int j = lt - ta;
+            const unsigned pos = atomicAdd(&sm.off[side][j], 1u);
+            const unsigned flags = (lx + bc.cxb == cx0 ? kFlagCol : 0u) | (ly + bc.cyb == cy0 ? kFlagRow : 0u);
+            sm.key[pos] = k;
+            sm.mbr[pos] = mb;
+            sm.id[pos] = t.x | flags;
+            sm.tile[pos] = (unsigned short)j;
+        }
+}
+
 // Steps of one band [ta, tb): offsets, scatter into the tile segments,
-// ranks -> sorted entries.  Returns nothing; results live in sm.
-__device__ __forceinline__ void band_stage(BJSmem &sm, const BlockCtx &bc, int ta, int tb, int &nRb,
-                                           int &nSb) {
+// ranks -> sorted entries.  Entries come from the row lists when rl is
+// given, else from the block's whole L1 range.  Results live in sm.
+__device__ __forceinline__ void band_stage(BJSmem &sm, const BlockCtx &bc, int ta, int tb, int &nRb, int &nSb,
+                                           const RowLists *rl) {
     const int NT = kBJThreads;
     const int nt = tb - ta;
     // packed exclusive scan of (R count | S count << 32) over the band's tiles
@@ -480,40 +525,29 @@ __device__ __forceinline__ void band_stage(BJSmem &sm, const BlockCtx &bc, int t
     __syncthreads();
     // scatter the block's entries into the band's tile segments
     const int row_a = ta / bc.gw, row_b = (tb - 1) / bc.gw;
-    const int n1 = (int)(bc.nr1 + bc.ns1);
-    for (int e = threadIdx.x; e < n1; e += NT) {
-        const int side = e >= (int)bc.nr1;
-        const uint4 *p = reinterpret_cast<const uint4 *>(side ? bc.es + (e - bc.nr1) : bc.er + e);
-        const uint4 t = p[1];
-        const uint4 hd = p[0];
-        const int cx0 = t.y & 0xffff, cx1 = t.y >> 16, cy0 = t.z & 0xffff, cy1 = t.z >> 16;
-        const int ly0 = max(cy0 - bc.cyb, row_a), ly1 = min(cy1 - bc.cyb, row_b);
-        if (ly0 > ly1) continue;
-        const int lx0 = max(cx0 - bc.cxb, 0), lx1 = min(cx1 - bc.cxb, bc.gw - 1);
-        const float4 mb = make_float4(__uint_as_float(hd.x), __uint_as_float(hd.y), __uint_as_float(hd.z),
-                                      __uint_as_float(hd.w));
-        const unsigned k = xkey(mb.x);
-        for (int ly = ly0; ly <= ly1; ly++)
-            for (int lx = lx0; lx <= lx1; lx++) {
-                const int lt = ly * bc.gw + lx;
-                if (lt < ta || lt >= tb) continue;
-                const int j = lt - ta;
-                const unsigned pos = atomicAdd(&sm.off[side][j], 1u);
-                const unsigned flags = (lx + bc.cxb == cx0 ? kFlagCol : 0u) | (ly + bc.cyb == cy0 ? kFlagRow : 0u);
-                sm.key[pos] = k;
-                sm.mbr[pos] = mb;
-                sm.id[pos] = t.x | flags;
-                sm.tile[pos] = (unsigned short)j;
+    if (rl) {
+        const unsigned i0 = rl->pre[row_a], i1 = rl->pre[row_b + 1];
+        for (unsigned i = i0 + threadIdx.x; i < i1; i += NT) {
+            int lo = row_a, hi = row_b;   // the row holding item i: last y with pre[y] <= i
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (rl->pre[mid] <= i) lo = mid;
+                else hi = mid - 1;
             }
+            stage_entry(sm, bc, (int)rl->pool[rl->off[lo] + (i - rl->pre[lo])], ta, tb, row_a, row_b, lo);
+        }
+    } else {
+        const int n1 = (int)(bc.nr1 + bc.ns1);
+        for (int e = threadIdx.x; e < n1; e += NT) stage_entry(sm, bc, e, ta, tb, row_a, row_b, -1);
     }
     __syncthreads();
-    // sort every tile segment by x_l in place: rank of each position among
-    // its segment (ties by position), then move through registers
+    // sort every tile segment by x_l: the rank of each position among its
+    // segment (ties by position) gives key[segment start + rank] = position,
+    // i.e. after this step key[] holds the x_l order of every segment and
+    // the entries themselves stay where the scatter put them
     const int nb = nRb + nSb;
     constexpr int KP = kFineCap / kBJThreads;
     int dst[KP];
-    float4 vm[KP];
-    unsigned vi[KP];
 #pragma unroll
     for (int q = 0; q < KP; q++) {
         const int pidx = threadIdx.x + q * NT;
@@ -530,21 +564,17 @@ __device__ __forceinline__ void band_stage(BJSmem &sm, const BlockCtx &bc, int t
                 r += (kq < k0) | ((kq == k0) & (qq < pidx));
             }
             dst[q] = s0 + r;
-            vm[q] = sm.mbr[pidx];
-            vi[q] = sm.id[pidx];
         }
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < KP; q++)
-        if (dst[q] >= 0) {
-            sm.mbr[dst[q]] = vm[q];
-            sm.id[dst[q]] = vi[q];
-        }
+        if (dst[q] >= 0) sm.key[dst[q]] = (unsigned)(threadIdx.x + q * NT);
     __syncthreads();
 }
 
-// Candidate range of pivot p in the other side of its tile.
+// Candidate range of pivot p (any position) in the other side of its tile:
+// ranks k..kend-1 of that segment's x_l order (entry sm.key[k]).
 __device__ __forceinline__ void band_pivot(const BJSmem &sm, int nRb, int p, float4 &pv, unsigned &pid, int &k,
                                            int &kend, bool &isR) {
     isR = p < nRb;
@@ -555,10 +585,10 @@ __device__ __forceinline__ void band_pivot(const BJSmem &sm, int nRb, int p, flo
     int lo = j ? (int)sm.off[o][j - 1] : (o ? nRb : 0);
     int hi = (int)sm.off[o][j];
     kend = hi;
-    // first x_l > pivot.x_l (R pivot) or >= pivot.x_l (S pivot)
+    // first x_l > pivot.x_l (R pivot) or >= pivot.x_l (S pivot), in x_l order
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        const float xm = sm.mbr[mid].x;
+        const float xm = sm.mbr[sm.key[mid]].x;
         const bool right = isR ? (xm > pv.x) : (xm >= pv.x);
         if (right) hi = mid;
         else lo = mid + 1;
@@ -580,9 +610,10 @@ __device__ __forceinline__ unsigned band_count(const BJSmem &sm, const BlockCtx 
         band_pivot(sm, nRb, p, pv, pid, k, kend, isR);
         unsigned c = 0;
         for (; k < kend; k++) {
-            const float4 o = sm.mbr[k];
+            const unsigned q = sm.key[k];
+            const float4 o = sm.mbr[q];
             if (o.x > pv.z) break;
-            if (o.y <= pv.w && pv.y <= o.w && reported_here(pid, sm.id[k])) c++;
+            if (o.y <= pv.w && pv.y <= o.w && reported_here(pid, sm.id[q])) c++;
         }
         if (tile_pairs && c) {
             const int lt = ta + sm.tile[p];
@@ -611,9 +642,11 @@ __device__ __forceinline__ void band_write(const BJSmem &sm, int nRb, int nSb, i
         bool go = active;
         for (;;) {
             float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+            unsigned q = 0;
             bool cand = false;
             if (go && k < kend) {
-                o = sm.mbr[k];
+                q = sm.key[k];
+                o = sm.mbr[q];
                 cand = o.x <= pv.z;
             }
             if (!__any_sync(kFullMask, cand)) break;
@@ -622,7 +655,7 @@ __device__ __forceinline__ void band_write(const BJSmem &sm, int nRb, int nSb, i
             int2 pr = make_int2(0, 0);
             if (cand) {
                 if (o.y <= pv.w && pv.y <= o.w) {
-                    const unsigned oid = sm.id[k];
+                    const unsigned oid = sm.id[q];
                     if (reported_here(pid, oid)) {
                         hit = true;
                         pr = isR ? make_int2((int)(pid & kIdMask), (int)(oid & kIdMask))
@@ -641,6 +674,96 @@ __device__ __forceinline__ void band_write(const BJSmem &sm, int nRb, int nSb, i
             }
         }
     }
+}
+
+// Pairs of the staged band into the block's shared buffer (one-pass join):
+// every hit takes the next slot of *s_pc (warp-aggregated); hits beyond the
+// buffer are only counted.
+__device__ __forceinline__ void band_collect(BJSmem &sm, int nRb, int nSb, unsigned *s_pc) {
+    const int nb = nRb + nSb;
+    if (nRb == 0 || nSb == 0) return;
+    for (int p = threadIdx.x; p < nb; p += kBJThreads) {
+        float4 pv;
+        unsigned pid;
+        int k, kend;
+        bool isR;
+        band_pivot(sm, nRb, p, pv, pid, k, kend, isR);
+        for (; k < kend; k++) {
+            const unsigned q = sm.key[k];
+            const float4 o = sm.mbr[q];
+            if (o.x > pv.z) break;
+            if (o.y <= pv.w && pv.y <= o.w) {
+                const unsigned oid = sm.id[q];
+                if (reported_here(pid, oid)) {
+                    const unsigned m = __activemask();
+                    const int leader = __ffs(m) - 1;
+                    unsigned pos = 0;
+                    if ((int)(threadIdx.x & 31) == leader) pos = atomicAdd(s_pc, (unsigned)__popc(m));
+                    pos = __shfl_sync(m, pos, leader) + __popc(m & lanemask_lt_b());
+                    if (pos < (unsigned)kPairBuf)
+                        sm.pbuf[pos] = isR ? make_int2((int)(pid & kIdMask), (int)(oid & kIdMask))
+                                           : make_int2((int)(oid & kIdMask), (int)(pid & kIdMask));
+                }
+            }
+        }
+    }
+}
+
+// Row lists of a block that needs several bands (see RowLists).  The slice
+// comes from the pool cursor of this launch; rl.on = 0 when the pool is
+// exhausted (the bands then read the whole L1 range).  Ends with a barrier.
+__device__ void build_row_lists(BJSmem &sm, const BlockCtx &bc, RowLists &rl, unsigned *pool,
+                                unsigned long long pool_cap, unsigned long long *cursor) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int y = warp; y < bc.gh; y += kBJThreads / 32) {
+        unsigned c = lane < bc.gw ? sm.cnt[0][y * bc.gw + lane] + sm.cnt[1][y * bc.gw + lane] : 0u;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(kFullMask, c, d);
+        if (lane == 0) rl.pre[y] = c;   // room of row y
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned c = lane < bc.gh ? rl.pre[lane] : 0u;
+        unsigned inc = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned o = __shfl_up_sync(kFullMask, inc, d);
+            if (lane >= d) inc += o;
+        }
+        const unsigned total = __shfl_sync(kFullMask, inc, 31);
+        rl.off[lane] = inc - c;
+        rl.cur[lane] = 0;
+        if (lane == 0) {
+            rl.off[kMaxG] = total;
+            const unsigned long long b = atomicAdd(cursor, (unsigned long long)total);
+            rl.on = b + total <= pool_cap;
+            rl.pool = pool + b;
+        }
+    }
+    __syncthreads();
+    if (!rl.on) return;
+    const int n1 = (int)(bc.nr1 + bc.ns1);
+    for (int e = threadIdx.x; e < n1; e += kBJThreads) {
+        const int side = e >= (int)bc.nr1;
+        const uint4 t = reinterpret_cast<const uint4 *>(side ? bc.es + (e - bc.nr1) : bc.er + e)[1];
+        const int ly0 = max((int)(t.z & 0xffff) - bc.cyb, 0), ly1 = min((int)(t.z >> 16) - bc.cyb, bc.gh - 1);
+        const int lx0 = max((int)(t.y & 0xffff) - bc.cxb, 0), lx1 = min((int)(t.y >> 16) - bc.cxb, bc.gw - 1);
+        if (lx0 > lx1) continue;   // counted in no tile of the block (never for a written entry)
+        for (int y = ly0; y <= ly1; y++) rl.pool[rl.off[y] + atomicAdd(&rl.cur[y], 1u)] = (unsigned)e;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned c = lane < bc.gh ? rl.cur[lane] : 0u;
+        unsigned inc = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned o = __shfl_up_sync(kFullMask, inc, d);
+            if (lane >= d) inc += o;
+        }
+        rl.pre[lane] = inc - c;
+        if (lane == 31) rl.pre[kMaxG] = inc;
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ unsigned block_sum(unsigned v, unsigned *s_red) {
@@ -750,7 +873,8 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BJSmem &sm = *reinterpret_cast<BJSmem *>(smem_raw);
     __shared__ unsigned s_meta[2][12];  // current / next item: item, block, r0, nr, s0, ns, join geometry
-    __shared__ unsigned s_nbands, s_cursor;
+    __shared__ unsigned s_nbands, s_cursor, s_pc;
+    __shared__ RowLists s_rows;
     __shared__ int s_ok, s_huge;
     __shared__ unsigned long long s_base;
     __shared__ unsigned s_red[kBJThreads / 32];
@@ -848,7 +972,10 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
             } else {
                 band_split(sm, bc.ntl, &s_nbands, &s_huge);
             }
-            if (threadIdx.x == 0) s_cursor = 0;
+            if (threadIdx.x == 0) {
+                s_cursor = 0;
+                s_pc = 0;
+            }
         }
         __syncthreads();
         if (s_huge) {   // a single tile exceeds shared memory: the caller reruns on the direct path
@@ -858,11 +985,18 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
             }
         } else {
             const int nbands = (int)s_nbands;
+            // a block staged in several bands first lists its entries per tile
+            // row, so that every band reads only the entries of its rows
+            const RowLists *rl = nullptr;
+            if (nbands > 1 && a.lpool) {
+                build_row_lists(sm, bc, s_rows, a.lpool, a.lpool_cap, &a.st->lpool[o.work_slot & 3]);
+                if (s_rows.on) rl = &s_rows;
+            }
             if (MODE == MODE_WRITE) {
                 const unsigned long long base = o.off_in[it];
                 for (int bi = 0; bi < nbands; bi++) {
                     int nRb, nSb;
-                    band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb);
+                    band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb, rl);
                     band_write(sm, nRb, nSb, o.out, base, &s_cursor);
                     __syncthreads();
                 }
@@ -870,11 +1004,17 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                 unsigned tot = 0;
                 int nRb = 0, nSb = 0;
                 for (int bi = 0; bi < nbands; bi++) {
-                    band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb);
-                    tot += block_sum(band_count(sm, bc, sm.band[bi], nRb, nSb,
-                                                MODE == MODE_TILES ? o.tile_pairs : nullptr, a.g.nx),
-                                     s_red);
+                    band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb, rl);
+                    if (MODE == MODE_RESERVE) {
+                        band_collect(sm, nRb, nSb, &s_pc);
+                        __syncthreads();
+                    } else {
+                        tot += block_sum(band_count(sm, bc, sm.band[bi], nRb, nSb,
+                                                    MODE == MODE_TILES ? o.tile_pairs : nullptr, a.g.nx),
+                                         s_red);
+                    }
                 }
+                if (MODE == MODE_RESERVE) tot = s_pc;
                 if (MODE == MODE_COUNT || MODE == MODE_RESERVE) {
                     if (threadIdx.x == 0) {
                         if (MODE == MODE_COUNT) {
@@ -893,11 +1033,13 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                     }
                     __syncthreads();
                     if (MODE == MODE_RESERVE && s_ok) {
-                        if (nbands == 1) {
+                        if (tot <= (unsigned)kPairBuf) {   // the usual case: copy the collected pairs
+                            for (unsigned i = threadIdx.x; i < tot; i += kBJThreads) o.out[s_base + i] = sm.pbuf[i];
+                        } else if (nbands == 1) {
                             band_write(sm, nRb, nSb, o.out, s_base, &s_cursor);
                         } else {
                             for (int bi = 0; bi < nbands; bi++) {
-                                band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb);
+                                band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb, rl);
                                 band_write(sm, nRb, nSb, o.out, s_base, &s_cursor);
                                 __syncthreads();
                             }

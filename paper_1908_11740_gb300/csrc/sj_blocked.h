@@ -13,6 +13,7 @@ constexpr int kFineCap = 3072;       // tile entries staged in shared memory per
 constexpr int kMaxG = 32;            // tiles per block side
 constexpr int kLoadBatch = 4;        // entries a thread loads before using them
 constexpr int kMaxJoins = 4096;      // joins in one batch
+constexpr int kPairBuf = 1536;       // pairs a one-pass block collects in shared memory
 constexpr int kMaxFine = kMaxG * kMaxG;
 
 // An L1 entry: one aligned 32-byte sector.
@@ -68,6 +69,8 @@ struct BArgs {
     int nbt;                    // blocks of all joins (== nb for a single join)
     unsigned *ijoin;            // join of every work item
     unsigned *jfirst;           // first work item of every join (nj + 1)
+    unsigned *lpool;            // optional: row lists of blocks staged in several bands
+    unsigned long long lpool_cap;
     Stats *st;
 };
 

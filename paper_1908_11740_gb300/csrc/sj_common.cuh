@@ -64,6 +64,7 @@ struct Stats {
     unsigned int nfail;                 // one-pass chunks that did not fit
     unsigned int nfail_large;           // one-pass large-tile blocks that did not fit
     unsigned int work[8];               // work counters of persistent kernels
+    unsigned long long lpool[4];        // blocked path: row-list pool cursor per work slot
     int err;
     int need_direct;                    // blocked path: a tile exceeds shared memory
     int pad;

@@ -30,6 +30,7 @@ struct Workspace {
     Buf bH, bTot, bBoR, bBoS, bItems, bEntR, bEntS, bPc, bPoff, bResv, bFail, bImeta, bIns;
     Buf bFeatRaw, bFeat, bPred, bOrder, bCapTot;   // learned one-pass sizing
     Buf bCur;                                      // shared L1 write cursors
+    Buf bList;                                     // row lists of multi-band blocks
     Buf bJd, bIjoin, bJfirst, bJoff;               // join table (batches: per-join offsets)
     unsigned long long bcap_r = 0, bcap_s = 0;
     unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
@@ -111,6 +112,9 @@ int out_acquire(sj_ctx *ctx, Workspace &w, OutSpec &os, unsigned long long P);
 void out_abandon(sj_ctx *ctx, OutSpec &os);
 bool plan_blocked(sj_ctx *ctx, const GridDev &g, long long nR, long long nS, BPlan &p);
 int size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p);
+// Entries of the row-list pool: 5/4 of the L1 capacity (a block that finds
+// the pool exhausted stages its bands from the whole L1 range instead).
+inline unsigned long long list_pool_cap(const Workspace &w) { return (w.bcap_r + w.bcap_s) * 5 / 4 + 1024; }
 BArgs blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long nR, const float4 *S, long long nS,
                    const GridDev &g);
 BJoinOut bjoin_out(Workspace &w, int slot);

@@ -22,6 +22,8 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--mode", default="two_pass")
     ap.add_argument("--rho", type=float, default=0.0)
+    ap.add_argument("--model", default=None,
+                    help="trained predictor (.npz) for --mode one_pass/auto; default: the packaged one")
     a = ap.parse_args(argv)
 
     import torch
@@ -37,7 +39,12 @@ def main(argv=None):
         R, S = inputs.uniform_pair(int(10_000_000 * a.scale), int(10_000_000 * a.scale), seed=1)
     dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
     ctx = sj.sj_create(0)
+    model = None
     try:
+        if a.mode in ("one_pass", "auto"):
+            from . import learn
+            model, _ = learn.load(ctx, a.model or learn.DEFAULT_MODEL)
+            sj.sj_set_model(ctx, model)
         g = sj.make_grid(a.grid)
         opts = sj.make_opts(a.mode)
         n = 0
@@ -50,6 +57,9 @@ def main(argv=None):
         print(json.dumps({"pairs": n, "stats": sj.sj_last_stats(ctx),
                           "phases_ms": {k: v[1] for k, v in t.items() if k != "launches" and v[0]}}))
     finally:
+        if model is not None:
+            sj.sj_set_model(ctx, None)
+            model.free()
         sj.sj_destroy(ctx)
 
 
