@@ -97,7 +97,7 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
                   &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out, &w.bH,
                   &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
                   &w.bResv, &w.bFail, &w.bImeta, &w.bIns, &w.bFeatRaw, &w.bFeat, &w.bPred,
-                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff};
+                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bSpill, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff};
     for (Buf *b : all) {
         dev_free(ctx, b->p);
         b->p = nullptr;
@@ -624,6 +624,7 @@ int sj::size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p) {
     if ((st = ensure(ctx, w.bFail, 4ull * (p.nb + 1)))) return st;
     if ((st = ensure(ctx, w.bCur, 8ull * (p.nb + 1)))) return st;
     if ((st = ensure(ctx, w.bList, 4ull * list_pool_cap(w)))) return st;
+    if ((st = ensure(ctx, w.bSpill, 8ull * kPairSpill * ctx->num_sms * ctx->bjoin_bps))) return st;
     if ((st = ensure(ctx, w.bJd, sizeof(JoinDesc) * 2))) return st;
     return SJ_OK;
 }
@@ -672,6 +673,7 @@ BJoinOut sj::bjoin_out(Workspace &w, int slot) {
     o.resv = (unsigned long long *)w.bResv.p;
     o.fail = (unsigned *)w.bFail.p;
     o.nfail = &((Stats *)w.stats.p)->nfail;
+    o.spill = (int2 *)w.bSpill.p;
     return o;
 }
 

@@ -215,7 +215,7 @@ static int size_learned(sj_ctx *ctx, Workspace &w, const BPlan &p) {
     if ((st = ensure(ctx, w.bFeat, 4ull * kFeat * (p.nb + 1)))) return st;
     if ((st = ensure(ctx, w.bPred, 4ull * (p.nb + 1)))) return st;
     if ((st = ensure(ctx, w.bOrder, 4ull * (p.nb + 1)))) return st;
-    if ((st = ensure(ctx, w.bCapTot, 64))) return st;
+    if ((st = ensure(ctx, w.bCapTot, kPlanScratch))) return st;
     return SJ_OK;
 }
 
@@ -336,7 +336,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         }
         unsigned long long *d_cap = (unsigned long long *)w.bCapTot.p;
         {
-            PhaseScope ph(ctx, PH_MODEL, 4);
+            PhaseScope ph(ctx, PH_MODEL, 5);
             if ((e = launch_bfeat_sample(a, ctx->num_sms * 4, s))) return cuda_fail(ctx, e, "sampling");
             if ((e = launch_features((const unsigned *)w.bFeatRaw.p, a.items, a.btot, p.nb, a.st, (float *)w.bFeat.p,
                                      ctx->num_sms * 2, s)))
@@ -350,7 +350,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
             }
             if (e) return cuda_fail(ctx, e, "prediction");
             if ((e = launch_plan((const float *)w.bPred.p, a.imeta, a.ins, a.st, margin, slack, d_cap,
-                                 (unsigned *)w.bOrder.p, s)))
+                                 (unsigned *)w.bOrder.p, ctx->num_sms, s)))
                 return cuda_fail(ctx, e, "plan");
             if ((e = cudaMemcpyAsync(ctx->h_aux, d_cap, 8, cudaMemcpyDeviceToHost, s)) ||
                 (e = cudaEventRecord(ctx->ev_aux, s)))

@@ -49,15 +49,16 @@ __global__ void __launch_bounds__(kL1Threads) k_bcount(BArgs a) {
     const long long q = (n + gridDim.x - 1) / gridDim.x;
     const long long i0 = (long long)blockIdx.x * q, i1 = min(n, i0 + q);
     int bad = 0;
-    for (long long base = i0 + threadIdx.x; base < i1; base += 4ll * kL1Threads) {
-        float4 m[4];
+    constexpr int U = 8;   // loads in flight per thread
+    for (long long base = i0 + threadIdx.x; base < i1; base += (long long)U * kL1Threads) {
+        float4 m[U];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < U; u++) {
             const long long i = base + (long long)u * kL1Threads;
             if (i < i1) m[u] = ld_stream(i < a.nR ? a.R + i : a.S + (i - a.nR));
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < U; u++) {
             const long long i = base + (long long)u * kL1Threads;
             if (i >= i1) break;
             if (!rect_ok(m[u])) {
@@ -107,81 +108,116 @@ __global__ void __launch_bounds__(256) k_bscan_ctas(BArgs a, int nc) {
 // totals of each side -> block starts (and the shared write cursors); the
 // work list of blocks that hold both sides, in block order (so the items of
 // each join are consecutive), with their ranges, join and each join's first
-// item; the totals.
+// item; the totals.  One pass over chunks of 8192 blocks: every thread loads
+// 8 consecutive blocks of each side, the chunk is scanned once for the packed
+// (R, S) prefix and once for the work-item count, and a carry links chunks.
+constexpr int kScanPer = 8;
+__device__ __forceinline__ void load8(const unsigned *__restrict__ p, int b, int nb, unsigned (&v)[kScanPer]) {
+    if (b + kScanPer <= nb && ((reinterpret_cast<uintptr_t>(p + b) & 15) == 0)) {
+        const uint4 x = *reinterpret_cast<const uint4 *>(p + b), y = *reinterpret_cast<const uint4 *>(p + b + 4);
+        v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w, v[4] = y.x, v[5] = y.y, v[6] = y.z, v[7] = y.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) v[k] = b + k < nb ? p[b + k] : 0u;
+    }
+}
+
+// Exclusive block scan (1024 threads) of v; *total gets the sum.  Two barriers.
+template <typename T>
+__device__ __forceinline__ T scan1024(T v, T *s_w, T *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T o = __shfl_up_sync(kFullMask, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const T x = s_w[lane];
+        T xi = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T o = __shfl_up_sync(kFullMask, xi, d);
+            if (lane >= d) xi += o;
+        }
+        s_w[lane] = xi - x;
+        if (lane == 31) s_w[32] = xi;
+    }
+    __syncthreads();
+    *total = s_w[32];
+    return s_w[wid] + inc - v;
+}
+
 __global__ void __launch_bounds__(1024) k_bscan_blocks(BArgs a) {
-    __shared__ unsigned long long sh[1024];
+    __shared__ unsigned long long s_w64[33];
+    __shared__ unsigned s_w32[33];
     __shared__ int s_boff[kMaxJoins + 1];
     const int nb = a.nbt;
-    const int per = (nb + 1023) / 1024;
-    const int b0 = threadIdx.x * per;
     for (int j = threadIdx.x; j < a.nj; j += 1024) s_boff[j] = a.jd[j].boff;
-    for (int side = 0; side < 2; side++) {
-        unsigned long long sum = 0;
-        for (int k = 0; k < per; k++)
-            if (b0 + k < nb) sum += a.btot[side * nb + b0 + k];
-        sh[threadIdx.x] = sum;
-        __syncthreads();
-        for (int d = 1; d < 1024; d <<= 1) {
-            const unsigned long long x = threadIdx.x >= (unsigned)d ? sh[threadIdx.x - d] : 0;
-            __syncthreads();
-            sh[threadIdx.x] += x;
-            __syncthreads();
+    __syncthreads();
+    const unsigned *__restrict__ btot = a.btot;
+    unsigned long long carry_r = 0, carry_s = 0;   // entries before this chunk
+    unsigned carry_f = 0;                          // work items before this chunk
+    for (int c0 = 0; c0 < nb; c0 += 1024 * kScanPer) {
+        const int b0 = c0 + threadIdx.x * kScanPer;
+        unsigned vr[kScanPer], vs[kScanPer];
+        load8(btot, b0, nb, vr);
+        load8(btot + nb, b0, nb, vs);
+        unsigned long long sr = 0, ss = 0;
+        unsigned sf = 0;
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) {
+            sr += vr[k];
+            ss += vs[k];
+            sf += (vr[k] > 0 && vs[k] > 0);
         }
-        unsigned long long run = sh[threadIdx.x] - sum;
-        unsigned *bo = side ? a.bo_s : a.bo_r;
-        for (int k = 0; k < per; k++)
-            if (b0 + k < nb) {
-                bo[b0 + k] = (unsigned)run;
-                if (a.cur) a.cur[side * nb + b0 + k] = (unsigned)run;
-                run += a.btot[side * nb + b0 + k];
+        unsigned long long tr, ts;
+        unsigned tf;
+        unsigned long long pr = carry_r + scan1024(sr, s_w64, &tr);
+        unsigned long long ps = carry_s + scan1024(ss, s_w64, &ts);
+        unsigned idx = carry_f + scan1024(sf, s_w32, &tf);
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) {
+            const int b = b0 + k;
+            if (b >= nb) break;
+            a.bo_r[b] = (unsigned)pr;
+            a.bo_s[b] = (unsigned)ps;
+            if (a.cur) {
+                a.cur[b] = (unsigned)pr;
+                a.cur[nb + b] = (unsigned)ps;
             }
-        if (threadIdx.x == 1023) {
-            bo[nb] = (unsigned)sh[1023];
-            if (side) a.st->e_s = sh[1023];
-            else a.st->e_r = sh[1023];
-            const unsigned long long cap = side ? a.cap_s : a.cap_r;
-            if (sh[1023] > cap) atomicOr(&a.st->err, kErrEntCap);
+            // join of block b: the last join whose first block is <= b
+            int lo = 0, hi = a.nj;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_boff[mid] <= b) lo = mid;
+                else hi = mid;
+            }
+            if (a.jfirst && s_boff[lo] == b) a.jfirst[lo] = idx;
+            if (vr[k] > 0 && vs[k] > 0) {
+                a.items[idx] = (unsigned)b;
+                a.imeta[idx] = make_uint4((unsigned)b, (unsigned)pr, vr[k], (unsigned)ps);
+                a.ins[idx] = vs[k];
+                if (a.ijoin) a.ijoin[idx] = (unsigned)lo;
+                idx++;
+            }
+            pr += vr[k];
+            ps += vs[k];
         }
-        __syncthreads();
+        carry_r += tr;
+        carry_s += ts;
+        carry_f += tf;
     }
-    // work list in block order: exclusive scan of the "both sides" flags
-    unsigned cntf = 0;
-    for (int k = 0; k < per; k++) {
-        const int b = b0 + k;
-        cntf += (b < nb && a.btot[b] > 0 && a.btot[nb + b] > 0);
-    }
-    sh[threadIdx.x] = cntf;
-    __syncthreads();
-    for (int d = 1; d < 1024; d <<= 1) {
-        const unsigned long long x = threadIdx.x >= (unsigned)d ? sh[threadIdx.x - d] : 0;
-        __syncthreads();
-        sh[threadIdx.x] += x;
-        __syncthreads();
-    }
-    unsigned idx = (unsigned)(sh[threadIdx.x] - cntf);
-    for (int k = 0; k < per; k++) {
-        const int b = b0 + k;
-        if (b >= nb) break;
-        // join of block b: the last join whose first block is <= b
-        int lo = 0, hi = a.nj;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_boff[mid] <= b) lo = mid;
-            else hi = mid;
-        }
-        if (a.jfirst && s_boff[lo] == b) a.jfirst[lo] = idx;
-        if (a.btot[b] > 0 && a.btot[nb + b] > 0) {
-            a.items[idx] = (unsigned)b;
-            a.imeta[idx] = make_uint4((unsigned)b, a.bo_r[b], a.btot[b], a.bo_s[b]);
-            a.ins[idx] = a.btot[nb + b];
-            if (a.ijoin) a.ijoin[idx] = (unsigned)lo;
-            idx++;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 1023) {
-        a.st->nchunks = (unsigned)sh[1023];
-        if (a.jfirst) a.jfirst[a.nj] = (unsigned)sh[1023];
+    if (threadIdx.x == 0) {
+        a.bo_r[nb] = (unsigned)carry_r;
+        a.bo_s[nb] = (unsigned)carry_s;
+        a.st->e_r = carry_r;
+        a.st->e_s = carry_s;
+        if (carry_r > a.cap_r || carry_s > a.cap_s) atomicOr(&a.st->err, kErrEntCap);
+        a.st->nchunks = carry_f;
+        if (a.jfirst) a.jfirst[a.nj] = carry_f;
     }
 }
 
@@ -269,6 +305,11 @@ __device__ __forceinline__ int div_gj(int x, const JoinDesc &d) {
     return d.G == 1 ? x : (int)__umulhi((unsigned)x, d.gmul);
 }
 
+// Every thread takes kScatterU rectangles per step in phases: all loads,
+// then cells and block keys, then the warp-aggregated cursor atomics of
+// the first blocks, then the stores, so that the DRAM loads and the L2
+// atomic round trips of the kScatterU rectangles overlap.
+constexpr int kScatterU = 4;
 __global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
     extern __shared__ long long s_jin[];   // nj + 1
     if (block_skip(a.st)) return;
@@ -277,52 +318,66 @@ __global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
     __syncthreads();
     const long long n = s_jin[a.nj];
     const unsigned lane = threadIdx.x & 31;
-    for (long long base = blockIdx.x * 256ll * 4 + threadIdx.x; base - threadIdx.x < n;
-         base += 256ll * 4 * gridDim.x) {
+    for (long long base = blockIdx.x * 256ll * kScatterU + threadIdx.x; base - threadIdx.x < n;
+         base += 256ll * kScatterU * gridDim.x) {
+        float4 v[kScatterU];
+        int jj[kScatterU];
+        unsigned idx[kScatterU];   // index in its side | side << 31
+        bool ok[kScatterU];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < kScatterU; u++) {   // loads
             const long long i = base + u * 256;
-            bool valid = i < n;
-            const int j = valid ? (a.nj == 1 ? 0 : join_of(s_jin, a.nj, i)) : 0;
-            const JoinDesc &d = a.jd[j];
-            const long long li = i - s_jin[j];
+            ok[u] = i < n;
+            jj[u] = ok[u] ? (a.nj == 1 ? 0 : join_of(s_jin, a.nj, i)) : 0;
+            const JoinDesc &d = a.jd[jj[u]];
+            const long long li = i - s_jin[jj[u]];
             const int side = li >= d.nR;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (valid) v = ld_stream(side ? d.S + (li - d.nR) : d.R + li);
-            if (valid && !rect_ok(v)) valid = false;
-            v.x = __fadd_rn(v.x, 0.0f);
-            v.y = __fadd_rn(v.y, 0.0f);
-            v.z = __fadd_rn(v.z, 0.0f);
-            v.w = __fadd_rn(v.w, 0.0f);
-            const unsigned id = (unsigned)(side ? li - d.nR : li);
-            int cx0 = 0, cx1 = -1, cy0 = 0, cy1 = -1;
-            if (valid) {
-                cx0 = cell_of(v.x, d.g.x0, d.g.gx, d.g.nx);
-                cx1 = cell_of(v.z, d.g.x0, d.g.gx, d.g.nx);
-                cy0 = cell_of(v.y, d.g.y0, d.g.gy, d.g.ny);
-                cy1 = cell_of(v.w, d.g.y0, d.g.gy, d.g.ny);
+            idx[u] = (unsigned)(side ? li - d.nR : li) | ((unsigned)side << 31);
+            v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok[u]) v[u] = ld_stream(side ? d.S + (li - d.nR) : d.R + li);
+        }
+        unsigned cxp[kScatterU], cyp[kScatterU], key[kScatterU], pos0[kScatterU], peers[kScatterU];
+#pragma unroll
+        for (int u = 0; u < kScatterU; u++) {   // cells, first block, cursor atomic
+            const JoinDesc &d = a.jd[jj[u]];
+            if (ok[u] && !rect_ok(v[u])) ok[u] = false;
+            v[u].x = __fadd_rn(v[u].x, 0.0f);
+            v[u].y = __fadd_rn(v[u].y, 0.0f);
+            v[u].z = __fadd_rn(v[u].z, 0.0f);
+            v[u].w = __fadd_rn(v[u].w, 0.0f);
+            int cx0 = 0, cx1 = 0, cy0 = 0, cy1 = 0;
+            if (ok[u]) {
+                cx0 = cell_of(v[u].x, d.g.x0, d.g.gx, d.g.nx);
+                cx1 = cell_of(v[u].z, d.g.x0, d.g.gx, d.g.nx);
+                cy0 = cell_of(v[u].y, d.g.y0, d.g.gy, d.g.ny);
+                cy1 = cell_of(v[u].w, d.g.y0, d.g.gy, d.g.ny);
             }
-            const uint4 head = make_uint4(__float_as_uint(v.x), __float_as_uint(v.y), __float_as_uint(v.z),
-                                          __float_as_uint(v.w));
-            const uint4 tail = make_uint4(id, (unsigned)cx0 | ((unsigned)cx1 << 16),
-                                          (unsigned)cy0 | ((unsigned)cy1 << 16), 0u);
+            cxp[u] = (unsigned)cx0 | ((unsigned)cx1 << 16);
+            cyp[u] = (unsigned)cy0 | ((unsigned)cy1 << 16);
+            const unsigned cb = (idx[u] >> 31) * (unsigned)a.nbt + (unsigned)d.boff;
+            key[u] = ok[u] ? cb + (unsigned)(div_gj(cy0, d) * d.bx + div_gj(cx0, d)) : 0xffffffffu;
+            peers[u] = __match_any_sync(0xffffffffu, key[u]);
+            pos0[u] = 0;
+            if (ok[u] && (int)lane == __ffs(peers[u]) - 1) pos0[u] = atomicAdd(a.cur + key[u], (unsigned)__popc(peers[u]));
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterU; u++) {   // slots, stores (further blocks: one atomic each)
+            pos0[u] = __shfl_sync(0xffffffffu, pos0[u], __ffs(peers[u]) - 1) + __popc(peers[u] & ((1u << lane) - 1u));
+            if (!ok[u]) continue;
+            const JoinDesc &d = a.jd[jj[u]];
+            const int side = idx[u] >> 31;
+            const int cx0 = cxp[u] & 0xffff, cx1 = cxp[u] >> 16, cy0 = cyp[u] & 0xffff, cy1 = cyp[u] >> 16;
+            const uint4 head = make_uint4(__float_as_uint(v[u].x), __float_as_uint(v[u].y), __float_as_uint(v[u].z),
+                                          __float_as_uint(v[u].w));
+            const uint4 tail = make_uint4(idx[u] & 0x7fffffffu, cxp[u], cyp[u], 0u);
             BEnt *dst = side ? a.bent_s : a.bent_r;
             const unsigned long long cap = side ? a.cap_s : a.cap_r;
-            const int bx0 = valid ? div_gj(cx0, d) : 0, bx1 = valid ? div_gj(cx1, d) : -1;
-            const int by0 = valid ? div_gj(cy0, d) : 0, by1 = valid ? div_gj(cy1, d) : -1;
             const unsigned cb = (unsigned)side * (unsigned)a.nbt + (unsigned)d.boff;
-            // first block: warp-aggregated slot; further blocks (replicas) one atomic each
-            const unsigned key = valid ? cb + (unsigned)(by0 * d.bx + bx0) : 0xffffffffu;
-            const unsigned peers = __match_any_sync(0xffffffffu, key);
-            const int leader = __ffs(peers) - 1;
-            unsigned pos0 = 0;
-            if (valid && (int)lane == leader) pos0 = atomicAdd(a.cur + key, (unsigned)__popc(peers));
-            pos0 = __shfl_sync(0xffffffffu, pos0, leader);
-            if (!valid) continue;
-            pos0 += __popc(peers & ((1u << lane) - 1u));
+            const int bx0 = div_gj(cx0, d), bx1 = div_gj(cx1, d), by0 = div_gj(cy0, d), by1 = div_gj(cy1, d);
             for (int by = by0; by <= by1; by++)
                 for (int bx = bx0; bx <= bx1; bx++) {
-                    const unsigned pos = (by == by0 && bx == bx0) ? pos0 : atomicAdd(a.cur + cb + by * d.bx + bx, 1u);
+                    const unsigned pos =
+                        (by == by0 && bx == bx0) ? pos0[u] : atomicAdd(a.cur + cb + by * d.bx + bx, 1u);
                     if (pos < cap) store_bent(dst + pos, head, tail);
                     else atomicOr(&a.st->err, kErrEntCap);
                 }
@@ -443,15 +498,12 @@ struct BlockCtx {
     const BEnt *er, *es;   // the block's R and S entries (shared-memory copy or global)
 };
 
-// Write entry e of the block into every tile of [ta, tb) it overlaps (rows
-// row_a..row_b of the block).  With row >= 0 the entry comes from the list
-// of that row and is taken only there if it is its first row in the band.
-__device__ __forceinline__ void stage_entry(BJSmem &sm, const BlockCtx &bc, int e, int ta, int tb, int row_a,
-                                            int row_b, int row) {
-    const int side = e >= (int)bc.nr1;
-    const uint4 *p = reinterpret_cast<const uint4 *>(side ? bc.es + (e - bc.nr1) : bc.er + e);
-    const uint4 t = p[1];
-    const uint4 hd = p[0];
+// Write an entry of the block (side, MBR words hd, tail words t) into every
+// tile of [ta, tb) it overlaps (rows row_a..row_b of the block).  With
+// row >= 0 the entry comes from the list of that row and is taken only there
+// if it is its first row in the band.
+__device__ __forceinline__ void place_entry(BJSmem &sm, const BlockCtx &bc, int side, const uint4 &hd,
+                                            const uint4 &t, int ta, int tb, int row_a, int row_b, int row) {
     const int cx0 = t.y & 0xffff, cx1 = t.y >> 16, cy0 = t.z & 0xffff, cy1 = t.z >> 16;
     const int ly0 = max(cy0 - bc.cyb, row_a), ly1 = min(cy1 - bc.cyb, row_b);
     if (ly0 > ly1 || (row >= 0 && ly0 != row)) return;
@@ -473,11 +525,14 @@ __device__ __forceinline__ void stage_entry(BJSmem &sm, const BlockCtx &bc, int 
         }
 }
 
-// Steps of one band [ta, tb): offsets, scatter into the tile segments,
-// ranks -> sorted entries.  Entries come from the row lists when rl is
-// given, else from the block's whole L1 range.  Results live in sm.
-__device__ __forceinline__ void band_stage(BJSmem &sm, const BlockCtx &bc, int ta, int tb, int &nRb, int &nSb,
-                                           const RowLists *rl) {
+__device__ __forceinline__ const uint4 *entry_words(const BlockCtx &bc, int e) {
+    return reinterpret_cast<const uint4 *>(e >= (int)bc.nr1 ? bc.es + (e - bc.nr1) : bc.er + e);
+}
+
+// Offsets of the band [ta, tb): sm.off[0][j] / sm.off[1][j] = start of tile
+// ta + j's R / S segment (S segments after all R segments); nRb, nSb = the
+// band's entries per side.  Ends with a barrier.
+__device__ __forceinline__ void band_offsets(BJSmem &sm, int ta, int tb, int &nRb, int &nSb) {
     const int NT = kBJThreads;
     const int nt = tb - ta;
     // packed exclusive scan of (R count | S count << 32) over the band's tiles
@@ -523,22 +578,65 @@ __device__ __forceinline__ void band_stage(BJSmem &sm, const BlockCtx &bc, int t
         }
     }
     __syncthreads();
+}
+
+// Scatter of the band's entries into its tile segments (entries from the row
+// lists when rl is given, else from the block's whole L1 range; every thread
+// loads kStageU entries before placing them), then the x_l order of every
+// segment.  Needs band_offsets first; results live in sm.
+constexpr int kStageU = 1;
+__device__ __forceinline__ void band_fill(BJSmem &sm, const BlockCtx &bc, int ta, int tb, int nRb, int nSb,
+                                          const RowLists *rl) {
+    const int NT = kBJThreads;
     // scatter the block's entries into the band's tile segments
     const int row_a = ta / bc.gw, row_b = (tb - 1) / bc.gw;
     if (rl) {
         const unsigned i0 = rl->pre[row_a], i1 = rl->pre[row_b + 1];
-        for (unsigned i = i0 + threadIdx.x; i < i1; i += NT) {
-            int lo = row_a, hi = row_b;   // the row holding item i: last y with pre[y] <= i
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (rl->pre[mid] <= i) lo = mid;
-                else hi = mid - 1;
+        for (unsigned ib = i0 + threadIdx.x; ib < i1; ib += kStageU * NT) {
+            int e[kStageU], row[kStageU];
+            uint4 hd[kStageU], t[kStageU];
+#pragma unroll
+            for (int u = 0; u < kStageU; u++) {
+                const unsigned i = ib + u * NT;
+                e[u] = -1;
+                if (i < i1) {
+                    int lo = row_a, hi = row_b;   // the row holding item i: last y with pre[y] <= i
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (rl->pre[mid] <= i) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    row[u] = lo;
+                    e[u] = (int)rl->pool[rl->off[lo] + (i - rl->pre[lo])];
+                }
             }
-            stage_entry(sm, bc, (int)rl->pool[rl->off[lo] + (i - rl->pre[lo])], ta, tb, row_a, row_b, lo);
+#pragma unroll
+            for (int u = 0; u < kStageU; u++)
+                if (e[u] >= 0) {
+                    const uint4 *w = entry_words(bc, e[u]);
+                    hd[u] = w[0];
+                    t[u] = w[1];
+                }
+#pragma unroll
+            for (int u = 0; u < kStageU; u++)
+                if (e[u] >= 0) place_entry(sm, bc, e[u] >= (int)bc.nr1, hd[u], t[u], ta, tb, row_a, row_b, row[u]);
         }
     } else {
         const int n1 = (int)(bc.nr1 + bc.ns1);
-        for (int e = threadIdx.x; e < n1; e += NT) stage_entry(sm, bc, e, ta, tb, row_a, row_b, -1);
+        for (int eb = threadIdx.x; eb < n1; eb += kStageU * NT) {
+            uint4 hd[kStageU], t[kStageU];
+#pragma unroll
+            for (int u = 0; u < kStageU; u++)
+                if (eb + u * NT < n1) {
+                    const uint4 *w = entry_words(bc, eb + u * NT);
+                    hd[u] = w[0];
+                    t[u] = w[1];
+                }
+#pragma unroll
+            for (int u = 0; u < kStageU; u++)
+                if (eb + u * NT < n1)
+                    place_entry(sm, bc, eb + u * NT >= (int)bc.nr1, hd[u], t[u], ta, tb, row_a, row_b, -1);
+        }
     }
     __syncthreads();
     // sort every tile segment by x_l: the rank of each position among its
@@ -571,6 +669,20 @@ __device__ __forceinline__ void band_stage(BJSmem &sm, const BlockCtx &bc, int t
     for (int q = 0; q < KP; q++)
         if (dst[q] >= 0) sm.key[dst[q]] = (unsigned)(threadIdx.x + q * NT);
     __syncthreads();
+}
+
+// All steps of one band [ta, tb): offsets (unless the band is the whole
+// block and they were computed already: entries nR0, nS0), scatter, x_l
+// order.
+__device__ __forceinline__ void stage_band(BJSmem &sm, const BlockCtx &bc, int ta, int tb, bool have_offsets,
+                                        int nR0, int nS0, const RowLists *rl, int &nRb, int &nSb) {
+    if (have_offsets) {
+        nRb = nR0;
+        nSb = nS0;
+    } else {
+        band_offsets(sm, ta, tb, nRb, nSb);
+    }
+    band_fill(sm, bc, ta, tb, nRb, nSb, rl);
 }
 
 // Candidate range of pivot p (any position) in the other side of its tile:
@@ -677,9 +789,10 @@ __device__ __forceinline__ void band_write(const BJSmem &sm, int nRb, int nSb, i
 }
 
 // Pairs of the staged band into the block's shared buffer (one-pass join):
-// every hit takes the next slot of *s_pc (warp-aggregated); hits beyond the
-// buffer are only counted.
-__device__ __forceinline__ void band_collect(BJSmem &sm, int nRb, int nSb, unsigned *s_pc) {
+// every hit takes the next slot of *s_pc (warp-aggregated); slots beyond the
+// buffer go to the CTA's spill area (if any), slots beyond both are only
+// counted.
+__device__ __forceinline__ void band_collect(BJSmem &sm, int nRb, int nSb, unsigned *s_pc, int2 *spill) {
     const int nb = nRb + nSb;
     if (nRb == 0 || nSb == 0) return;
     for (int p = threadIdx.x; p < nb; p += kBJThreads) {
@@ -700,9 +813,10 @@ __device__ __forceinline__ void band_collect(BJSmem &sm, int nRb, int nSb, unsig
                     unsigned pos = 0;
                     if ((int)(threadIdx.x & 31) == leader) pos = atomicAdd(s_pc, (unsigned)__popc(m));
                     pos = __shfl_sync(m, pos, leader) + __popc(m & lanemask_lt_b());
-                    if (pos < (unsigned)kPairBuf)
-                        sm.pbuf[pos] = isR ? make_int2((int)(pid & kIdMask), (int)(oid & kIdMask))
-                                           : make_int2((int)(oid & kIdMask), (int)(pid & kIdMask));
+                    const int2 pr = isR ? make_int2((int)(pid & kIdMask), (int)(oid & kIdMask))
+                                        : make_int2((int)(oid & kIdMask), (int)(pid & kIdMask));
+                    if (pos < (unsigned)kPairBuf) sm.pbuf[pos] = pr;
+                    else if (spill && pos < (unsigned)(kPairBuf + kPairSpill)) spill[pos - kPairBuf] = pr;
                 }
             }
         }
@@ -815,6 +929,7 @@ __device__ void band_split(BJSmem &sm, int ntl, unsigned *s_nbands, int *s_huge)
         if (l0 + k < ntl) {
             sm.off[0][l0 + k] = run;
             run += sm.cnt[0][l0 + k] + sm.cnt[1][l0 + k];
+            if (l0 + k == ntl - 1) sm.off[0][ntl] = run;
         }
     __syncthreads();
     // band-start flags -> sm.off[1][lt]
@@ -862,7 +977,16 @@ __device__ void band_split(BJSmem &sm, int ntl, unsigned *s_nbands, int *s_huge)
     __syncthreads();
     if (threadIdx.x == 0) {
         sm.band[s_t] = (unsigned short)ntl;
-        *s_nbands = s_t;
+        // the rule above leaves bands of h to 2h entries: merge neighbours
+        // greedily while the merged band still fits (sm.off[0] = prefix)
+        unsigned k = s_t;
+        if (!s_hg) {
+            k = 0;
+            for (unsigned i = 1; i < s_t; i++)
+                if (sm.off[0][sm.band[i + 1]] - sm.off[0][sm.band[k]] > (unsigned)kFineCap) sm.band[++k] = sm.band[i];
+            sm.band[++k] = (unsigned short)ntl;
+        }
+        *s_nbands = k;
         *s_huge = s_hg;
     }
     __syncthreads();
@@ -943,26 +1067,37 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
         }
         __syncthreads();
         const int n1 = (int)(bc.nr1 + bc.ns1);
-        for (int e = threadIdx.x; e < n1; e += kBJThreads) {
-            const int side = e >= (int)bc.nr1;
-            const BEnt *p = side ? bc.es + (e - bc.nr1) : bc.er + e;
-            const uint4 t = reinterpret_cast<const uint4 *>(p)[1];
-            const int lx0 = max((int)(t.y & 0xffff) - bc.cxb, 0), lx1 = min((int)(t.y >> 16) - bc.cxb, bc.gw - 1);
-            const int ly0 = max((int)(t.z & 0xffff) - bc.cyb, 0), ly1 = min((int)(t.z >> 16) - bc.cyb, bc.gh - 1);
-            for (int ly = ly0; ly <= ly1; ly++)
-                for (int lx = lx0; lx <= lx1; lx++) atomicAdd(&sm.cnt[side][ly * bc.gw + lx], 1u);
+        constexpr int kCountU = 2;   // entries a thread loads before counting them
+        for (int eb = threadIdx.x; eb < n1; eb += kCountU * kBJThreads) {
+            uint4 t[kCountU];
+#pragma unroll
+            for (int u = 0; u < kCountU; u++)
+                if (eb + u * kBJThreads < n1) t[u] = entry_words(bc, eb + u * kBJThreads)[1];
+#pragma unroll
+            for (int u = 0; u < kCountU; u++) {
+                const int e = eb + u * kBJThreads;
+                if (e >= n1) break;
+                const int side = e >= (int)bc.nr1;
+                const int lx0 = max((int)(t[u].y & 0xffff) - bc.cxb, 0);
+                const int lx1 = min((int)(t[u].y >> 16) - bc.cxb, bc.gw - 1);
+                const int ly0 = max((int)(t[u].z & 0xffff) - bc.cyb, 0);
+                const int ly1 = min((int)(t[u].z >> 16) - bc.cyb, bc.gh - 1);
+                for (int ly = ly0; ly <= ly1; ly++)
+                    for (int lx = lx0; lx <= lx1; lx++) atomicAdd(&sm.cnt[side][ly * bc.gw + lx], 1u);
+            }
         }
         __syncthreads();
         // step 2: bands of consecutive tiles that fit in shared memory.
-        // Usually the whole block fits (one band).  Otherwise, with h = half
+        // Usually the whole block fits (one band): the offsets of the whole
+        // block computed here are then its band's.  Otherwise, with h = half
         // the capacity, a band starts at every tile whose exclusive prefix
         // of entries enters a new multiple of h, and around every tile
-        // heavier than h; each band then holds fewer than 2h entries.
+        // heavier than h (each band then holds fewer than 2h entries), and
+        // neighbouring bands are merged while they fit.
+        int nR0, nS0;
+        band_offsets(sm, 0, bc.ntl, nR0, nS0);
         {
-            unsigned my = 0;
-            for (int lt = threadIdx.x; lt < bc.ntl; lt += kBJThreads) my += sm.cnt[0][lt] + sm.cnt[1][lt];
-            const unsigned total = block_sum(my, s_red);
-            if (total <= (unsigned)kFineCap) {
+            if (nR0 + nS0 <= kFineCap) {
                 if (threadIdx.x == 0) {
                     sm.band[0] = 0;
                     sm.band[1] = (unsigned short)bc.ntl;
@@ -992,11 +1127,15 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                 build_row_lists(sm, bc, s_rows, a.lpool, a.lpool_cap, &a.st->lpool[o.work_slot & 3]);
                 if (s_rows.on) rl = &s_rows;
             }
+            // band bi into shared memory (a single band has its offsets already)
+            auto stage = [&](int bi, int &nRb, int &nSb) {
+                stage_band(sm, bc, sm.band[bi], sm.band[bi + 1], nbands == 1, nR0, nS0, rl, nRb, nSb);
+            };
             if (MODE == MODE_WRITE) {
                 const unsigned long long base = o.off_in[it];
                 for (int bi = 0; bi < nbands; bi++) {
                     int nRb, nSb;
-                    band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb, rl);
+                    stage(bi, nRb, nSb);
                     band_write(sm, nRb, nSb, o.out, base, &s_cursor);
                     __syncthreads();
                 }
@@ -1004,9 +1143,10 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                 unsigned tot = 0;
                 int nRb = 0, nSb = 0;
                 for (int bi = 0; bi < nbands; bi++) {
-                    band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb, rl);
+                    stage(bi, nRb, nSb);
                     if (MODE == MODE_RESERVE) {
-                        band_collect(sm, nRb, nSb, &s_pc);
+                        band_collect(sm, nRb, nSb, &s_pc,
+                                     o.spill ? o.spill + (size_t)blockIdx.x * kPairSpill : nullptr);
                         __syncthreads();
                     } else {
                         tot += block_sum(band_count(sm, bc, sm.band[bi], nRb, nSb,
@@ -1033,13 +1173,16 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                     }
                     __syncthreads();
                     if (MODE == MODE_RESERVE && s_ok) {
-                        if (tot <= (unsigned)kPairBuf) {   // the usual case: copy the collected pairs
-                            for (unsigned i = threadIdx.x; i < tot; i += kBJThreads) o.out[s_base + i] = sm.pbuf[i];
+                        const unsigned kept = o.spill ? kPairBuf + kPairSpill : kPairBuf;
+                        if (tot <= kept) {   // the usual case: copy the collected pairs
+                            const int2 *sp = o.spill + (size_t)blockIdx.x * kPairSpill;
+                            for (unsigned i = threadIdx.x; i < tot; i += kBJThreads)
+                                o.out[s_base + i] = i < (unsigned)kPairBuf ? sm.pbuf[i] : sp[i - kPairBuf];
                         } else if (nbands == 1) {
                             band_write(sm, nRb, nSb, o.out, s_base, &s_cursor);
                         } else {
                             for (int bi = 0; bi < nbands; bi++) {
-                                band_stage(sm, bc, sm.band[bi], sm.band[bi + 1], nRb, nSb, rl);
+                                stage(bi, nRb, nSb);
                                 band_write(sm, nRb, nSb, o.out, s_base, &s_cursor);
                                 __syncthreads();
                             }

@@ -47,16 +47,22 @@ __global__ void k_features(const unsigned *__restrict__ raw, const unsigned *__r
 // ---------------------------------------------------------------------------
 // MLP forward (inference): one warp per sample, bf16 weights in shared memory
 // ---------------------------------------------------------------------------
+// Weights are kept input-major (w1t[k][j] = W1[j][k], w2t[k][j] = W2[j][k]):
+// in the forward pass the 32 lanes of a warp compute 32 consecutive units j
+// and read 32 consecutive values; the backward pass (lane = k) walks j from
+// a lane-dependent start, so the lanes again fall in different banks.
 struct MlpSmem {
-    __nv_bfloat16 w1[kH1 * kFeat];
-    __nv_bfloat16 w2[kH2 * kH1];
+    __nv_bfloat16 w1t[kFeat * kH1];
+    __nv_bfloat16 w2t[kH1 * kH2];
     __nv_bfloat16 w3[kH2];
     float b1[kH1], b2[kH2], b3;
 };
 
 __device__ __forceinline__ void mlp_load(MlpSmem &m, const MlpWeights &w) {
-    for (int k = threadIdx.x; k < kH1 * kFeat; k += blockDim.x) m.w1[k] = w.w1[k];
-    for (int k = threadIdx.x; k < kH2 * kH1; k += blockDim.x) m.w2[k] = w.w2[k];
+#pragma unroll 8
+    for (int k = threadIdx.x; k < kH1 * kFeat; k += blockDim.x) m.w1t[(k % kFeat) * kH1 + k / kFeat] = w.w1[k];
+#pragma unroll 8
+    for (int k = threadIdx.x; k < kH2 * kH1; k += blockDim.x) m.w2t[(k % kH1) * kH2 + k / kH1] = w.w2[k];
     for (int k = threadIdx.x; k < kH2; k += blockDim.x) {
         m.w3[k] = w.w3[k];
         m.b2[k] = w.b2[k];
@@ -78,7 +84,7 @@ __device__ __forceinline__ float mlp_warp_forward(const MlpSmem &m, const float 
         const int j = lane + 32 * u;
         float acc = m.b1[j];
 #pragma unroll 8
-        for (int k = 0; k < kFeat; k++) acc = fmaf(__bfloat162float(m.w1[j * kFeat + k]), x[k], acc);
+        for (int k = 0; k < kFeat; k++) acc = fmaf(__bfloat162float(m.w1t[k * kH1 + j]), x[k], acc);
         z1[u] = acc;
         h1s[j] = fmaxf(acc, 0.0f);
     }
@@ -88,7 +94,7 @@ __device__ __forceinline__ float mlp_warp_forward(const MlpSmem &m, const float 
         const int j = lane + 32 * u;
         float acc = m.b2[j];
 #pragma unroll 8
-        for (int k = 0; k < kH1; k++) acc = fmaf(__bfloat162float(m.w2[j * kH1 + k]), h1s[k], acc);
+        for (int k = 0; k < kH1; k++) acc = fmaf(__bfloat162float(m.w2t[k * kH2 + j]), h1s[k], acc);
         z2[u] = acc;
     }
     float part = 0.0f;
@@ -187,7 +193,10 @@ __global__ void __launch_bounds__(kMlpThreads) k_mlp_grad(MlpWeights w, const fl
         for (int u = 0; u < 2; u++) {
             const int k = lane + 32 * u;
             float acc = 0.0f;
-            for (int j = 0; j < kH2; j++) acc = fmaf(d2s[wid][j], __bfloat162float(m.w2[j * kH1 + k]), acc);
+            for (int jj = 0; jj < kH2; jj++) {
+                const int j = (jj + lane) & (kH2 - 1);
+                acc = fmaf(d2s[wid][j], __bfloat162float(m.w2t[k * kH2 + j]), acc);
+            }
             d1[u] = z1s[wid][k] > 0.0f ? acc : 0.0f;          // d loss / d z1_k
         }
         // layer 1
@@ -261,46 +270,83 @@ __global__ void k_heur_pred(const float *__restrict__ feat, const unsigned *__re
     }
 }
 
-// One CTA of 1024 threads: cap[it] = ceil(expm1(pred) * (1 + margin)) + slack
-// (at least 0); total -> *cap_total; order = items sorted by predicted cost
-// (L1 entries + predicted pairs) into 32 log2 classes, heaviest first.
+// cap[it] = ceil(expm1(pred) * (1 + margin)) + slack (at least 0), summed
+// into the total; order = items sorted by predicted cost (L1 entries +
+// predicted pairs) into 32 log2 classes, heaviest first.  Two launches over
+// all items: class histogram and total, then the slots.  scratch (zeroed by
+// the launcher) holds hist[32], cursor[32].
 __device__ __forceinline__ int cost_class(float cost) {
     return cost >= 1.0f ? min(31, (int)log2f(cost)) : 0;
 }
 
-__global__ void __launch_bounds__(1024) k_plan(const float *__restrict__ pred, const uint4 *__restrict__ imeta,
-                                               const unsigned *__restrict__ ins, const Stats *__restrict__ st,
-                                               float margin, unsigned slack, unsigned long long *cap_total,
-                                               unsigned *__restrict__ order) {
-    __shared__ unsigned hist[32], base[32];
+__device__ __forceinline__ int plan_class(const float *__restrict__ pred, const uint4 *__restrict__ imeta,
+                                          const unsigned *__restrict__ ins, unsigned it, float &e) {
+    e = expm1f(fminf(fmaxf(pred[it], 0.0f), 21.0f));   // at most ~1.3e9 pairs a block
+    return 31 - cost_class((float)imeta[it].z + (float)ins[it] + e);
+}
+
+__global__ void __launch_bounds__(256) k_plan_count(const float *__restrict__ pred, const uint4 *__restrict__ imeta,
+                                                    const unsigned *__restrict__ ins, const Stats *__restrict__ st,
+                                                    float margin, unsigned slack, unsigned long long *cap_total,
+                                                    unsigned *__restrict__ scratch) {
+    __shared__ unsigned hist[32];
     __shared__ unsigned long long s_tot;
     const unsigned n = st->nchunks;
     if (threadIdx.x < 32) hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_tot = 0;
     __syncthreads();
+    const unsigned lanelt = (1u << (threadIdx.x & 31)) - 1u;
     unsigned long long my = 0;
-    for (unsigned it = threadIdx.x; it < n; it += blockDim.x) {
-        const float e = expm1f(fminf(fmaxf(pred[it], 0.0f), 21.0f));   // at most ~1.3e9 pairs a block
-        my += (unsigned long long)ceilf(e * (1.0f + margin)) + slack;
-        const float cost = (float)imeta[it].z + (float)ins[it] + e;
-        atomicAdd(&hist[31 - cost_class(cost)], 1u);
-    }
-    atomicAdd(&s_tot, my);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned acc = 0;
-        for (int q = 0; q < 32; q++) {
-            base[q] = acc;
-            acc += hist[q];
+    for (unsigned b = blockIdx.x * 256; b < n; b += 256 * gridDim.x) {   // whole warps per step
+        const unsigned it = b + threadIdx.x;
+        int c = -1;
+        if (it < n) {
+            float e;
+            c = plan_class(pred, imeta, ins, it, e);
+            my += (unsigned long long)ceilf(e * (1.0f + margin)) + slack;
         }
-        *cap_total = s_tot;
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        if (c >= 0 && (peers & lanelt) == 0) atomicAdd(&hist[c], (unsigned)__popc(peers));
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) my += __shfl_xor_sync(0xffffffffu, my, d);
+    if ((threadIdx.x & 31) == 0 && my) atomicAdd(&s_tot, my);
+    __syncthreads();
+    if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(scratch + threadIdx.x, hist[threadIdx.x]);
+    if (threadIdx.x == 0 && s_tot) atomicAdd(cap_total, s_tot);
+}
+
+__global__ void __launch_bounds__(256) k_plan_order(const float *__restrict__ pred, const uint4 *__restrict__ imeta,
+                                                    const unsigned *__restrict__ ins, const Stats *__restrict__ st,
+                                                    unsigned *__restrict__ scratch, unsigned *__restrict__ order) {
+    __shared__ unsigned base[32];
+    const unsigned n = st->nchunks;
+    if (threadIdx.x < 32) {   // exclusive scan of the class histogram
+        const unsigned h = scratch[threadIdx.x];
+        unsigned inc = h;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned o = __shfl_up_sync(0xffffffffu, inc, d);
+            if ((int)threadIdx.x >= d) inc += o;
+        }
+        base[threadIdx.x] = inc - h;
     }
     __syncthreads();
-    for (unsigned it = threadIdx.x; it < n; it += blockDim.x) {
-        const float e = expm1f(fminf(fmaxf(pred[it], 0.0f), 21.0f));
-        const float cost = (float)imeta[it].z + (float)ins[it] + e;
-        const unsigned pos = atomicAdd(&base[31 - cost_class(cost)], 1u);
-        order[pos] = it;
+    const unsigned lanelt = (1u << (threadIdx.x & 31)) - 1u;
+    unsigned *cursor = scratch + 32;
+    for (unsigned b = blockIdx.x * 256; b < n; b += 256 * gridDim.x) {
+        const unsigned it = b + threadIdx.x;
+        int c = -1;
+        if (it < n) {
+            float e;
+            c = plan_class(pred, imeta, ins, it, e);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const int leader = __ffs(peers) - 1;
+        unsigned pos = 0;
+        if (c >= 0 && (int)(threadIdx.x & 31) == leader) pos = atomicAdd(cursor + c, (unsigned)__popc(peers));
+        pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & lanelt);
+        if (c >= 0) order[base[c] + pos] = it;
     }
 }
 
@@ -352,9 +398,15 @@ cudaError_t launch_heur_pred(const float *feat, const unsigned *items, const uns
     return cudaGetLastError();
 }
 
+// cap_total points to kPlanScratch bytes: the total, then the class
+// histogram and cursors.  grid: CTAs of 256 over the items.
 cudaError_t launch_plan(const float *pred, const uint4 *imeta, const unsigned *ins, const Stats *st, float margin,
-                        unsigned slack, unsigned long long *cap_total, unsigned *order, cudaStream_t s) {
-    k_plan<<<1, 1024, 0, s>>>(pred, imeta, ins, st, margin, slack, cap_total, order);
+                        unsigned slack, unsigned long long *cap_total, unsigned *order, int grid, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(cap_total, 0, kPlanScratch, s);
+    if (e) return e;
+    unsigned *scratch = reinterpret_cast<unsigned *>(cap_total + 1);
+    k_plan_count<<<grid, 256, 0, s>>>(pred, imeta, ins, st, margin, slack, cap_total, scratch);
+    k_plan_order<<<grid, 256, 0, s>>>(pred, imeta, ins, st, scratch, order);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@ constexpr int kMaxG = 32;            // tiles per block side
 constexpr int kLoadBatch = 4;        // entries a thread loads before using them
 constexpr int kMaxJoins = 4096;      // joins in one batch
 constexpr int kPairBuf = 1536;       // pairs a one-pass block collects in shared memory
+constexpr int kPairSpill = 16384;    // ... and then in its CTA's global spill area
 constexpr int kMaxFine = kMaxG * kMaxG;
 
 // An L1 entry: one aligned 32-byte sector.
@@ -86,6 +87,7 @@ struct BJoinOut {
     int2 *out;
     unsigned long long cap;
     unsigned *tile_pairs;       // MODE_TILES
+    int2 *spill;                // MODE_RESERVE, optional: kPairSpill pairs per CTA
 };
 
 cudaError_t blocked_setup();

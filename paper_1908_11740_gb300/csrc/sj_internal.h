@@ -31,6 +31,7 @@ struct Workspace {
     Buf bFeatRaw, bFeat, bPred, bOrder, bCapTot;   // learned one-pass sizing
     Buf bCur;                                      // shared L1 write cursors
     Buf bList;                                     // row lists of multi-band blocks
+    Buf bSpill;                                    // one-pass pair spill per block-join CTA
     Buf bJd, bIjoin, bJfirst, bJoff;               // join table (batches: per-join offsets)
     unsigned long long bcap_r = 0, bcap_s = 0;
     unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
