@@ -82,13 +82,15 @@ __global__ void __launch_bounds__(kL1Threads) k_bcount(BArgs a) {
     if (bad) atomicOr(&a.st->err, kErrBadRect);
 }
 
-// L1 scan, part 1: for every (side, block), the exclusive prefix over CTAs
-// (in place) and the total per (side, block).
+// L1 scan, part 1: for every (side, block), the total per (side, block) and,
+// for the CTA-private write ranges (no shared cursors), the exclusive prefix
+// over CTAs (in place).
 __global__ void __launch_bounds__(256) k_bscan_ctas(BArgs a, int nc) {
     const int NB2 = 2 * a.nb;
     const int sb = blockIdx.x * 256 + threadIdx.x;
     if (sb >= NB2) return;
     unsigned *__restrict__ H = a.H;
+    const bool prefix = a.cur == nullptr;
     unsigned run = 0;
     for (int c0 = 0; c0 < nc; c0 += 16) {
         unsigned v[16];
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(256) k_bscan_ctas(BArgs a, int nc) {
 #pragma unroll
         for (int u = 0; u < 16; u++)
             if (c0 + u < nc) {
-                H[(size_t)(c0 + u) * NB2 + sb] = run;
+                if (prefix) H[(size_t)(c0 + u) * NB2 + sb] = run;
                 run += v[u];
             }
     }
@@ -119,6 +121,18 @@ __device__ __forceinline__ void load8(const unsigned *__restrict__ p, int b, int
     } else {
 #pragma unroll
         for (int k = 0; k < kScanPer; k++) v[k] = b + k < nb ? p[b + k] : 0u;
+    }
+}
+
+// p[b .. b+7] = v (two 16-byte stores when aligned and in range).
+__device__ __forceinline__ void store8(unsigned *__restrict__ p, int b, int nb, const unsigned (&v)[kScanPer]) {
+    if (b + kScanPer <= nb && ((reinterpret_cast<uintptr_t>(p + b) & 15) == 0)) {
+        *reinterpret_cast<uint4 *>(p + b) = make_uint4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<uint4 *>(p + b + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++)
+            if (b + k < nb) p[b + k] = v[k];
     }
 }
 
@@ -178,16 +192,24 @@ __global__ void __launch_bounds__(1024) k_bscan_blocks(BArgs a) {
         unsigned long long pr = carry_r + scan1024(sr, s_w64, &tr);
         unsigned long long ps = carry_s + scan1024(ss, s_w64, &ts);
         unsigned idx = carry_f + scan1024(sf, s_w32, &tf);
+        unsigned orr[kScanPer], oss[kScanPer];
+#pragma unroll
+        for (int k = 0; k < kScanPer; k++) {
+            orr[k] = (unsigned)pr;
+            oss[k] = (unsigned)ps;
+            pr += vr[k];
+            ps += vs[k];
+        }
+        store8(a.bo_r, b0, nb, orr);
+        store8(a.bo_s, b0, nb, oss);
+        if (a.cur) {
+            store8(a.cur, b0, nb, orr);
+            store8(a.cur + nb, b0, nb, oss);
+        }
 #pragma unroll
         for (int k = 0; k < kScanPer; k++) {
             const int b = b0 + k;
             if (b >= nb) break;
-            a.bo_r[b] = (unsigned)pr;
-            a.bo_s[b] = (unsigned)ps;
-            if (a.cur) {
-                a.cur[b] = (unsigned)pr;
-                a.cur[nb + b] = (unsigned)ps;
-            }
             // join of block b: the last join whose first block is <= b
             int lo = 0, hi = a.nj;
             while (hi - lo > 1) {
@@ -198,13 +220,11 @@ __global__ void __launch_bounds__(1024) k_bscan_blocks(BArgs a) {
             if (a.jfirst && s_boff[lo] == b) a.jfirst[lo] = idx;
             if (vr[k] > 0 && vs[k] > 0) {
                 a.items[idx] = (unsigned)b;
-                a.imeta[idx] = make_uint4((unsigned)b, (unsigned)pr, vr[k], (unsigned)ps);
+                a.imeta[idx] = make_uint4((unsigned)b, orr[k], vr[k], oss[k]);
                 a.ins[idx] = vs[k];
                 if (a.ijoin) a.ijoin[idx] = (unsigned)lo;
                 idx++;
             }
-            pr += vr[k];
-            ps += vs[k];
         }
         carry_r += tr;
         carry_s += ts;
