@@ -197,7 +197,7 @@ def alg_bytes(phase, n_in, E, P):
 
 
 KERNELS = {
-    1: {"count": "k_bcount", "scatter": "k_bscatter", "sweep_count": "k_bjoin<COUNT>",
+    1: {"count": "k_bcount", "scatter": "k_bscatter_shared", "sweep_count": "k_bjoin<COUNT>",
         "sweep_write": "k_bjoin<WRITE>", "sweep_reserve": "k_bjoin<RESERVE>"},
     0: {"count": "k_count", "scatter": "k_scatter", "sweep_count": "k_sweep_chunks<COUNT>",
         "sweep_write": "k_sweep_chunks<WRITE>", "sweep_reserve": "k_sweep_chunks<RESERVE>"},
