@@ -97,7 +97,7 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
                   &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out, &w.bH,
                   &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
                   &w.bResv, &w.bFail, &w.bImeta, &w.bIns, &w.bFeatRaw, &w.bFeat, &w.bPred,
-                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bSpill, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff};
+                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bSpill, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff, &w.bScanPart};
     for (Buf *b : all) {
         dev_free(ctx, b->p);
         b->p = nullptr;
@@ -626,6 +626,7 @@ int sj::size_blocked(sj_ctx *ctx, Workspace &w, const BPlan &p) {
     if ((st = ensure(ctx, w.bList, 4ull * list_pool_cap(w)))) return st;
     if ((st = ensure(ctx, w.bSpill, 8ull * kPairSpill * ctx->num_sms * ctx->bjoin_bps))) return st;
     if ((st = ensure(ctx, w.bJd, sizeof(JoinDesc) * 2))) return st;
+    if ((st = ensure(ctx, w.bScanPart, 24ull * (bscan_chunks(p.nb) + 1)))) return st;
     return SJ_OK;
 }
 
@@ -657,6 +658,7 @@ BArgs sj::blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long 
     a.cur = nullptr;
     a.lpool = (unsigned *)w.bList.p;
     a.lpool_cap = list_pool_cap(w);
+    a.scan_part = (unsigned long long *)w.bScanPart.p;
     a.jd = (const JoinDesc *)w.bJd.p;   // filled by enqueue_blocked_partition
     a.nj = 1;
     a.nbt = p.nb;

@@ -245,7 +245,7 @@ extern "C" int sj_block_features(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, co
         if ((st = enqueue_blocked_partition(ctx, w, p, a))) return st;
         {
             PhaseScope ph(ctx, PH_MODEL, 2);
-            if ((e = launch_bfeat_sample(a, ctx->num_sms * 4, ctx->stream))) return cuda_fail(ctx, e, "sampling");
+            if ((e = launch_bfeat_sample(a, ctx->num_sms * 16, ctx->stream))) return cuda_fail(ctx, e, "sampling");
             if ((e = launch_features((const unsigned *)w.bFeatRaw.p, a.items, a.btot, p.nb, a.st,
                                      (float *)w.bFeat.p, ctx->num_sms * 2, ctx->stream)))
                 return cuda_fail(ctx, e, "features");
@@ -337,16 +337,16 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         unsigned long long *d_cap = (unsigned long long *)w.bCapTot.p;
         {
             PhaseScope ph(ctx, PH_MODEL, 5);
-            if ((e = launch_bfeat_sample(a, ctx->num_sms * 4, s))) return cuda_fail(ctx, e, "sampling");
+            if ((e = launch_bfeat_sample(a, ctx->num_sms * 16, s))) return cuda_fail(ctx, e, "sampling");
             if ((e = launch_features((const unsigned *)w.bFeatRaw.p, a.items, a.btot, p.nb, a.st, (float *)w.bFeat.p,
-                                     ctx->num_sms * 2, s)))
+                                     ctx->num_sms * 8, s)))
                 return cuda_fail(ctx, e, "features");
             if (heuristic) {
                 e = launch_heur_pred((const float *)w.bFeat.p, a.items, a.btot, p.nb, a.st, (float *)w.bPred.p,
                                      ctx->num_sms * 2, s);
             } else {
                 e = launch_mlp_forward(weights_of(ctx->model), (const float *)w.bFeat.p, 0, &a.st->nchunks,
-                                       (float *)w.bPred.p, ctx->num_sms * 2, s);
+                                       (float *)w.bPred.p, ctx->num_sms * 8, s);
             }
             if (e) return cuda_fail(ctx, e, "prediction");
             if ((e = launch_plan((const float *)w.bPred.p, a.imeta, a.ins, a.st, margin, slack, d_cap,

@@ -66,10 +66,9 @@ __global__ void __launch_bounds__(kL1Threads) k_bcount(BArgs a) {
                 continue;
             }
             const int side = i >= a.nR;
-            const int bx0 = div_g(cell_of(m[u].x, a.g.x0, a.g.gx, a.g.nx), a);
-            const int bx1 = div_g(cell_of(m[u].z, a.g.x0, a.g.gx, a.g.nx), a);
-            const int by0 = div_g(cell_of(m[u].y, a.g.y0, a.g.gy, a.g.ny), a);
-            const int by1 = div_g(cell_of(m[u].w, a.g.y0, a.g.gy, a.g.ny), a);
+            const int cx0 = cell_of(m[u].x, a.g.x0, a.g.gx, a.g.nx), cx1 = cell_of(m[u].z, a.g.x0, a.g.gx, a.g.nx);
+            const int cy0 = cell_of(m[u].y, a.g.y0, a.g.gy, a.g.ny), cy1 = cell_of(m[u].w, a.g.y0, a.g.gy, a.g.ny);
+            const int bx0 = div_g(cx0, a), bx1 = div_g(cx1, a), by0 = div_g(cy0, a), by1 = div_g(cy1, a);
             unsigned *h = hist + side * a.nb;
             for (int by = by0; by <= by1; by++)
                 for (int bx = bx0; bx <= bx1; bx++) atomicAdd(h + by * a.bx + bx, 1u);
@@ -114,6 +113,8 @@ __global__ void __launch_bounds__(256) k_bscan_ctas(BArgs a, int nc) {
 // 8 consecutive blocks of each side, the chunk is scanned once for the packed
 // (R, S) prefix and once for the work-item count, and a carry links chunks.
 constexpr int kScanPer = 8;
+constexpr int kScanThreads = 256;
+constexpr int kScanChunk = kScanThreads * kScanPer;   // blocks per CTA of the block scan
 __device__ __forceinline__ void load8(const unsigned *__restrict__ p, int b, int nb, unsigned (&v)[kScanPer]) {
     if (b + kScanPer <= nb && ((reinterpret_cast<uintptr_t>(p + b) & 15) == 0)) {
         const uint4 x = *reinterpret_cast<const uint4 *>(p + b), y = *reinterpret_cast<const uint4 *>(p + b + 4);
@@ -164,80 +165,162 @@ __device__ __forceinline__ T scan1024(T v, T *s_w, T *total) {
     return s_w[wid] + inc - v;
 }
 
-__global__ void __launch_bounds__(1024) k_bscan_blocks(BArgs a) {
-    __shared__ unsigned long long s_w64[33];
-    __shared__ unsigned s_w32[33];
-    __shared__ int s_boff[kMaxJoins + 1];
-    const int nb = a.nbt;
-    for (int j = threadIdx.x; j < a.nj; j += 1024) s_boff[j] = a.jd[j].boff;
+// Exclusive block scan (256 threads) of v; *total gets the sum.  Two
+// barriers; every warp writes only its own slot of s_w before the first one,
+// so consecutive calls may share s_w.
+template <typename T>
+__device__ __forceinline__ T scan256(T v, T *s_w, T *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T o = __shfl_up_sync(kFullMask, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) s_w[wid] = inc;
     __syncthreads();
-    const unsigned *__restrict__ btot = a.btot;
-    unsigned long long carry_r = 0, carry_s = 0;   // entries before this chunk
-    unsigned carry_f = 0;                          // work items before this chunk
-    for (int c0 = 0; c0 < nb; c0 += 1024 * kScanPer) {
-        const int b0 = c0 + threadIdx.x * kScanPer;
-        unsigned vr[kScanPer], vs[kScanPer];
-        load8(btot, b0, nb, vr);
-        load8(btot + nb, b0, nb, vs);
-        unsigned long long sr = 0, ss = 0;
-        unsigned sf = 0;
+    if (wid == 0) {
+        const T x = lane < kScanThreads / 32 ? s_w[lane] : T(0);
+        T xi = x;
 #pragma unroll
-        for (int k = 0; k < kScanPer; k++) {
-            sr += vr[k];
-            ss += vs[k];
-            sf += (vr[k] > 0 && vs[k] > 0);
+        for (int d = 1; d < 32; d <<= 1) {
+            const T o = __shfl_up_sync(kFullMask, xi, d);
+            if (lane >= d) xi += o;
         }
-        unsigned long long tr, ts;
-        unsigned tf;
-        unsigned long long pr = carry_r + scan1024(sr, s_w64, &tr);
-        unsigned long long ps = carry_s + scan1024(ss, s_w64, &ts);
-        unsigned idx = carry_f + scan1024(sf, s_w32, &tf);
-        unsigned orr[kScanPer], oss[kScanPer];
+        if (lane < kScanThreads / 32) s_w[lane] = xi - x;
+        if (lane == kScanThreads / 32 - 1) s_w[kScanThreads / 32] = xi;
+    }
+    __syncthreads();
+    *total = s_w[kScanThreads / 32];
+    return s_w[wid] + inc - v;
+}
+
+// Part 2a: per chunk of kScanChunk blocks, the entries of each side and the
+// blocks that hold both sides -> part[3 c .. 3 c + 2].
+__global__ void __launch_bounds__(kScanThreads) k_bscan_part(BArgs a, unsigned long long *__restrict__ part) {
+    __shared__ unsigned long long s_w64[kScanThreads / 32 + 1];
+    __shared__ unsigned s_w32[kScanThreads / 32 + 1];
+    const int nb = a.nbt;
+    const int b0 = blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    unsigned vr[kScanPer], vs[kScanPer];
+    load8(a.btot, b0, nb, vr);
+    load8(a.btot + nb, b0, nb, vs);
+    unsigned long long sr = 0, ss = 0;
+    unsigned sf = 0;
 #pragma unroll
-        for (int k = 0; k < kScanPer; k++) {
-            orr[k] = (unsigned)pr;
-            oss[k] = (unsigned)ps;
-            pr += vr[k];
-            ps += vs[k];
+    for (int k = 0; k < kScanPer; k++) {
+        sr += vr[k];
+        ss += vs[k];
+        sf += (vr[k] > 0 && vs[k] > 0);
+    }
+    unsigned long long tr, ts;
+    unsigned tf;
+    scan256(sr, s_w64, &tr);
+    scan256(ss, s_w64, &ts);
+    scan256(sf, s_w32, &tf);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = tr;
+        part[3 * blockIdx.x + 1] = ts;
+        part[3 * blockIdx.x + 2] = tf;
+    }
+}
+
+// Part 2b (one CTA): exclusive scan of the chunk sums in place; the totals.
+__global__ void __launch_bounds__(1024) k_bscan_top(BArgs a, unsigned long long *__restrict__ part, int nch) {
+    __shared__ unsigned long long s_w64[33];
+    const int nb = a.nbt;
+    unsigned long long cr = 0, cs = 0, cf = 0;
+    for (int c0 = 0; c0 < nch; c0 += 1024) {
+        const int c = c0 + threadIdx.x;
+        const unsigned long long r = c < nch ? part[3 * c] : 0ull, sv = c < nch ? part[3 * c + 1] : 0ull,
+                                 f = c < nch ? part[3 * c + 2] : 0ull;
+        unsigned long long tr, ts, tf;
+        const unsigned long long er = cr + scan1024(r, s_w64, &tr);
+        const unsigned long long es = cs + scan1024(sv, s_w64, &ts);
+        const unsigned long long ef = cf + scan1024(f, s_w64, &tf);
+        if (c < nch) {
+            part[3 * c] = er;
+            part[3 * c + 1] = es;
+            part[3 * c + 2] = ef;
         }
-        store8(a.bo_r, b0, nb, orr);
-        store8(a.bo_s, b0, nb, oss);
-        if (a.cur) {
-            store8(a.cur, b0, nb, orr);
-            store8(a.cur + nb, b0, nb, oss);
-        }
+        cr += tr;
+        cs += ts;
+        cf += tf;
+    }
+    if (threadIdx.x == 0) {
+        a.bo_r[nb] = (unsigned)cr;
+        a.bo_s[nb] = (unsigned)cs;
+        a.st->e_r = cr;
+        a.st->e_s = cs;
+        if (cr > a.cap_r || cs > a.cap_s) atomicOr(&a.st->err, kErrEntCap);
+        a.st->nchunks = (unsigned)cf;
+        if (a.jfirst) a.jfirst[a.nj] = (unsigned)cf;
+    }
+}
+
+// Part 2c: every chunk's blocks -> block starts (and shared cursors), work
+// items with their ranges and join, first item of every join.
+__global__ void __launch_bounds__(kScanThreads) k_bscan_fill(BArgs a, const unsigned long long *__restrict__ part) {
+    __shared__ unsigned long long s_w64[kScanThreads / 32 + 1];
+    __shared__ unsigned s_w32[kScanThreads / 32 + 1];
+    __shared__ int s_boff[kMaxJoins];
+    const int nb = a.nbt;
+    if (a.nj > 1)
+        for (int j = threadIdx.x; j < a.nj; j += kScanThreads) s_boff[j] = a.jd[j].boff;
+    const int b0 = blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    unsigned vr[kScanPer], vs[kScanPer];
+    load8(a.btot, b0, nb, vr);
+    load8(a.btot + nb, b0, nb, vs);
+    unsigned long long sr = 0, ss = 0;
+    unsigned sf = 0;
 #pragma unroll
-        for (int k = 0; k < kScanPer; k++) {
-            const int b = b0 + k;
-            if (b >= nb) break;
-            // join of block b: the last join whose first block is <= b
-            int lo = 0, hi = a.nj;
+    for (int k = 0; k < kScanPer; k++) {
+        sr += vr[k];
+        ss += vs[k];
+        sf += (vr[k] > 0 && vs[k] > 0);
+    }
+    unsigned long long tr, ts;
+    unsigned tf;
+    unsigned long long pr = part[3 * blockIdx.x] + scan256(sr, s_w64, &tr);
+    unsigned long long ps = part[3 * blockIdx.x + 1] + scan256(ss, s_w64, &ts);
+    unsigned idx = (unsigned)part[3 * blockIdx.x + 2] + scan256(sf, s_w32, &tf);
+    unsigned orr[kScanPer], oss[kScanPer];
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) {
+        orr[k] = (unsigned)pr;
+        oss[k] = (unsigned)ps;
+        pr += vr[k];
+        ps += vs[k];
+    }
+    store8(a.bo_r, b0, nb, orr);
+    store8(a.bo_s, b0, nb, oss);
+    if (a.cur) {
+        store8(a.cur, b0, nb, orr);
+        store8(a.cur + nb, b0, nb, oss);
+    }
+#pragma unroll
+    for (int k = 0; k < kScanPer; k++) {
+        const int b = b0 + k;
+        if (b >= nb) break;
+        int lo = 0;
+        if (a.nj > 1) {   // join of block b: the last join whose first block is <= b
+            int hi = a.nj;
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
                 if (s_boff[mid] <= b) lo = mid;
                 else hi = mid;
             }
             if (a.jfirst && s_boff[lo] == b) a.jfirst[lo] = idx;
-            if (vr[k] > 0 && vs[k] > 0) {
-                a.items[idx] = (unsigned)b;
-                a.imeta[idx] = make_uint4((unsigned)b, orr[k], vr[k], oss[k]);
-                a.ins[idx] = vs[k];
-                if (a.ijoin) a.ijoin[idx] = (unsigned)lo;
-                idx++;
-            }
+        } else if (a.jfirst && b == 0) {
+            a.jfirst[0] = idx;
         }
-        carry_r += tr;
-        carry_s += ts;
-        carry_f += tf;
-    }
-    if (threadIdx.x == 0) {
-        a.bo_r[nb] = (unsigned)carry_r;
-        a.bo_s[nb] = (unsigned)carry_s;
-        a.st->e_r = carry_r;
-        a.st->e_s = carry_s;
-        if (carry_r > a.cap_r || carry_s > a.cap_s) atomicOr(&a.st->err, kErrEntCap);
-        a.st->nchunks = carry_f;
-        if (a.jfirst) a.jfirst[a.nj] = carry_f;
+        if (vr[k] > 0 && vs[k] > 0) {
+            a.items[idx] = (unsigned)b;
+            a.imeta[idx] = make_uint4((unsigned)b, orr[k], vr[k], oss[k]);
+            a.ins[idx] = vs[k];
+            if (a.ijoin) a.ijoin[idx] = (unsigned)lo;
+            idx++;
+        }
     }
 }
 
@@ -1238,13 +1321,13 @@ __global__ void __launch_bounds__(256) k_extent_stats(BArgs a, double *__restric
 }
 
 // ---- launchers -------------------------------------------------------------
-cudaError_t launch_extent_stats(const BArgs &a, double *out, int grid, cudaStream_t s) {
-    k_extent_stats<<<grid, 256, 8ull * (a.nj + 1), s>>>(a, out);
+cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s) {
+    k_bfeat_sample<<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s) {
-    k_bfeat_sample<<<grid, 256, 0, s>>>(a);
+cudaError_t launch_extent_stats(const BArgs &a, double *out, int grid, cudaStream_t s) {
+    k_extent_stats<<<grid, 256, 8ull * (a.nj + 1), s>>>(a, out);
     return cudaGetLastError();
 }
 
@@ -1281,14 +1364,18 @@ cudaError_t launch_bcount(const BArgs &a, int nc, cudaStream_t s) {
 }
 
 cudaError_t launch_bscan_blocks_only(const BArgs &a, cudaStream_t s) {
-    k_bscan_blocks<<<1, 1024, 0, s>>>(a);
+    const int nch = (a.nbt + kScanChunk - 1) / kScanChunk;
+    k_bscan_part<<<nch, kScanThreads, 0, s>>>(a, a.scan_part);
+    k_bscan_top<<<1, 1024, 0, s>>>(a, a.scan_part, nch);
+    k_bscan_fill<<<nch, kScanThreads, 0, s>>>(a, a.scan_part);
     return cudaGetLastError();
 }
 
+int bscan_chunks(int nb) { return (nb + kScanChunk - 1) / kScanChunk; }
+
 cudaError_t launch_bscan(const BArgs &a, int nc, cudaStream_t s) {
     k_bscan_ctas<<<(2 * a.nb + 255) / 256, 256, 0, s>>>(a, nc);
-    k_bscan_blocks<<<1, 1024, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_bscan_blocks_only(a, s);
 }
 
 cudaError_t launch_bcount_global(const BArgs &a, int grid, cudaStream_t s) {

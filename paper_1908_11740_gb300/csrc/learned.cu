@@ -24,23 +24,21 @@ namespace sj {
 // ---------------------------------------------------------------------------
 // feat[it][32] of every work item (block with both sides), scaled to the
 // exact entry counts btot.  A block side without a sample gets its entries
-// spread evenly over the 8 buckets.
+// spread evenly over the 8 buckets.  One warp per item, lane q = feature q
+// (side q / 16), so reads and writes are coalesced.
 __global__ void k_features(const unsigned *__restrict__ raw, const unsigned *__restrict__ items,
                            const unsigned *__restrict__ btot, int nb, const Stats *__restrict__ st,
                            float *__restrict__ feat) {
     const unsigned n = st->nchunks;
-    for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x) {
+    const unsigned q = threadIdx.x & 31, side = q >> 4;
+    const unsigned nwarps = gridDim.x * (blockDim.x >> 5);
+    for (unsigned it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < n; it += nwarps) {
         const unsigned b = items[it];
         const unsigned *r = raw + (size_t)b * kRawPerBlock;
-        float *f = feat + (size_t)it * kFeat;
-        for (int side = 0; side < 2; side++) {
-            const float nt = (float)btot[side * nb + b];
-            const unsigned samp = r[32 + side];
-            for (int q = 0; q < 16; q++) {
-                const float h = samp ? (float)r[side * 16 + q] * nt / (float)samp : nt * 0.125f;
-                f[side * 16 + q] = log1pf(h);
-            }
-        }
+        const float nt = (float)btot[side * nb + b];
+        const unsigned samp = r[32 + side];
+        const float h = samp ? (float)r[q] * nt / (float)samp : nt * 0.125f;
+        feat[(size_t)it * kFeat + q] = log1pf(h);
     }
 }
 

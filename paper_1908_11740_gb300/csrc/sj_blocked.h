@@ -70,6 +70,7 @@ struct BArgs {
     int nbt;                    // blocks of all joins (== nb for a single join)
     unsigned *ijoin;            // join of every work item
     unsigned *jfirst;           // first work item of every join (nj + 1)
+    unsigned long long *scan_part;   // block scan: 3 sums per chunk of blocks (bscan_chunks(nbt))
     unsigned *lpool;            // optional: row lists of blocks staged in several bands
     unsigned long long lpool_cap;
     Stats *st;
@@ -101,6 +102,7 @@ cudaError_t launch_join_offsets(const BArgs &a, const unsigned long long *poff, 
                                 cudaStream_t s);
 cudaError_t launch_bscan(const BArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_bscan_blocks_only(const BArgs &a, cudaStream_t s);
+int bscan_chunks(int nb);
 cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, cudaStream_t s);
