@@ -29,6 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1908_11740_gb300 import dist as sjdist  # noqa: E402
 from paper_1908_11740_gb300 import inputs  # noqa: E402
 
 METRIC = "join time and result pairs/s on 1 GB300; learned one-pass vs plain two-pass"
@@ -209,18 +210,12 @@ def ours(args):
 
     from paper_1908_11740_gb300 import build, sj
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    env = sjdist.setup("nccl")
+    world, rank, local = env.world, env.rank, env.local_rank
     torch.cuda.set_device(local)
     build.build()
     # each rank joins its own independent workload (weak scaling)
-    R, S = inputs.gis_pair(args.n_r, args.n_s, seed=args.seed + rank)
+    R, S = inputs.gis_pair(args.n_r, args.n_s, seed=sjdist.instance_seed(args.seed, env))
     hR = torch.from_numpy(R).pin_memory()
     hS = torch.from_numpy(S).pin_memory()
     dR, dS = hR.cuda(), hS.cuda()
@@ -239,8 +234,7 @@ def ours(args):
         for _ in range(max(3, args.warmup)):
             sj.sj_join(ctx, dR, dS, grid, o)
         torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
+        sjdist.barrier(env)
         torch.cuda.synchronize()
         sj.sj_timing_enable(ctx, True)
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -253,8 +247,7 @@ def ours(args):
             del out
         ev1.record(stream)
         torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
+        sjdist.barrier(env)
         tm = sj.sj_timing_read(ctx)
         sj.sj_timing_enable(ctx, False)
         return ev0.elapsed_time(ev1) / steps, tm, npairs
@@ -285,15 +278,7 @@ def ours(args):
             compare[name] = {"ms_per_step": cms, "value": cP / (cms / 1e3), "pairs": cP,
                              "capacity": cl["capacity"] if cl["one_pass"] else None,
                              "refit_blocks": cl["refit_items"] if cl["one_pass"] else None}
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        tp = torch.tensor([float(P)], device="cuda")
-        dist.all_reduce(tp, op=dist.ReduceOp.SUM)
-        p_all = float(tp.item())
-    else:
-        p_all = float(P)
+    ms, p_all = sjdist.reduce_result(ms, P, env)
     value = p_all / (ms / 1e3)
 
     # end to end through the host-buffer entry point (pinned host arrays)
@@ -301,18 +286,14 @@ def ours(args):
     e2e_steps = max(3, min(args.steps, 20))
     for _ in range(2):
         sj.sj_join_host(ctx, hR, hS, grid, hout, opts)
-    if dist:
-        dist.barrier()
+    sjdist.barrier(env)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         res = sj.sj_join_host(ctx, hR, hS, grid, hout, opts)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms, _ = sjdist.reduce_result(e2e_ms, P, env)
     assert res.shape[0] == P
 
     phases = {k: v for k, v in timing.items() if k != "launches" and v[0] > 0}
@@ -368,31 +349,38 @@ def ours(args):
     if model is not None:
         model.free()
     sj.sj_destroy(ctx)
-    if dist:
-        dist.destroy_process_group()
+    sjdist.teardown(env)
 
 
 def batch_arm(args):
-    """256 independent joins (sizes log-uniform in [1e3, 2e6] per side) in
-    one batched pass, grids by the rule of thumb per join."""
+    """256 independent joins (sizes log-uniform in [1e3, 2e6] per side), grids
+    by the rule of thumb per join.  With N ranks the joins are split into N
+    disjoint shards of about equal input size (no data-path collective); each
+    rank joins its shard in one batched call.  Total work is fixed as N grows
+    (strong scaling); value = all pairs / the slowest rank's time."""
     import torch
 
     from paper_1908_11740_gb300 import build, sj
 
+    env = sjdist.setup("nccl")
+    torch.cuda.set_device(env.local_rank)
     build.build()
     joins = inputs.batch_pairs(n_joins=args.joins)
-    Rs = [torch.from_numpy(r).cuda() for r, _ in joins]
-    Ss = [torch.from_numpy(s).cuda() for _, s in joins]
+    mine = sjdist.shard([len(r) + len(s) for r, s in joins], env.rank, env.world)
+    Rs = [torch.from_numpy(joins[j][0]).cuda() for j in mine]
+    Ss = [torch.from_numpy(joins[j][1]).cuda() for j in mine]
     n_in = sum(len(r) + len(s) for r, s in joins)
-    ctx = sj.sj_create(0)
+    ctx = sj.sj_create(env.local_rank)
     pairs, offs = sj.sj_join_batch(ctx, Rs, Ss, None)
     out = torch.empty((int(offs[-1]) + 1, 2), dtype=torch.int32, device="cuda")
     for _ in range(max(3, args.warmup)):
         sj.sj_join_batch(ctx, Rs, Ss, None, out=out)
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(env.local_rank)
     clocks.start()
     time.sleep(0.3)
+    sjdist.barrier(env)
+    torch.cuda.synchronize()
     sj.sj_timing_enable(ctx, True)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -401,22 +389,27 @@ def batch_arm(args):
         sj.sj_join_batch(ctx, Rs, Ss, None, out=out)
     ev1.record(stream)
     torch.cuda.synchronize()
+    sjdist.barrier(env)
     tm = sj.sj_timing_read(ctx)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    P = int(offs[-1])
-    line = {"metric": METRIC + " (batched joins)", "value": P / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{args.joins} independent joins, per-side sizes log-uniform in [1e3, 2e6], "
-                                   f"uniform / mixture centres, log-normal extents median 1e-4",
-                       "rectangles": n_in, "pairs": P, "grids": "rule of thumb per join",
-                       "mode": "batched two-pass, CUDA graphs replayed"},
-            "gpu_launches": tm["launches"], "clocks": clk,
-            "input_gbs": 16 * n_in / (ms / 1e3) / 1e9,
-            "phases_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in tm.items() if k != "launches" and v[0]}}
-    print(json.dumps(line), flush=True)
+    ms, P = sjdist.reduce_result(ev0.elapsed_time(ev1) / args.steps, int(offs[-1]), env)
+    if env.rank == 0:
+        line = {"metric": METRIC + " (batched joins)", "value": P / (ms / 1e3), "unit": UNIT,
+                "n_gpus": env.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{args.joins} independent joins, per-side sizes log-uniform in [1e3, 2e6], "
+                                       f"uniform / mixture centres, log-normal extents median 1e-4",
+                           "rectangles": n_in, "pairs": P, "grids": "rule of thumb per join",
+                           "mode": "batched two-pass, CUDA graphs replayed",
+                           "sharding": "joins split over ranks by input size, no data-path collective"},
+                "gpu_launches": tm["launches"], "clocks": clk,
+                "input_gbs": 16 * n_in / (ms / 1e3) / 1e9,
+                "phases_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in tm.items()
+                                       if k != "launches" and v[0]}}
+        print(json.dumps(line), flush=True)
     sj.sj_destroy(ctx)
+    sjdist.teardown(env)
 
 
 def main():
