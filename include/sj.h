@@ -241,7 +241,9 @@ int  sj_mlp_set_params(sj_ctx *ctx, sj_mlp *m, const float *h_params);
 /* Model -> host: fp32 master parameters, and (if h_inference != NULL) the
  * values inference uses (weights rounded to bf16, as fp32).  Synchronises. */
 int  sj_mlp_get_params(sj_ctx *ctx, const sj_mlp *m, float *h_params, float *h_inference);
-/* d_y[i] = model(d_X[i]) for n rows of SJ_MLP_FEATURES floats (device). */
+/* d_y[i] = model(d_X[i]) for n rows of SJ_MLP_FEATURES floats (device; d_X
+ * 16-byte aligned, else SJ_EINVAL).  Sums in fp32 in a fixed order: the same
+ * bits as the forward pass of sj_mlp_grad. */
 int  sj_mlp_forward(sj_ctx *ctx, const sj_mlp *m, const float *d_X, int64_t n, float *d_y);
 /* Gradient of the mean squared error of the n rows (device d_X, d_Y) with
  * respect to the parameters as inference uses them: d_grad (SJ_MLP_PARAMS

@@ -138,9 +138,11 @@ extern "C" int sj_mlp_get_params(sj_ctx *ctx, const sj_mlp *m, float *h_params, 
             (e = cudaMemcpyAsync(&b3, m->b3, sizeof b3, cudaMemcpyDeviceToHost, ctx->stream)))
             return cuda_fail(ctx, e, "weight download");
         if ((e = cudaStreamSynchronize(ctx->stream))) return cuda_fail(ctx, e, "sync");
-        for (int k = 0; k < kH1 * kFeat; k++) h_inference[kOffW1 + k] = bf16_to_float(w1[k]);
+        // the device keeps W1 and W2 input-major (w1[k][j] = W1[j][k]); the
+        // parameter vector is row-major
+        for (int k = 0; k < kH1 * kFeat; k++) h_inference[kOffW1 + k] = bf16_to_float(w1[(k % kFeat) * kH1 + k / kFeat]);
         for (int k = 0; k < kH1; k++) h_inference[kOffB1 + k] = b1[k];
-        for (int k = 0; k < kH2 * kH1; k++) h_inference[kOffW2 + k] = bf16_to_float(w2[k]);
+        for (int k = 0; k < kH2 * kH1; k++) h_inference[kOffW2 + k] = bf16_to_float(w2[(k % kH1) * kH2 + k / kH1]);
         for (int k = 0; k < kH2; k++) h_inference[kOffB2 + k] = b2[k];
         for (int k = 0; k < kH2; k++) h_inference[kOffW3 + k] = bf16_to_float(w3[k]);
         h_inference[kOffB3] = b3;
@@ -157,12 +159,21 @@ static int mlp_grid(sj_ctx *ctx, int64_t n) {
     return g < 1 ? 1 : (int)g;
 }
 
+// Inference: one thread per sample, 64 per CTA.
+static int mlp_infer_grid(sj_ctx *ctx, int64_t n) {
+    long long g = (n + 63) / 64;
+    const long long cap = (long long)ctx->num_sms * 16;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
 extern "C" int sj_mlp_forward(sj_ctx *ctx, const sj_mlp *m, const float *d_X, int64_t n, float *d_y) {
     if (!ctx || !m || n < 0 || (n && (!d_X || !d_y))) return SJ_EINVAL;
     if (n == 0) return SJ_OK;
+    if (reinterpret_cast<uintptr_t>(d_X) & 15) return fail(ctx, SJ_EINVAL, "d_X must be 16-byte aligned");
     DeviceGuard dg(ctx->device);
     PhaseScope ph(ctx, PH_MODEL, 1);
-    cudaError_t e = launch_mlp_forward(weights_of(m), d_X, n, nullptr, d_y, mlp_grid(ctx, n), ctx->stream);
+    cudaError_t e = launch_mlp_forward(weights_of(m), d_X, n, nullptr, d_y, mlp_infer_grid(ctx, n), ctx->stream);
     return e ? cuda_fail(ctx, e, "mlp forward") : SJ_OK;
 }
 
@@ -245,7 +256,7 @@ extern "C" int sj_block_features(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, co
         if ((st = enqueue_blocked_partition(ctx, w, p, a))) return st;
         {
             PhaseScope ph(ctx, PH_MODEL, 2);
-            if ((e = launch_bfeat_sample(a, ctx->num_sms * 16, ctx->stream))) return cuda_fail(ctx, e, "sampling");
+            if ((e = launch_bfeat_sample(a, ctx->num_sms * 4, ctx->stream))) return cuda_fail(ctx, e, "sampling");
             if ((e = launch_features((const unsigned *)w.bFeatRaw.p, a.items, a.btot, p.nb, a.st,
                                      (float *)w.bFeat.p, ctx->num_sms * 2, ctx->stream)))
                 return cuda_fail(ctx, e, "features");
@@ -337,7 +348,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         unsigned long long *d_cap = (unsigned long long *)w.bCapTot.p;
         {
             PhaseScope ph(ctx, PH_MODEL, 5);
-            if ((e = launch_bfeat_sample(a, ctx->num_sms * 16, s))) return cuda_fail(ctx, e, "sampling");
+            if ((e = launch_bfeat_sample(a, ctx->num_sms * 4, s))) return cuda_fail(ctx, e, "sampling");
             if ((e = launch_features((const unsigned *)w.bFeatRaw.p, a.items, a.btot, p.nb, a.st, (float *)w.bFeat.p,
                                      ctx->num_sms * 8, s)))
                 return cuda_fail(ctx, e, "features");
@@ -346,7 +357,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
                                      ctx->num_sms * 2, s);
             } else {
                 e = launch_mlp_forward(weights_of(ctx->model), (const float *)w.bFeat.p, 0, &a.st->nchunks,
-                                       (float *)w.bPred.p, ctx->num_sms * 8, s);
+                                       (float *)w.bPred.p, mlp_infer_grid(ctx, p.nb), s);
             }
             if (e) return cuda_fail(ctx, e, "prediction");
             if ((e = launch_plan((const float *)w.bPred.p, a.imeta, a.ins, a.st, margin, slack, d_cap,

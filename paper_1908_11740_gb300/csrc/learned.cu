@@ -49,7 +49,7 @@ __global__ void k_features(const unsigned *__restrict__ raw, const unsigned *__r
 // in the forward pass the 32 lanes of a warp compute 32 consecutive units j
 // and read 32 consecutive values; the backward pass (lane = k) walks j from
 // a lane-dependent start, so the lanes again fall in different banks.
-struct MlpSmem {
+struct __align__(16) MlpSmem {
     __nv_bfloat16 w1t[kFeat * kH1];
     __nv_bfloat16 w2t[kH1 * kH2];
     __nv_bfloat16 w3[kH2];
@@ -57,10 +57,13 @@ struct MlpSmem {
 };
 
 __device__ __forceinline__ void mlp_load(MlpSmem &m, const MlpWeights &w) {
-#pragma unroll 8
-    for (int k = threadIdx.x; k < kH1 * kFeat; k += blockDim.x) m.w1t[(k % kFeat) * kH1 + k / kFeat] = w.w1[k];
-#pragma unroll 8
-    for (int k = threadIdx.x; k < kH2 * kH1; k += blockDim.x) m.w2t[(k % kH1) * kH2 + k / kH1] = w.w2[k];
+    // the published weights are input-major already: straight 16-byte copies
+    {
+        const uint4 *s1 = reinterpret_cast<const uint4 *>(w.w1), *s2 = reinterpret_cast<const uint4 *>(w.w2);
+        uint4 *d1 = reinterpret_cast<uint4 *>(m.w1t), *d2 = reinterpret_cast<uint4 *>(m.w2t);
+        for (int k = threadIdx.x; k < kH1 * kFeat / 8; k += blockDim.x) d1[k] = s1[k];
+        for (int k = threadIdx.x; k < kH2 * kH1 / 8; k += blockDim.x) d2[k] = s2[k];
+    }
     for (int k = threadIdx.x; k < kH2; k += blockDim.x) {
         m.w3[k] = w.w3[k];
         m.b2[k] = w.b2[k];
@@ -113,22 +116,94 @@ __device__ __forceinline__ float mlp_warp_forward(const MlpSmem &m, const float 
 constexpr int kMlpThreads = 256;
 constexpr int kMlpWarps = kMlpThreads / 32;
 
-// y[i] = f(X[i]) for i < n (n read from *n_dev when given).
-__global__ void __launch_bounds__(kMlpThreads) k_mlp_forward(MlpWeights w, const float *__restrict__ X,
-                                                             long long n, const unsigned *n_dev,
-                                                             float *__restrict__ y) {
-    __shared__ MlpSmem m;
-    __shared__ float xs[kMlpWarps][kFeat];
-    __shared__ float hs[kMlpWarps][kH1];
+// y[i] = f(X[i]) for i < n (n read from *n_dev when given).  One thread per
+// sample; every warp reads the same weights at the same time (shared-memory
+// broadcasts, 8 bf16 weights per 16-byte load; a bf16 is the high half of
+// the float with the same bits).  The sums run in the order of mlp_warp_forward (k ascending
+// from the bias; the output's partials per lane l = w3[l] h2[l] + w3[l+32]
+// h2[l+32], then halved pairwise like the butterfly), so inference and the
+// training forward give the same bits.
+constexpr int kMlpInfThreads = 64;
+__global__ void __launch_bounds__(kMlpInfThreads) k_mlp_forward(MlpWeights w, const float *__restrict__ X,
+                                                                long long n, const unsigned *n_dev,
+                                                                float *__restrict__ y) {
+    __shared__ __align__(16) MlpSmem m;
+    // this thread's input and hidden layer (rows padded: no bank conflicts)
+    __shared__ float xs[kMlpInfThreads][kFeat + 1];
+    __shared__ float h1s[kMlpInfThreads][kH1 + 1];
     mlp_load(m, w);
     const long long nn = n_dev ? (long long)*n_dev : n;
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (long long i = (long long)blockIdx.x * kMlpWarps + wid; i < nn; i += (long long)gridDim.x * kMlpWarps) {
-        xs[wid][lane] = X[i * kFeat + lane];
-        __syncwarp();
-        const float out = mlp_warp_forward(m, xs[wid], hs[wid], nullptr, nullptr);
-        if (lane == 0) y[i] = out;
-        __syncwarp();
+    float *x = xs[threadIdx.x];
+    float *h1 = h1s[threadIdx.x];
+    for (long long i = (long long)blockIdx.x * kMlpInfThreads + threadIdx.x; i < nn;
+         i += (long long)gridDim.x * kMlpInfThreads) {
+        const float4 *xv = reinterpret_cast<const float4 *>(X + i * kFeat);
+#pragma unroll
+        for (int q = 0; q < kFeat / 4; q++) {
+            const float4 t = xv[q];
+            x[4 * q] = t.x;
+            x[4 * q + 1] = t.y;
+            x[4 * q + 2] = t.z;
+            x[4 * q + 3] = t.w;
+        }
+        {
+            float acc[kH1];
+#pragma unroll
+            for (int j = 0; j < kH1; j++) acc[j] = m.b1[j];
+#pragma unroll 2
+            for (int k = 0; k < kFeat; k++) {
+                const float xk = x[k];
+                const uint4 *row = reinterpret_cast<const uint4 *>(m.w1t + k * kH1);   // 8 weights per load
+#pragma unroll
+                for (int q = 0; q < kH1 / 8; q++) {
+                    const uint4 u = row[q];
+                    const unsigned wd[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                    for (int t = 0; t < 4; t++) {
+                        const int j = 8 * q + 2 * t;
+                        acc[j] = fmaf(__uint_as_float(wd[t] << 16), xk, acc[j]);
+                        acc[j + 1] = fmaf(__uint_as_float(wd[t] & 0xffff0000u), xk, acc[j + 1]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kH1; j++) h1[j] = fmaxf(acc[j], 0.0f);
+        }
+        float part[32];
+#pragma unroll
+        for (int c = 0; c < kH2 / 16; c++) {
+            float acc[16];
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) acc[jj] = m.b2[c * 16 + jj];
+#pragma unroll 4
+            for (int k = 0; k < kH1; k++) {
+                const float hk = h1[k];
+                const uint4 *row = reinterpret_cast<const uint4 *>(m.w2t + k * kH2 + c * 16);
+#pragma unroll
+                for (int q = 0; q < 2; q++) {
+                    const uint4 u = row[q];
+                    const unsigned wd[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                    for (int t = 0; t < 4; t++) {
+                        const int jj = 8 * q + 2 * t;
+                        acc[jj] = fmaf(__uint_as_float(wd[t] << 16), hk, acc[jj]);
+                        acc[jj + 1] = fmaf(__uint_as_float(wd[t] & 0xffff0000u), hk, acc[jj + 1]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < 16; jj++) {
+                const int j = c * 16 + jj;
+                const float t = fmaxf(acc[jj], 0.0f);
+                if (j < 32) part[j] = fmaf(__bfloat162float(m.w3[j]), t, 0.0f);
+                else part[j - 32] = fmaf(__bfloat162float(m.w3[j]), t, part[j - 32]);
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+            for (int l = 0; l < d; l++) part[l] += part[l + d];
+        y[i] = part[0] + m.b3;
     }
 }
 
@@ -234,9 +309,10 @@ __global__ void k_adam(MlpParams p, const float *__restrict__ grad, float lr, fl
 __global__ void k_mlp_publish(MlpParams p, MlpWeights w) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < kParams; k += gridDim.x * blockDim.x) {
         const float v = p.master[k];
-        if (k < kOffB1) w.w1[k - kOffW1] = __float2bfloat16_rn(v);
+        // W1[j][k] (master, row-major) -> w1[k][j] (input-major), W2 alike
+        if (k < kOffB1) w.w1[((k - kOffW1) % kFeat) * kH1 + (k - kOffW1) / kFeat] = __float2bfloat16_rn(v);
         else if (k < kOffW2) w.b1[k - kOffB1] = v;
-        else if (k < kOffB2) w.w2[k - kOffW2] = __float2bfloat16_rn(v);
+        else if (k < kOffB2) w.w2[((k - kOffW2) % kH1) * kH2 + (k - kOffW2) / kH1] = __float2bfloat16_rn(v);
         else if (k < kOffW3) w.b2[k - kOffB2] = v;
         else if (k < kOffB3) w.w3[k - kOffW3] = __float2bfloat16_rn(v);
         else w.b3[0] = v;
@@ -369,7 +445,7 @@ cudaError_t launch_features(const unsigned *raw, const unsigned *items, const un
 
 cudaError_t launch_mlp_forward(const MlpWeights &w, const float *X, long long n, const unsigned *n_dev, float *y,
                                int grid, cudaStream_t s) {
-    k_mlp_forward<<<grid, kMlpThreads, 0, s>>>(w, X, n, n_dev, y);
+    k_mlp_forward<<<grid, kMlpInfThreads, 0, s>>>(w, X, n, n_dev, y);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ constexpr int kOffW3 = kOffB2 + kH2;
 constexpr int kOffB3 = kOffW3 + kH2;
 constexpr int kParams = kOffB3 + 1;   // 6337
 
-struct MlpWeights {               // inference copy: bf16 weights, fp32 biases
+struct MlpWeights {               // inference copy: bf16 weights (w1, w2 input-major), fp32 biases
     __nv_bfloat16 *w1, *w2, *w3;
     float *b1, *b2, *b3;
 };
