@@ -97,7 +97,8 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
                   &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out, &w.bH,
                   &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
                   &w.bResv, &w.bFail, &w.bImeta, &w.bIns, &w.bFeatRaw, &w.bFeat, &w.bPred,
-                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bSpill, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff, &w.bScanPart};
+                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bSpill, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff, &w.bScanPart,
+                  &w.lstart, &w.lcoff, &w.lvb};
     for (Buf *b : all) {
         dev_free(ctx, b->p);
         b->p = nullptr;
@@ -360,6 +361,9 @@ int sj::size_workspace(sj_ctx *ctx, Workspace &w, long long T) {
     if ((st = ensure(ctx, w.val_b, 4ull * (w.items_cap + 1)))) return st;
     if ((st = ensure(ctx, w.lmbr, 16ull * (w.items_cap + 1)))) return st;
     if ((st = ensure(ctx, w.lid, 4ull * (w.items_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.lstart, 4ull * (w.items_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.lcoff, 8ull * (w.items_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.lvb, 32ull * (w.vb_cap + 2)))) return st;
     if ((st = ensure(ctx, w.pc, 4ull * nslots))) return st;
     if ((st = ensure(ctx, w.poff, 8ull * nslots))) return st;
     if ((st = ensure(ctx, w.resv, 8ull * nslots))) return st;
@@ -389,6 +393,16 @@ LargeArgs sj::large_args(Workspace &w) {
     a.lid = (unsigned *)w.lid.p;
     a.items_cap = w.items_cap;
     a.vb_cap = w.vb_cap;
+    if (w.lcoff.p && w.lstart.p && w.lvb.p) {
+        a.lstart = (unsigned *)w.lstart.p;
+        a.lcoff = (unsigned long long *)w.lcoff.p;
+        unsigned long long *v = (unsigned long long *)w.lvb.p;
+        const size_t n = (size_t)w.vb_cap + 2;
+        a.vbc = v;
+        a.vbpairs = v + n;
+        a.vbcur = v + 2 * n;
+        a.vbch = (unsigned *)(v + 3 * n);
+    }
     a.st = (Stats *)w.stats.p;
     return a;
 }
@@ -473,7 +487,8 @@ int sj::enqueue_sweep(sj_ctx *ctx, Workspace &w, int mode, int2 *out, unsigned l
     b.nfail = &((Stats *)w.stats.p)->nfail_large;
     b.work_slot = slot_base + 1;
     {
-        PhaseScope ph(ctx, mode == MODE_WRITE || mode == MODE_RESERVE ? PH_LSWEEP_WRITE : PH_LSWEEP_COUNT, 1);
+        PhaseScope ph(ctx, mode == MODE_WRITE || mode == MODE_RESERVE ? PH_LSWEEP_WRITE : PH_LSWEEP_COUNT,
+                      w.lcoff.p && mode != MODE_RESERVE ? (mode == MODE_COUNT ? 4 : 3) : 1);
         if ((e = launch_sweep_large(mode, large_args(w), b, ctx->num_sms * 4, s)))
             return cuda_fail(ctx, e, "large-tile sweep kernel");
     }

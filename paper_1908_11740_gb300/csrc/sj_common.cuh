@@ -68,6 +68,8 @@ struct Stats {
     int err;
     int need_direct;                    // blocked path: a tile exceeds shared memory
     int pad;
+    unsigned int nlch;                  // candidate chunks of the large-tile sweep
+    unsigned int pad2;
 };
 
 // ---- the cell function (tile index of a coordinate) ------------------------

@@ -34,6 +34,7 @@ struct Workspace {
     Buf bSpill;                                    // one-pass pair spill per block-join CTA
     Buf bJd, bIjoin, bJfirst, bJoff;               // join table (batches: per-join offsets)
     Buf bScanPart;                                 // block scan: sums per chunk of blocks
+    Buf lstart, lcoff, lvb;                        // candidate-parallel sweep of the large tiles
     unsigned long long bcap_r = 0, bcap_s = 0;
     unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
     long long T = 0;

@@ -49,6 +49,13 @@ struct LargeArgs {
     unsigned *key_in, *val_in, *key_out, *val_out;
     float4 *lmbr;                     // sorted entries of the large tiles
     unsigned *lid;
+    // candidate-parallel sweep (optional: all null -> one thread per pivot)
+    unsigned *lstart;                 // first candidate of every pivot (position in the other segment)
+    unsigned long long *lcoff;        // exclusive prefix of the pivots' candidate counts, per virtual block
+    unsigned long long *vbc;          // candidates of every virtual block
+    unsigned long long *vbpairs;      // pairs of every virtual block (count pass)
+    unsigned long long *vbcur;        // write cursor of every virtual block (write pass)
+    unsigned *vbch;                   // first candidate chunk of every virtual block (vb_cap + 1)
     unsigned long long items_cap;
     unsigned vb_cap;
     Stats *st;

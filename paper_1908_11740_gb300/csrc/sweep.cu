@@ -621,6 +621,248 @@ __global__ void __launch_bounds__(256) k_sweep_large(LargeArgs a, SweepArgs o) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Candidate-parallel sweep of the large tiles.  A pivot of a large tile can
+// have millions of candidates (a wide rectangle over a dense tile), so the
+// work is divided by candidates, not by pivots:
+//  1. k_large_ranges (one CTA per virtual block): every pivot's candidate
+//     range [start, end) in the other segment -- the positions the forward
+//     scan of Algorithm 1 visits: x_l in (x_l, x_u] of an R pivot, in
+//     [x_l, x_u] of an S pivot -- and the exclusive prefix of the range
+//     sizes within the virtual block;
+//  2. k_large_plan (one CTA): kCandChunk candidates per chunk, the chunks of
+//     every virtual block and their prefix;
+//  3. k_large_cand: persistent CTAs take chunks; every thread tests its
+//     candidates (y-test, reference-point test of Eq. 1); a chunk's pairs
+//     are counted per virtual block, or collected in shared memory and
+//     written with one atomic on the virtual block's cursor, at the block's
+//     offset from the count pass;
+//  4. k_large_finish (count pass): the per-block counts as 32-bit work-item
+//     counts of the pair scan.
+// ---------------------------------------------------------------------------
+constexpr int kCandChunk = 4096;
+constexpr int kCandThreads = 256;
+
+// Exclusive scan over the NT threads of a block; *total = sum.  Every warp
+// writes only its own slot of s_w before the first barrier, so consecutive
+// calls may share s_w.
+template <int NT, typename T>
+__device__ __forceinline__ T block_scan_ex(T v, T *s_w, T *total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const T o = __shfl_up_sync(kFull, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const T x = lane < NT / 32 ? s_w[lane] : T(0);
+        T xi = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T o = __shfl_up_sync(kFull, xi, d);
+            if (lane >= d) xi += o;
+        }
+        if (lane < NT / 32) s_w[lane] = xi - x;
+        if (lane == NT / 32 - 1) s_w[NT / 32] = xi;
+    }
+    __syncthreads();
+    *total = s_w[NT / 32];
+    return s_w[wid] + inc - v;
+}
+
+// Pivots [q0, q1) of virtual block vb, its segment sg and the other segment's range.
+struct VbRange {
+    unsigned sg, q0, q1;
+    int o0, o1;
+};
+__device__ __forceinline__ VbRange vb_range(const LargeArgs &a, unsigned nseg, unsigned vb) {
+    VbRange r;
+    r.sg = seg_of_vb(a.seg_vb, nseg, vb);
+    const unsigned og = r.sg ^ 1u;
+    r.o0 = (int)a.seg_off[og];
+    r.o1 = (int)a.seg_off[og + 1];
+    r.q0 = a.seg_off[r.sg] + (vb - a.seg_vb[r.sg]) * kRadixBlock;
+    r.q1 = min(a.seg_off[r.sg + 1], r.q0 + kRadixBlock);
+    return r;
+}
+
+__global__ void __launch_bounds__(kCandThreads) k_large_ranges(LargeArgs a) {
+    __shared__ unsigned long long s_w[kCandThreads / 32 + 1];
+    if (block_skip(a.st)) return;
+    const unsigned nvb = min(a.st->nvb, a.vb_cap), nseg = 2 * a.st->nlarge;
+    auto getx = [&](int q) { return a.lmbr[q].x; };
+    for (unsigned vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        const VbRange v = vb_range(a, nseg, vb);
+        const bool isR = (v.sg & 1) == 0;
+        unsigned long long carry = 0;
+        for (unsigned pb = v.q0; pb < v.q1; pb += kCandThreads) {
+            const unsigned p = pb + threadIdx.x;
+            unsigned long long num = 0;
+            if (p < v.q1) {
+                const float4 pv = a.lmbr[p];
+                const int k = isR ? lower_pos<true>(v.o0, v.o1, pv.x, getx) : lower_pos<false>(v.o0, v.o1, pv.x, getx);
+                // end = first x_l > x_u: gallop from k (the range [lo, lo + len) is
+                // known to lie at or below x_u while its last element does), then
+                // search the last interval
+                int lo = k, len = 1;
+                while (lo + len - 1 < v.o1 && getx(lo + len - 1) <= pv.z) {
+                    lo += len;
+                    len <<= 1;
+                }
+                const int e = lower_pos<true>(lo, min(v.o1, lo + len - 1), pv.z, getx);
+                a.lstart[p] = (unsigned)k;
+                num = (unsigned long long)(e - k);
+            }
+            unsigned long long tot;
+            const unsigned long long ex = carry + block_scan_ex<kCandThreads>(num, s_w, &tot);
+            if (p < v.q1) a.lcoff[p] = ex;
+            carry += tot;
+        }
+        if (threadIdx.x == 0) a.vbc[vb] = carry;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_large_plan(LargeArgs a) {
+    __shared__ unsigned long long s_w[33];
+    if (block_skip(a.st)) return;
+    const unsigned nvb = min(a.st->nvb, a.vb_cap);
+    unsigned long long carry = 0;
+    for (unsigned b0 = 0; b0 < nvb; b0 += 1024) {
+        const unsigned vb = b0 + threadIdx.x;
+        unsigned long long ch = 0;
+        if (vb < nvb) {
+            ch = (a.vbc[vb] + kCandChunk - 1) / kCandChunk;
+            a.vbpairs[vb] = 0;
+            a.vbcur[vb] = 0;
+        }
+        unsigned long long tot;
+        const unsigned long long ex = carry + block_scan_ex<1024>(ch, s_w, &tot);
+        if (vb < nvb) a.vbch[vb] = (unsigned)ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        a.vbch[nvb] = (unsigned)carry;
+        a.st->nlch = (unsigned)carry;
+        if (carry > 0xffffffffull) atomicOr(&a.st->err, kErrLargeCap);
+    }
+}
+
+// Last p in [lo, hi] with lcoff[p] <= c (lcoff[lo] <= c).
+__device__ __forceinline__ unsigned cand_owner(const unsigned long long *lcoff, unsigned lo, unsigned hi,
+                                               unsigned long long c) {
+    hi += 1;
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (lcoff[mid] <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kCandThreads) k_large_cand(LargeArgs a, SweepArgs o) {
+    __shared__ int2 s_pairs[kCandChunk];   // MODE_WRITE: the chunk's pairs
+    __shared__ unsigned s_item, s_vb, s_sg, s_pa, s_pb, s_n;
+    __shared__ unsigned long long s_c0, s_c1, s_base;
+    __shared__ unsigned s_red[kCandThreads / 32];
+    if (block_skip(o.st)) return;
+    const unsigned nch = a.st->nlch, nvb = min(a.st->nvb, a.vb_cap), nseg = 2 * a.st->nlarge;
+    const unsigned lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned w = atomicAdd(&o.st->work[o.work_slot], 1u);
+            s_item = w;
+            s_n = 0;
+            if (w < nch) {
+                unsigned lo = 0, hi = nvb;   // the virtual block: last vb with vbch[vb] <= w
+                while (hi - lo > 1) {
+                    const unsigned mid = (lo + hi) >> 1;
+                    if (a.vbch[mid] <= w) lo = mid;
+                    else hi = mid;
+                }
+                const VbRange v = vb_range(a, nseg, lo);
+                const unsigned long long c0 = (unsigned long long)(w - a.vbch[lo]) * kCandChunk;
+                const unsigned long long c1 = min(c0 + (unsigned long long)kCandChunk, a.vbc[lo]);
+                s_vb = lo;
+                s_sg = v.sg;
+                s_c0 = c0;
+                s_c1 = c1;
+                s_pa = cand_owner(a.lcoff, v.q0, v.q1 - 1, c0);
+                s_pb = cand_owner(a.lcoff, s_pa, v.q1 - 1, c1 - 1);
+            }
+        }
+        __syncthreads();
+        if (s_item >= nch) break;
+        const unsigned vb = s_vb, pa = s_pa, pb = s_pb;
+        const bool isR = (s_sg & 1) == 0;
+        const unsigned long long c0 = s_c0, c1 = s_c1;
+        unsigned my = 0;
+        for (unsigned long long cb = c0; cb < c1; cb += kCandThreads) {
+            const unsigned long long c = cb + threadIdx.x;
+            bool hit = false;
+            int2 pr = make_int2(0, 0);
+            if (c < c1) {
+                const unsigned p = cand_owner(a.lcoff, pa, pb, c);
+                const unsigned q = a.lstart[p] + (unsigned)(c - a.lcoff[p]);
+                const float4 pv = a.lmbr[p], ob = a.lmbr[q];
+                if (ob.y <= pv.w && pv.y <= ob.w) {
+                    const unsigned pid = a.lid[p], oid = a.lid[q];
+                    if (reported_here(pid, oid)) {
+                        hit = true;
+                        pr = isR ? make_int2((int)(pid & kIdMask), (int)(oid & kIdMask))
+                                 : make_int2((int)(oid & kIdMask), (int)(pid & kIdMask));
+                    }
+                }
+            }
+            if (MODE == MODE_WRITE) {
+                const unsigned hm = __ballot_sync(kFull, hit);
+                if (hm) {
+                    unsigned pos = 0;
+                    if (lane == (unsigned)(__ffs(hm) - 1)) pos = atomicAdd(&s_n, (unsigned)__popc(hm));
+                    pos = __shfl_sync(kFull, pos, __ffs(hm) - 1) + __popc(hm & lanemask_lt());
+                    if (hit) s_pairs[pos] = pr;
+                }
+            } else {
+                my += hit;
+            }
+        }
+        if (MODE == MODE_WRITE) {
+            __syncthreads();
+            if (threadIdx.x == 0 && s_n)
+                s_base = o.off_in[o.cnt_base + vb] + atomicAdd(&a.vbcur[vb], (unsigned long long)s_n);
+            __syncthreads();
+            const unsigned n = s_n;
+            for (unsigned i = threadIdx.x; i < n; i += kCandThreads) o.out[s_base + i] = s_pairs[i];
+        } else {
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) my += __shfl_xor_sync(kFull, my, d);
+            if (lane == 0) s_red[threadIdx.x >> 5] = my;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned tot = 0;
+                for (int w = 0; w < kCandThreads / 32; w++) tot += s_red[w];
+                if (tot) {
+                    if (MODE == MODE_TILES) atomicAdd(o.tile_pairs + a.large[s_sg >> 1], tot);
+                    else atomicAdd(&a.vbpairs[vb], (unsigned long long)tot);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_large_finish(LargeArgs a, SweepArgs o) {
+    const unsigned nvb = min(a.st->nvb, a.vb_cap);
+    for (unsigned vb = blockIdx.x * blockDim.x + threadIdx.x; vb < nvb; vb += gridDim.x * blockDim.x) {
+        const unsigned long long v = a.vbpairs[vb];
+        if (v > 0xffffffffull) atomicOr(&a.st->err, kErrLargeCap);   // one work item over 2^32 pairs
+        o.cnt_out[o.cnt_base + vb] = (unsigned)v;
+    }
+}
+
 // Exclusive scan of n uint32 pair counts into uint64 offsets; the total goes
 // to st->npairs.  One block of 1024 threads.
 __global__ void __launch_bounds__(1024) k_scan_pairs(const unsigned *__restrict__ cnt, unsigned n,
@@ -708,6 +950,17 @@ cudaError_t launch_large_sort(LargeArgs a, int grid, cudaStream_t s) {
 
 cudaError_t launch_sweep_large(int mode, const LargeArgs &a, const SweepArgs &o, int grid,
                                cudaStream_t s) {
+    if (a.lcoff && !o.list && mode != MODE_RESERVE) {   // candidate-parallel
+        k_large_ranges<<<grid, kCandThreads, 0, s>>>(a);
+        k_large_plan<<<1, 1024, 0, s>>>(a);
+        switch (mode) {
+            case MODE_COUNT: k_large_cand<MODE_COUNT><<<grid, kCandThreads, 0, s>>>(a, o); break;
+            case MODE_WRITE: k_large_cand<MODE_WRITE><<<grid, kCandThreads, 0, s>>>(a, o); break;
+            default: k_large_cand<MODE_TILES><<<grid, kCandThreads, 0, s>>>(a, o); break;
+        }
+        if (mode == MODE_COUNT) k_large_finish<<<grid, 256, 0, s>>>(a, o);
+        return cudaGetLastError();
+    }
     switch (mode) {
         case MODE_COUNT: k_sweep_large<MODE_COUNT><<<grid, 256, 0, s>>>(a, o); break;
         case MODE_WRITE: k_sweep_large<MODE_WRITE><<<grid, 256, 0, s>>>(a, o); break;
