@@ -29,15 +29,27 @@ __global__ void __launch_bounds__(256) k_count(const float4 *__restrict__ R, lon
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            long long i = base + (long long)u * blockDim.x;
-            if (i >= n) break;
-            if (!rect_ok(m[u])) { bad = 1; continue; }
+            const long long i = base + (long long)u * blockDim.x;
+            bool valid = i < n;
+            if (valid && !rect_ok(m[u])) {
+                bad = 1;
+                valid = false;
+            }
             const unsigned side = i >= nR;
-            int cx0 = cell_of(m[u].x, g.x0, g.gx, g.nx), cx1 = cell_of(m[u].z, g.x0, g.gx, g.nx);
-            int cy0 = cell_of(m[u].y, g.y0, g.gy, g.ny), cy1 = cell_of(m[u].w, g.y0, g.gy, g.ny);
+            int cx0 = 0, cx1 = -1, cy0 = 0, cy1 = -1;
+            if (valid) {
+                cx0 = cell_of(m[u].x, g.x0, g.gx, g.nx), cx1 = cell_of(m[u].z, g.x0, g.gx, g.nx);
+                cy0 = cell_of(m[u].y, g.y0, g.gy, g.ny), cy1 = cell_of(m[u].w, g.y0, g.gy, g.ny);
+            }
+            // the first tile: lanes of the warp that hit the same one add with
+            // one atomic (dense tiles would otherwise serialise on one counter)
+            const unsigned long long key =
+                valid ? 2ull * ((unsigned long long)cy0 * (unsigned)g.nx + (unsigned)cx0) + side : ~0ull;
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            if (valid && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(cnt + key, (unsigned)__popc(peers));
             for (int cy = cy0; cy <= cy1; cy++)
                 for (int cx = cx0; cx <= cx1; cx++)
-                    atomicAdd(cnt + 2 * ((long long)cy * g.nx + cx) + side, 1u);
+                    if (cy != cy0 || cx != cx0) atomicAdd(cnt + 2 * ((long long)cy * g.nx + cx) + side, 1u);
         }
     }
     if (bad) atomicOr(&st->err, kErrBadRect);
@@ -232,25 +244,39 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ R, l
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            long long i = base + (long long)u * blockDim.x;
-            if (i >= n) break;
+            const long long i = base + (long long)u * blockDim.x;
             float4 v = m[u];
-            if (!rect_ok(v)) continue;
+            const bool valid = i < n && rect_ok(v);
             v.x = __fadd_rn(v.x, 0.0f);
             v.y = __fadd_rn(v.y, 0.0f);
             v.z = __fadd_rn(v.z, 0.0f);
             v.w = __fadd_rn(v.w, 0.0f);
             const unsigned side = i >= nR;
             const unsigned id = (unsigned)(side ? i - nR : i);
-            int cx0 = cell_of(v.x, g.x0, g.gx, g.nx), cx1 = cell_of(v.z, g.x0, g.gx, g.nx);
-            int cy0 = cell_of(v.y, g.y0, g.gy, g.ny), cy1 = cell_of(v.w, g.y0, g.gy, g.ny);
+            int cx0 = 0, cx1 = -1, cy0 = 0, cy1 = -1;
+            if (valid) {
+                cx0 = cell_of(v.x, g.x0, g.gx, g.nx), cx1 = cell_of(v.z, g.x0, g.gx, g.nx);
+                cy0 = cell_of(v.y, g.y0, g.gy, g.ny), cy1 = cell_of(v.w, g.y0, g.gy, g.ny);
+            }
+            // slots of the first tile: lanes that hit the same tile take
+            // consecutive slots with one atomic on its counter
+            const unsigned long long key =
+                valid ? 2ull * ((unsigned long long)cy0 * (unsigned)g.nx + (unsigned)cx0) + side : ~0ull;
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            const int leader = __ffs(peers) - 1;
+            unsigned first = 0;
+            if (valid && (int)(threadIdx.x & 31) == leader) first = atomicSub(cnt + key, (unsigned)__popc(peers));
+            first = __shfl_sync(0xffffffffu, first, leader);
+            unsigned lt;
+            asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+            const unsigned k0 = first - 1u - (unsigned)__popc(peers & lt);
             float4 *ent = side ? ent_s : ent_r;
             unsigned *idw = side ? id_s : id_r;
             const unsigned long long cap = side ? cap_s : cap_r;
             for (int cy = cy0; cy <= cy1; cy++)
                 for (int cx = cx0; cx <= cx1; cx++) {
                     const long long t = (long long)cy * g.nx + cx;
-                    const unsigned k = atomicSub(cnt + 2 * t + side, 1u) - 1u;
+                    const unsigned k = (cy == cy0 && cx == cx0) ? k0 : atomicSub(cnt + 2 * t + side, 1u) - 1u;
                     const unsigned o = side ? off[t].y : off[t].x;
                     const unsigned long long pos = (unsigned long long)o + k;
                     if (pos < cap) {
