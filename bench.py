@@ -54,8 +54,11 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
                     help="CPU sample: rectangles whose centre has y < frac")
-    ap.add_argument("--workload", default="gis", choices=["gis", "batch"],
-                    help="gis: the 10M x 20M GIS-shaped join (default); batch: 256 joins of uneven size")
+    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew"],
+                    help="gis: the 10M x 20M GIS-shaped join (default); batch: 256 joins of uneven size; "
+                         "skew: the 20M x 20M Zipf extent / skew stress")
+    ap.add_argument("--rho", type=float, default=2.1e-4,
+                    help="skew: probability that S shares R's hot spots (2.1e-4: about 1e9 pairs)")
     ap.add_argument("--joins", type=int, default=256)
     return ap.parse_args()
 
@@ -412,12 +415,76 @@ def batch_arm(args):
     sjdist.teardown(env)
 
 
+def skew_arm(args):
+    """Extent / skew stress: |R| = |S| = 20M, Zipf(1.2) centres on a 1024^2
+    lattice, R extents U[0, 1e-4], S extents U[0, 1e-3], S sharing R's hot
+    spots with probability rho; grid 2000 x 2000.  Hot lattice cells hold
+    millions of entries, so the join runs on the single-level path (global
+    segmented radix sort of the large tiles).  Exact two-pass join: the
+    output is about 8 bytes per pair (8 GB at rho = 2.1e-4)."""
+    import torch
+
+    from paper_1908_11740_gb300 import build, sj
+
+    env = sjdist.setup("nccl")
+    torch.cuda.set_device(env.local_rank)
+    build.build()
+    R, S = inputs.zipf_pair(20_000_000, 20_000_000, seed=sjdist.instance_seed(3, env), rho=args.rho)
+    dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
+    ctx = sj.sj_create(env.local_rank)
+    g = sj.make_grid(2000)
+    o = sj.make_opts("two_pass")
+    for _ in range(max(3, args.warmup)):
+        sj.sj_join(ctx, dR, dS, g, o)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(env.local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    sjdist.barrier(env)
+    sj.sj_timing_enable(ctx, True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 10))
+    ev0.record(stream)
+    for _ in range(steps):
+        out = sj.sj_join(ctx, dR, dS, g, o)
+        P = out.shape[0]
+        del out
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sjdist.barrier(env)
+    tm = sj.sj_timing_read(ctx)
+    clk = clocks.stop()
+    st = sj.sj_last_stats(ctx)
+    ms, P_all = sjdist.reduce_result(ev0.elapsed_time(ev1) / steps, P, env)
+    if env.rank == 0:
+        n_in = 40_000_000
+        E = st["entries_r"] + st["entries_s"]
+        line = {"metric": METRIC + " (extent / skew stress)", "value": P_all / (ms / 1e3), "unit": UNIT,
+                "n_gpus": env.world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"Zipf(1.2) skew |R|=|S|=20M, rho={args.rho}, grid 2000x2000",
+                           "pairs": P, "entries": E, "mode": "two_pass",
+                           "path": "single-level" if st["path"] == 0 else "two-level"},
+                "join_roofline": {"alg_bytes": 16 * n_in + 40 * E + 8 * P,
+                                  "achieved_gbs": (16 * n_in + 40 * E + 8 * P) / (ms / 1e3) / 1e9},
+                "gpu_launches": tm["launches"], "clocks": clk,
+                "phases_ms_per_step": {k: round(v[1] / steps, 4) for k, v in tm.items()
+                                       if k != "launches" and v[0]}}
+        print(json.dumps(line), flush=True)
+    sj.sj_destroy(ctx)
+    sjdist.teardown(env)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
     elif args.workload == "batch":
         batch_arm(args)
+    elif args.workload == "skew":
+        skew_arm(args)
     else:
         ours(args)
 
