@@ -314,6 +314,14 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan_fill(BArgs a, const unsi
         } else if (a.jfirst && b == 0) {
             a.jfirst[0] = idx;
         }
+        // more entries than every tile of the block could hold in shared
+        // memory: some tile exceeds it (each entry covers a tile of its
+        // block), and the join needs the single-level path
+        {
+            const unsigned long long G = (unsigned long long)(a.nj > 1 ? a.jd[lo].G : (a.G > 0 ? a.G : a.jd[0].G));
+            if ((unsigned long long)vr[k] + vs[k] > (unsigned long long)kFineCap * G * G)
+                atomicOr(&a.st->need_direct, 1);
+        }
         if (vr[k] > 0 && vs[k] > 0) {
             a.items[idx] = (unsigned)b;
             a.imeta[idx] = make_uint4((unsigned)b, orr[k], vr[k], oss[k]);
@@ -338,7 +346,7 @@ __global__ void k_join_offsets(BArgs a, const unsigned long long *__restrict__ p
 // block start + this CTA's prefix.
 __global__ void __launch_bounds__(kL1Threads) k_bscatter(BArgs a) {
     extern __shared__ unsigned cur[];   // 2 * NB
-    if (block_skip(a.st)) return;
+    if (block_skip_blocked(a.st)) return;
     const int NB2 = 2 * a.nb;
     const unsigned *row = a.H + (size_t)blockIdx.x * NB2;
     for (int k = threadIdx.x; k < NB2; k += kL1Threads)
@@ -415,7 +423,7 @@ __device__ __forceinline__ int div_gj(int x, const JoinDesc &d) {
 constexpr int kScatterU = 4;
 __global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
     extern __shared__ long long s_jin[];   // nj + 1
-    if (block_skip(a.st)) return;
+    if (block_skip_blocked(a.st)) return;
     for (int j = threadIdx.x; j < a.nj; j += 256) s_jin[j] = a.jd[j].in_off;
     if (threadIdx.x == 0) s_jin[a.nj] = a.jd[a.nj - 1].in_off + a.jd[a.nj - 1].nR + a.jd[a.nj - 1].nS;
     __syncthreads();
@@ -1066,7 +1074,7 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
     __shared__ int s_ok, s_huge;
     __shared__ unsigned long long s_base;
     __shared__ unsigned s_red[kBJThreads / 32];
-    if (block_skip(a.st)) return;
+    if (block_skip_blocked(a.st)) return;
     const unsigned nlist = o.list ? *o.list_n : a.st->nchunks;
     // Thread 0 runs two steps ahead: the work counter is read for item k+2
     // and the (single-load) metadata of item k+1 is gathered while item k is

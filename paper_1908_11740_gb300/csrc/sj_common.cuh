@@ -121,4 +121,16 @@ __device__ __forceinline__ bool block_skip(const Stats *st) {
     return v != 0;
 }
 
+// Same, and also when the two-level path has been found unsuitable (a tile
+// exceeds shared memory): its remaining kernels would be wasted.
+__device__ __forceinline__ bool block_skip_blocked(const Stats *st) {
+    __shared__ int s_skip_b;
+    if (threadIdx.x == 0)
+        s_skip_b = ((*(volatile const int *)&st->err) & kErrFatal) | (*(volatile const int *)&st->need_direct);
+    __syncthreads();
+    const int v = s_skip_b;
+    __syncthreads();
+    return v != 0;
+}
+
 }  // namespace sj
