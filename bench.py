@@ -59,6 +59,8 @@ def parse():
                          "skew: the 20M x 20M Zipf extent / skew stress")
     ap.add_argument("--rho", type=float, default=2.1e-4,
                     help="skew: probability that S shares R's hot spots (2.1e-4: about 1e9 pairs)")
+    ap.add_argument("--skew-grid", type=int, default=500,
+                    help="skew: tiles per axis (500: fastest of 500-3000 on this workload)")
     ap.add_argument("--joins", type=int, default=256)
     return ap.parse_args()
 
@@ -418,10 +420,10 @@ def batch_arm(args):
 def skew_arm(args):
     """Extent / skew stress: |R| = |S| = 20M, Zipf(1.2) centres on a 1024^2
     lattice, R extents U[0, 1e-4], S extents U[0, 1e-3], S sharing R's hot
-    spots with probability rho; grid 2000 x 2000.  Hot lattice cells hold
+    spots with probability rho; grid --skew-grid (500 x 500).  Hot lattice cells hold
     millions of entries, so the join runs on the single-level path (global
     segmented radix sort of the large tiles).  Exact two-pass join: the
-    output is about 8 bytes per pair (8 GB at rho = 2.1e-4)."""
+    output is 8 bytes per pair (7.7 GB at rho = 2.1e-4)."""
     import torch
 
     from paper_1908_11740_gb300 import build, sj
@@ -432,7 +434,7 @@ def skew_arm(args):
     R, S = inputs.zipf_pair(20_000_000, 20_000_000, seed=sjdist.instance_seed(3, env), rho=args.rho)
     dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
     ctx = sj.sj_create(env.local_rank)
-    g = sj.make_grid(2000)
+    g = sj.make_grid(args.skew_grid)
     o = sj.make_opts("two_pass")
     for _ in range(max(3, args.warmup)):
         sj.sj_join(ctx, dR, dS, g, o)
@@ -464,7 +466,7 @@ def skew_arm(args):
                 "n_gpus": env.world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": f"Zipf(1.2) skew |R|=|S|=20M, rho={args.rho}, grid 2000x2000",
+                "config": {"workload": f"Zipf(1.2) skew |R|=|S|=20M, rho={args.rho}, grid {args.skew_grid}x{args.skew_grid}",
                            "pairs": P, "entries": E, "mode": "two_pass",
                            "path": "single-level" if st["path"] == 0 else "two-level"},
                 "join_roofline": {"alg_bytes": 16 * n_in + 40 * E + 8 * P,

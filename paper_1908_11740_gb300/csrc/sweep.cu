@@ -762,95 +762,160 @@ __device__ __forceinline__ unsigned cand_owner(const unsigned long long *lcoff, 
     return lo;
 }
 
+// Same, knowing lcoff[lo] <= c and that the answer is usually near lo:
+// gallop up from lo, then search the last interval.
+__device__ __forceinline__ unsigned cand_owner_from(const unsigned long long *lcoff, unsigned lo, unsigned hi,
+                                                    unsigned long long c) {
+    unsigned step = 1;
+    while (lo < hi) {
+        const unsigned b = min(hi, lo + step);
+        if (lcoff[b] <= c) {
+            lo = b;
+            step <<= 1;
+        } else {
+            return cand_owner(lcoff, lo, b - 1, c);
+        }
+    }
+    return lo;
+}
+
+// CTAs take groups of kCandGroup consecutive chunks from a counter; inside
+// a group, thread 0 walks the virtual blocks and the pivots forward from
+// one chunk to the next instead of searching them anew.
 template <int MODE>
 __global__ void __launch_bounds__(kCandThreads) k_large_cand(LargeArgs a, SweepArgs o) {
     __shared__ int2 s_pairs[kCandChunk];   // MODE_WRITE: the chunk's pairs
-    __shared__ unsigned s_item, s_vb, s_sg, s_pa, s_pb, s_n;
+    __shared__ unsigned s_vb, s_sg, s_pa, s_pb, s_n, s_q0;
     __shared__ unsigned long long s_c0, s_c1, s_base;
+    __shared__ float4 s_pv;
+    __shared__ unsigned s_pid;
     __shared__ unsigned s_red[kCandThreads / 32];
     if (block_skip(o.st)) return;
     const unsigned nch = a.st->nlch, nvb = min(a.st->nvb, a.vb_cap), nseg = 2 * a.st->nlarge;
     const unsigned lane = threadIdx.x & 31;
+    constexpr int kU = 4;   // candidates a thread loads before testing them
+    constexpr unsigned kCandGroup = 8;
+    __shared__ unsigned s_w0;
+    unsigned t_vb = 0xffffffffu, t_q1 = 0, t_sg = 0, t_prev = 0;   // thread 0's walk
     for (;;) {
         if (threadIdx.x == 0) {
-            const unsigned w = atomicAdd(&o.st->work[o.work_slot], 1u);
-            s_item = w;
-            s_n = 0;
-            if (w < nch) {
-                unsigned lo = 0, hi = nvb;   // the virtual block: last vb with vbch[vb] <= w
-                while (hi - lo > 1) {
-                    const unsigned mid = (lo + hi) >> 1;
-                    if (a.vbch[mid] <= w) lo = mid;
-                    else hi = mid;
-                }
-                const VbRange v = vb_range(a, nseg, lo);
-                const unsigned long long c0 = (unsigned long long)(w - a.vbch[lo]) * kCandChunk;
-                const unsigned long long c1 = min(c0 + (unsigned long long)kCandChunk, a.vbc[lo]);
-                s_vb = lo;
-                s_sg = v.sg;
-                s_c0 = c0;
-                s_c1 = c1;
-                s_pa = cand_owner(a.lcoff, v.q0, v.q1 - 1, c0);
-                s_pb = cand_owner(a.lcoff, s_pa, v.q1 - 1, c1 - 1);
-            }
+            s_w0 = atomicAdd(&o.st->work[o.work_slot], 1u) * kCandGroup;
+            t_vb = 0xffffffffu;
         }
         __syncthreads();
-        if (s_item >= nch) break;
-        const unsigned vb = s_vb, pa = s_pa, pb = s_pb;
-        const bool isR = (s_sg & 1) == 0;
-        const unsigned long long c0 = s_c0, c1 = s_c1;
-        unsigned my = 0;
-        for (unsigned long long cb = c0; cb < c1; cb += kCandThreads) {
-            const unsigned long long c = cb + threadIdx.x;
-            bool hit = false;
-            int2 pr = make_int2(0, 0);
-            if (c < c1) {
-                const unsigned p = cand_owner(a.lcoff, pa, pb, c);
-                const unsigned q = a.lstart[p] + (unsigned)(c - a.lcoff[p]);
-                const float4 pv = a.lmbr[p], ob = a.lmbr[q];
-                if (ob.y <= pv.w && pv.y <= ob.w) {
-                    const unsigned pid = a.lid[p], oid = a.lid[q];
-                    if (reported_here(pid, oid)) {
-                        hit = true;
-                        pr = isR ? make_int2((int)(pid & kIdMask), (int)(oid & kIdMask))
-                                 : make_int2((int)(oid & kIdMask), (int)(pid & kIdMask));
+        const unsigned w0 = s_w0;
+        if (w0 >= nch) break;
+        const unsigned w1 = min(nch, w0 + kCandGroup);
+        for (unsigned w = w0; w < w1; w++) {
+            if (threadIdx.x == 0) {
+                s_n = 0;
+                if (t_vb == 0xffffffffu || w >= a.vbch[t_vb + 1]) {   // the next virtual block with chunk w
+                    if (t_vb == 0xffffffffu) {
+                        unsigned lo = 0, hi = nvb;   // last vb with vbch[vb] <= w
+                        while (hi - lo > 1) {
+                            const unsigned mid = (lo + hi) >> 1;
+                            if (a.vbch[mid] <= w) lo = mid;
+                            else hi = mid;
+                        }
+                        t_vb = lo;
+                    } else {
+                        do t_vb++;
+                        while (a.vbch[t_vb + 1] <= w);
+                    }
+                    const VbRange v = vb_range(a, nseg, t_vb);
+                    t_q1 = v.q1;
+                    t_sg = v.sg;
+                    t_prev = v.q0;
+                }
+                const unsigned long long c0 = (unsigned long long)(w - a.vbch[t_vb]) * kCandChunk;
+                const unsigned long long c1 = min(c0 + (unsigned long long)kCandChunk, a.vbc[t_vb]);
+                const unsigned pa = cand_owner_from(a.lcoff, t_prev, t_q1 - 1, c0);
+                const unsigned pb = cand_owner_from(a.lcoff, pa, t_q1 - 1, c1 - 1);
+                t_prev = pb;
+                s_vb = t_vb;
+                s_sg = t_sg;
+                s_c0 = c0;
+                s_c1 = c1;
+                s_pa = pa;
+                s_pb = pb;
+                if (pa == pb) {   // one pivot owns the whole chunk (a heavy pivot): its data once
+                    s_pv = a.lmbr[pa];
+                    s_pid = a.lid[pa];
+                    s_q0 = a.lstart[pa] + (unsigned)(c0 - a.lcoff[pa]);
+                }
+            }
+            __syncthreads();
+            const unsigned vb = s_vb, pa = s_pa, pb = s_pb;
+            const bool isR = (s_sg & 1) == 0;
+            const unsigned long long c0 = s_c0, c1 = s_c1;
+            const unsigned nc = (unsigned)(c1 - c0);   // <= kCandChunk
+            const bool single = pa == pb;
+            unsigned my = 0;
+            for (unsigned jb = 0; jb < nc; jb += kCandThreads * kU) {
+                float4 pv[kU], ob[kU];
+                unsigned pid[kU], oid[kU];
+                bool ok[kU];
+#pragma unroll
+                for (int u = 0; u < kU; u++) {   // loads of kU candidates
+                    const unsigned j = jb + u * kCandThreads + threadIdx.x;
+                    ok[u] = j < nc;
+                    if (!ok[u]) continue;
+                    unsigned q;
+                    if (single) {
+                        pv[u] = s_pv;
+                        pid[u] = s_pid;
+                        q = s_q0 + j;
+                    } else {
+                        const unsigned long long c = c0 + j;
+                        const unsigned p = cand_owner(a.lcoff, pa, pb, c);
+                        q = a.lstart[p] + (unsigned)(c - a.lcoff[p]);
+                        pv[u] = a.lmbr[p];
+                        pid[u] = a.lid[p];
+                    }
+                    ob[u] = a.lmbr[q];
+                    oid[u] = a.lid[q];
+                }
+#pragma unroll
+                for (int u = 0; u < kU; u++) {   // y-test, reference-point test, emission
+                    const bool hit = ok[u] && ob[u].y <= pv[u].w && pv[u].y <= ob[u].w && reported_here(pid[u], oid[u]);
+                    if (MODE == MODE_WRITE) {
+                        const unsigned hm = __ballot_sync(kFull, hit);
+                        if (hm) {
+                            unsigned pos = 0;
+                            if (lane == (unsigned)(__ffs(hm) - 1)) pos = atomicAdd(&s_n, (unsigned)__popc(hm));
+                            pos = __shfl_sync(kFull, pos, __ffs(hm) - 1) + __popc(hm & lanemask_lt());
+                            if (hit)
+                                s_pairs[pos] = isR ? make_int2((int)(pid[u] & kIdMask), (int)(oid[u] & kIdMask))
+                                                   : make_int2((int)(oid[u] & kIdMask), (int)(pid[u] & kIdMask));
+                        }
+                    } else {
+                        my += hit;
                     }
                 }
             }
             if (MODE == MODE_WRITE) {
-                const unsigned hm = __ballot_sync(kFull, hit);
-                if (hm) {
-                    unsigned pos = 0;
-                    if (lane == (unsigned)(__ffs(hm) - 1)) pos = atomicAdd(&s_n, (unsigned)__popc(hm));
-                    pos = __shfl_sync(kFull, pos, __ffs(hm) - 1) + __popc(hm & lanemask_lt());
-                    if (hit) s_pairs[pos] = pr;
-                }
+                __syncthreads();
+                if (threadIdx.x == 0 && s_n)
+                    s_base = o.off_in[o.cnt_base + vb] + atomicAdd(&a.vbcur[vb], (unsigned long long)s_n);
+                __syncthreads();
+                const unsigned n = s_n;
+                for (unsigned i = threadIdx.x; i < n; i += kCandThreads) o.out[s_base + i] = s_pairs[i];
             } else {
-                my += hit;
-            }
-        }
-        if (MODE == MODE_WRITE) {
-            __syncthreads();
-            if (threadIdx.x == 0 && s_n)
-                s_base = o.off_in[o.cnt_base + vb] + atomicAdd(&a.vbcur[vb], (unsigned long long)s_n);
-            __syncthreads();
-            const unsigned n = s_n;
-            for (unsigned i = threadIdx.x; i < n; i += kCandThreads) o.out[s_base + i] = s_pairs[i];
-        } else {
 #pragma unroll
-            for (int d = 16; d > 0; d >>= 1) my += __shfl_xor_sync(kFull, my, d);
-            if (lane == 0) s_red[threadIdx.x >> 5] = my;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned tot = 0;
-                for (int w = 0; w < kCandThreads / 32; w++) tot += s_red[w];
-                if (tot) {
-                    if (MODE == MODE_TILES) atomicAdd(o.tile_pairs + a.large[s_sg >> 1], tot);
-                    else atomicAdd(&a.vbpairs[vb], (unsigned long long)tot);
+                for (int d = 16; d > 0; d >>= 1) my += __shfl_xor_sync(kFull, my, d);
+                if (lane == 0) s_red[threadIdx.x >> 5] = my;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    unsigned tot = 0;
+                    for (int w = 0; w < kCandThreads / 32; w++) tot += s_red[w];
+                    if (tot) {
+                        if (MODE == MODE_TILES) atomicAdd(o.tile_pairs + a.large[s_sg >> 1], tot);
+                        else atomicAdd(&a.vbpairs[vb], (unsigned long long)tot);
+                    }
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
