@@ -8,7 +8,9 @@ written from the paper ("Parallel In-Memory Evaluation of Spatial Joins"):
 * ``pbsm``   -- uniform-grid PBSM with replication, per-tile sort by x_l,
   Algorithm 1 per tile and the reference-point test of Eq. 1 (C);
 * ``tile_counts`` / ``cell`` -- the partitioning counts of Sec. 3.4 step 2;
-* ``features`` / ``mlp``    -- in :mod:`oracle.learned` (numpy, float64).
+* ``features`` / ``mlp``    -- in :mod:`oracle.learned` (numpy, float64);
+* ``dist_brute`` / ``dist_pbsm`` -- the eps-distance join on points of Sec. 1
+  (the definition; squares of side eps joined by PBSM, then refined) (C).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
@@ -71,6 +73,12 @@ def _load():
         lib.orc_cells.argtypes = [P, I64, I, I, F, F, F, F, P]
         lib.orc_tile_counts.restype = None
         lib.orc_tile_counts.argtypes = [P, I64, I, I, F, F, F, F, P]
+        lib.orc_dist_brute.restype = P
+        lib.orc_dist_brute.argtypes = [P, I64, P, I64, F]
+        lib.orc_dist_squares.restype = None
+        lib.orc_dist_squares.argtypes = [P, I64, F, P]
+        lib.orc_dist_pbsm.restype = P
+        lib.orc_dist_pbsm.argtypes = [P, I64, P, I64, F, I, I, F, F, F, F, P]
         _lib = lib
         return lib
 
@@ -162,3 +170,41 @@ def cells(A, nx: int, ny: int | None = None, x0=0.0, y0=0.0, x1=1.0, y1=1.0) -> 
     out = np.zeros((len(A), 4), np.int32)
     lib.orc_cells(A.ctypes.data, len(A), nx, ny, x0, y0, x1, y1, out.ctypes.data)
     return out
+
+
+def _points(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if a.ndim != 2 or a.shape[1] != 2:
+        raise ValueError("points must be float32[n, 2] (x, y)")
+    return a
+
+
+def dist_brute(P, Q, eps: float) -> np.ndarray:
+    """All (i, j) with |P[i] - Q[j]| <= eps, every pair tested (binary64
+    distance in a fixed order); int32[n, 2] sorted."""
+    lib = _load()
+    P, Q = _points(P), _points(Q)
+    return _take(lib, lib.orc_dist_brute(P.ctypes.data, len(P), Q.ctypes.data, len(Q), eps))
+
+
+def dist_squares(P, eps: float) -> np.ndarray:
+    """float32[n, 4]: the square of side eps around every point, widened and
+    rounded outward so that it holds the exact square."""
+    lib = _load()
+    P = _points(P)
+    out = np.zeros((len(P), 4), np.float32)
+    lib.orc_dist_squares(P.ctypes.data, len(P), eps, out.ctypes.data)
+    return out
+
+
+def dist_pbsm(P, Q, eps: float, nx: int, ny: int | None = None, x0: float = 0.0, y0: float = 0.0,
+              x1: float = 1.0, y1: float = 1.0, return_candidates: bool = False):
+    """The paper's route for the eps-distance join: squares of side eps, PBSM
+    on an nx x ny grid, distance test of every intersecting pair."""
+    lib = _load()
+    ny = nx if ny is None else ny
+    P, Q = _points(P), _points(Q)
+    nc = ctypes.c_int64(0)
+    out = _take(lib, lib.orc_dist_pbsm(P.ctypes.data, len(P), Q.ctypes.data, len(Q), eps,
+                                       nx, ny, x0, y0, x1, y1, ctypes.addressof(nc)))
+    return (out, nc.value) if return_candidates else out

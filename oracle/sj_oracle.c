@@ -362,3 +362,88 @@ void orc_cells(const orc_rect *A, int64_t n, int nx, int ny, float x0, float y0,
         out[4 * i + 3] = cell_of(A[i].yu, g.gy0, g.ginvy, ny);
     }
 }
+
+/* ---- epsilon-distance join on point sets (Sec. 1) ---------------------
+ * What it computes: J_eps = {(i,j) : |P[i] - Q[j]| <= eps}, the Euclidean
+ * distance between two float32 points.  The paper notes that an
+ * intersection join answers it: every point becomes a square of side eps
+ * centred on it, the squares are joined, and each intersecting pair is
+ * refined by its distance.
+ *
+ * Readings:
+ *  - The distance test is evaluated in IEEE binary64 in one fixed order:
+ *    dx = x_p - x_q, dy = y_p - y_q, d2 = dx*dx + dy*dy (each operation
+ *    rounded once, no fused multiply-add), accepted when d2 <= eps*eps
+ *    (eps widened to binary64, its square rounded once).  The paper fixes no
+ *    precision; with this order the decision is a plain function of the
+ *    inputs.
+ *  - The square is built so that it holds the exact square of side eps:
+ *    half-width h >= eps/2 * (1 + 2^-21), corners rounded outward to float32
+ *    (one float32 step beyond the nearest value).
+ *    An accepted pair has |dx|, |dy| <= eps * (1 + 2^-50) (binary64 rounding
+ *    error), so its squares intersect: the filter loses no pair.  Wider
+ *    squares only add candidates, which the test removes. */
+typedef struct { float x, y; } orc_point;
+
+static int within_eps(orc_point p, orc_point q, double e2)
+{
+    double dx = (double)p.x - (double)q.x;
+    double dy = (double)p.y - (double)q.y;
+    double d2 = dx * dx + dy * dy;
+    return d2 <= e2;
+}
+
+/* Definition, all pairs. */
+orc_res *orc_dist_brute(const orc_point *P, int64_t nP, const orc_point *Q, int64_t nQ, float eps)
+{
+    orc_res *res = res_new();
+    if (!res) return NULL;
+    double e2 = (double)eps * (double)eps;
+    for (int64_t i = 0; i < nP; i++)
+        for (int64_t j = 0; j < nQ; j++)
+            if (within_eps(P[i], Q[j], e2)) res_push(res, (int32_t)i, (int32_t)j);
+    return res_finish(res);
+}
+
+/* The square around every point (see the readings above). */
+void orc_dist_squares(const orc_point *P, int64_t n, float eps, orc_rect *out)
+{
+    float h = (float)((double)eps * 0.5 * (1.0 + 0x1p-20));
+    h = nextafterf(h, INFINITY);   /* the cast may have rounded down */
+    for (int64_t i = 0; i < n; i++) {
+        out[i].xl = nextafterf(P[i].x - h, -INFINITY);
+        out[i].xu = nextafterf(P[i].x + h, INFINITY);
+        out[i].yl = nextafterf(P[i].y - h, -INFINITY);
+        out[i].yu = nextafterf(P[i].y + h, INFINITY);
+    }
+}
+
+/* The paper's route: squares, PBSM on an nx x ny grid (the filter), then
+ * the distance test of every reported pair.  *ncand (if not NULL) receives
+ * the number of intersecting square pairs. */
+orc_res *orc_dist_pbsm(const orc_point *P, int64_t nP, const orc_point *Q, int64_t nQ, float eps,
+                       int nx, int ny, float x0, float y0, float x1, float y1, int64_t *ncand)
+{
+    orc_rect *sp = (orc_rect *)malloc((size_t)(nP ? nP : 1) * sizeof(orc_rect));
+    orc_rect *sq = (orc_rect *)malloc((size_t)(nQ ? nQ : 1) * sizeof(orc_rect));
+    orc_res *cand = NULL, *res = res_new();
+    if (!sp || !sq || !res) goto fail;
+    orc_dist_squares(P, nP, eps, sp);
+    orc_dist_squares(Q, nQ, eps, sq);
+    cand = orc_pbsm_ex(sp, nP, sq, nQ, nx, ny, x0, y0, x1, y1, NULL, NULL, NULL, NULL);
+    if (!cand || cand->failed) goto fail;
+    if (ncand) *ncand = cand->n;
+    double e2 = (double)eps * (double)eps;
+    for (int64_t k = 0; k < cand->n; k++) {
+        orc_pair c = cand->p[k];
+        if (within_eps(P[c.r], Q[c.s], e2)) res_push(res, c.r, c.s);
+    }
+    free(sp); free(sq);
+    orc_res_free(cand);
+    return res_finish(res);
+fail:
+    free(sp); free(sq);
+    orc_res_free(cand);
+    orc_res_free(res);
+    return NULL;
+}
