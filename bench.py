@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
                     help="CPU sample: rectangles whose centre has y < frac")
-    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew"],
+    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance"],
                     help="gis: the 10M x 20M GIS-shaped join (default); batch: 256 joins of uneven size; "
                          "skew: the 20M x 20M Zipf extent / skew stress")
     ap.add_argument("--rho", type=float, default=2.1e-4,
@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--skew-grid", type=int, default=500,
                     help="skew: tiles per axis (500: fastest of 500-3000 on this workload)")
     ap.add_argument("--joins", type=int, default=256)
+    ap.add_argument("--eps", type=float, default=5e-5, help="distance of the eps-distance join")
+    ap.add_argument("--dist-grid", type=int, default=2000, help="grid of the eps-distance join")
     return ap.parse_args()
 
 
@@ -479,6 +481,101 @@ def skew_arm(args):
     sjdist.teardown(env)
 
 
+def distance_arm(args):
+    """eps-distance join on points (Sec. 1): |P| = 10M, |Q| = 20M points with
+    the GIS-shaped mixture distribution, eps = 5e-5, grid 2000 x 2000 (tiles
+    about ten times eps).  Squares of side eps, the candidate join (the
+    learned one-pass join by default, two-pass timed alongside), binary64
+    distance test and ordered compaction, inputs resident.  The oracle (squares,
+    PBSM, distance test) is timed on a strip of the same workload."""
+    import torch
+
+    from paper_1908_11740_gb300 import build, learn, sj
+
+    env = sjdist.setup("nccl")
+    torch.cuda.set_device(env.local_rank)
+    build.build()
+    P, Q = inputs.gis_points(args.n_r, args.n_s, seed=sjdist.instance_seed(args.seed, env))
+    dP, dQ = torch.from_numpy(P).cuda(), torch.from_numpy(Q).cuda()
+    ctx = sj.sj_create(env.local_rank)
+    model, _ = learn.load(ctx, args.model or learn.DEFAULT_MODEL)
+    sj.sj_set_model(ctx, model)
+    g = sj.make_grid(args.dist_grid)
+    stream = torch.cuda.current_stream()
+
+    def timed(mode, steps):
+        o = sj.make_opts(mode)
+        for _ in range(max(3, args.warmup)):
+            sj.sj_distance_join(ctx, dP, dQ, args.eps, g, o)
+        torch.cuda.synchronize()
+        sjdist.barrier(env)
+        sj.sj_timing_enable(ctx, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            out, nc = sj.sj_distance_join(ctx, dP, dQ, args.eps, g, o, return_candidates=True)
+            npairs = out.shape[0]
+            del out
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sjdist.barrier(env)
+        tm = sj.sj_timing_read(ctx)
+        sj.sj_timing_enable(ctx, False)
+        return ev0.elapsed_time(ev1) / steps, tm, npairs, nc
+
+    clocks = ClockSampler(env.local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    steps = max(1, min(args.steps, 20))
+    ms, tm, npairs, ncand = timed(args.mode, steps)
+    clk = clocks.stop()
+    st = sj.sj_last_stats(ctx)
+    cms, _, cP, _ = timed("two_pass", max(3, steps // 2))
+    assert cP == npairs
+    ms, P_all = sjdist.reduce_result(ms, npairs, env)
+    cpu = None
+    if env.rank == 0 and not args.no_cpu:
+        import oracle
+
+        frac = 0.125
+        p = P[P[:, 1] < frac]
+        q = Q[Q[:, 1] < frac]
+        ny = max(1, int(round(args.dist_grid * frac)))
+        t0 = time.perf_counter()
+        res = oracle.dist_pbsm(p, q, args.eps, args.dist_grid, ny, 0.0, 0.0, 1.0, frac)
+        t = time.perf_counter() - t0
+        cpu = {"value": len(res) / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"single-threaded oracle (squares, PBSM, distance test) on the strip y<{frac}: "
+                         f"{len(p):,} x {len(q):,} points, {len(res):,} pairs, {t:.2f} s"}
+    if env.rank == 0:
+        n_in = args.n_r + args.n_s
+        E = st["l1_entries_r"] + st["l1_entries_s"] if st["path"] == 1 else st["entries_r"] + st["entries_s"]
+        b_alg = 8 * n_in + 40 * E + 8 * npairs
+        peak, _ = load_peaks()
+        line = {"metric": METRIC + " (eps-distance join on points)", "value": P_all / (ms / 1e3), "unit": UNIT,
+                "n_gpus": env.world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": f"eps-distance join, |P|={args.n_r:,} |Q|={args.n_s:,} mixture points, "
+                                       f"eps={args.eps}, grid {args.dist_grid}x{args.dist_grid}",
+                           "pairs": npairs, "candidates": ncand, "mode": args.mode,
+                           "one_pass_capacity": st["capacity"] if st["one_pass"] else None,
+                           "one_pass_refit_blocks": st["refit_items"] if st["one_pass"] else None,
+                           "stored_entries": E,
+                           "path": "two-level" if st["path"] == 1 else "single-level"},
+                "join_roofline": {"alg_bytes": b_alg, "achieved_gbs": b_alg / (ms / 1e3) / 1e9,
+                                  "frac": b_alg / (ms / 1e3) / 1e9 / peak},
+                "compare": {"two_pass": {"ms_per_step": cms, "value": cP / (cms / 1e3)}},
+                "cpu_baseline": cpu, "gpu_launches": tm["launches"], "clocks": clk,
+                "phases_ms_per_step": {k: round(v[1] / steps, 4) for k, v in tm.items()
+                                       if k != "launches" and v[0]}}
+        print(json.dumps(line), flush=True)
+    sj.sj_set_model(ctx, None)
+    model.free()
+    sj.sj_destroy(ctx)
+    sjdist.teardown(env)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -487,6 +584,8 @@ def main():
         batch_arm(args)
     elif args.workload == "skew":
         skew_arm(args)
+    elif args.workload == "distance":
+        distance_arm(args)
     else:
         ours(args)
 

@@ -61,6 +61,7 @@ extern "C" {
 /* ---- plain data types ------------------------------------------------- */
 typedef struct { float xl, yl, xu, yu; } sj_rect;       /* an MBR, Sec. 1        */
 typedef struct { int32_t r, s; } sj_pair;               /* one result of J       */
+typedef struct { float x, y; } sj_point;                /* a point (distance join) */
 
 /* Uniform grid over [x0, x1] x [y0, y1] with nx columns and ny rows (Sec. 2.2;
  * ny = 1 gives vertical stripes, Sec. 3.1).  Tile (col, row) has index
@@ -295,7 +296,7 @@ int sj_last_stats(sj_ctx *ctx, sj_stats *out);
  * context's stream; sj_timing_read synchronises the stream and returns the
  * summed device time of each phase since the last enable/read, with the
  * number of kernel launches.  Phase names: sj_timing_phase_name(i). */
-#define SJ_NPHASE 12
+#define SJ_NPHASE 13
 typedef struct {
     int64_t launches;        /* kernels of this library launched (all phases)  */
     int64_t n[SJ_NPHASE];    /* timed occurrences of each phase                 */
@@ -304,6 +305,44 @@ typedef struct {
 int sj_timing_enable(sj_ctx *ctx, int on);
 int sj_timing_read(sj_ctx *ctx, sj_timing *out);
 const char *sj_timing_phase_name(int phase);
+
+/* ---- eps-distance join on point sets (Sec. 1) ------------------------------- */
+/* All pairs (i, j) with Euclidean distance |P[i] - Q[j]| <= eps.  The paper
+ * (Sec. 1) answers this query with the intersection join: every point is
+ * replaced by a square of side eps centred on it, the squares are joined,
+ * and every intersecting pair is refined by its distance.  Here:
+ *   - the squares are built on the device with half-width eps * (1/2 +
+ *     2^-21) rounded up and corners rounded outward, so each holds the exact
+ *     square of side eps and no pair can be lost to rounding;
+ *   - the squares are joined on grid *g in mode o (as sj_join: the two-level
+ *     or single-level path, two-pass or one-pass), giving the candidates;
+ *   - the distance test runs in IEEE binary64 in a fixed order: dx = x_p -
+ *     x_q, dy = y_p - y_q, d2 = dx*dx + dy*dy, each operation rounded once
+ *     (no fused multiply-add), accepted when d2 <= (double)eps * (double)eps.
+ *     The decision is therefore a fixed function of the float32 inputs.
+ *   d_P, d_Q : device sj_point arrays (8 bytes each, 8-byte aligned), caller-
+ *       owned; 0 <= n < SJ_MAX_N.  Coordinates must be finite, and the
+ *       square corners must stay finite (else SJ_EINVAL from the join).
+ *   eps : 0 <= eps <= 1e18 (eps = 0 keeps coincident points only).
+ *   g, o : the grid of the squares and the join options, as for sj_join.
+ *   d_pairs / npairs : as for sj_join (exact-size buffer from the context's
+ *       allocator, release with sj_free; NULL when there is no pair).
+ *   ncand : if not NULL, receives the number of intersecting square pairs
+ *       (the candidates the distance test examined).
+ * Workspace: 16 bytes per point for the squares, 8 bytes per candidate, and
+ * a bit per candidate.  Synchronises the stream after the candidate join
+ * (as sj_join) and once more to size the output.  Pair order: ascending
+ * candidate order of the filter (unspecified unless o->sort_output). */
+int sj_distance_join(sj_ctx *ctx, const sj_point *d_P, int64_t nP, const sj_point *d_Q, int64_t nQ,
+                     float eps, const sj_grid *g, const sj_opts *o, sj_pair **d_pairs, int64_t *npairs,
+                     int64_t *ncand);
+
+/* As sj_distance_join, writing into a caller-owned device buffer of cap
+ * pairs; SJ_EOVERFLOW (with *npairs = the required count, nothing written)
+ * when it is too small. */
+int sj_distance_join_into(sj_ctx *ctx, const sj_point *d_P, int64_t nP, const sj_point *d_Q, int64_t nQ,
+                          float eps, const sj_grid *g, const sj_opts *o, sj_pair *d_buf, int64_t cap,
+                          int64_t *npairs, int64_t *ncand);
 
 /* ---- a join that allocates nothing --------------------------------------- */
 /* The paper has no counterpart to this entry point; it exists for callers

@@ -94,11 +94,11 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
     Buf *all[] = {&w.stats, &w.cnt, &w.off, &w.bsum, &w.ts, &w.large, &w.ent_r, &w.id_r,
                   &w.ent_s, &w.id_s, &w.seg_off, &w.seg_src, &w.seg_vb, &w.hist, &w.key_a,
                   &w.key_b, &w.val_a, &w.val_b, &w.lmbr, &w.lid, &w.pc, &w.poff, &w.resv,
-                  &w.fail_c, &w.fail_l, &w.sort_tmp, &w.in_r, &w.in_s, &w.out, &w.bH,
+                  &w.fail_c, &w.fail_l, &w.sort_tmp, &w.ps_hist, &w.ps_part, &w.in_r, &w.in_s, &w.out, &w.bH,
                   &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
                   &w.bResv, &w.bFail, &w.bImeta, &w.bIns, &w.bFeatRaw, &w.bFeat, &w.bPred,
                   &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bSpill, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff, &w.bScanPart,
-                  &w.lstart, &w.lcoff, &w.lvb};
+                  &w.lstart, &w.lcoff, &w.lvb, &w.dsq_r, &w.dsq_s, &w.dmask, &w.dcnt, &w.doff, &w.dstats};
     for (Buf *b : all) {
         dev_free(ctx, b->p);
         b->p = nullptr;
@@ -114,7 +114,8 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
 static const char *kPhaseNames[PH_N] = {"reset",        "count",       "scan",
                                         "scatter",      "large_sort",  "sweep_count",
                                         "pair_scan",    "sweep_write", "large_sweep_count",
-                                        "large_sweep_write", "model",  "other"};
+                                        "large_sweep_write", "model",  "other",
+                                        "refine"};
 
 static cudaEvent_t take_event(Timer &t) {
     if (!t.pool.empty()) {
@@ -797,8 +798,8 @@ int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const
     return fail(ctx, SJ_EINTERNAL, "blocked workspace did not converge");
 }
 
-static int join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
-                     int64_t nS, const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs) {
+int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
+                  int64_t nS, const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs) {
     const int mode = o ? o->mode : SJ_TWO_PASS;
     const bool one_pass = (mode == SJ_ONE_PASS || mode == SJ_ONE_PASS_HEUR ||
                            (mode == SJ_AUTO && ctx->mlp_loaded));

@@ -24,7 +24,7 @@ struct Workspace {
     Buf ent_r, id_r, ent_s, id_s;
     Buf seg_off, seg_src, seg_vb, hist, key_a, key_b, val_a, val_b, lmbr, lid;
     Buf pc, poff, resv, fail_c, fail_l;
-    Buf sort_tmp;
+    Buf sort_tmp, ps_hist, ps_part;   // sorted output: ping-pong pairs, digit table, scan parts
     Buf in_r, in_s, out;      // staging of sj_join_host
     // blocked (two-level) path
     Buf bH, bTot, bBoR, bBoS, bItems, bEntR, bEntS, bPc, bPoff, bResv, bFail, bImeta, bIns;
@@ -35,6 +35,7 @@ struct Workspace {
     Buf bJd, bIjoin, bJfirst, bJoff;               // join table (batches: per-join offsets)
     Buf bScanPart;                                 // block scan: sums per chunk of blocks
     Buf lstart, lcoff, lvb;                        // candidate-parallel sweep of the large tiles
+    Buf dsq_r, dsq_s, dmask, dcnt, doff, dstats;   // eps-distance join: squares, refinement
     unsigned long long bcap_r = 0, bcap_s = 0;
     unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
     long long T = 0;
@@ -48,7 +49,7 @@ void batch_release(sj_ctx *ctx);
 // Phases of a join, for the device-side timing of sj_timing_*.
 enum Phase {
     PH_RESET = 0, PH_COUNT, PH_SCAN, PH_SCATTER, PH_LSORT, PH_SWEEP_COUNT, PH_PAIRSCAN,
-    PH_SWEEP_WRITE, PH_LSWEEP_COUNT, PH_LSWEEP_WRITE, PH_MODEL, PH_OTHER, PH_N
+    PH_SWEEP_WRITE, PH_LSWEEP_COUNT, PH_LSWEEP_WRITE, PH_MODEL, PH_OTHER, PH_REFINE, PH_N
 };
 
 struct Timer {
@@ -125,6 +126,9 @@ int enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, const B
 int blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const float4 *R, long long nR,
                             const float4 *S, long long nS, const GridDev &g, Stats *stats, bool *use_direct);
 int check_opts(sj_ctx *ctx, const sj_opts *o);
+// The join of sj_join / sj_join_into / sj_join_host on checked inputs.
+int join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+              const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs);
 int upload_joins(sj_ctx *ctx, Workspace &w, const JoinDesc *h, int nj);
 int upload_single_join(sj_ctx *ctx, Workspace &w, const BArgs &a);
 

@@ -126,6 +126,29 @@ def gis_pair(n_r: int = 10_000_000, n_s: int = 20_000_000, seed: int = 2,
     return out[0], out[1]
 
 
+def gis_points(n_p: int = 10_000_000, n_q: int = 20_000_000, seed: int = 2,
+               background: float = 0.2):
+    """Point sets for the eps-distance join, with the spatial distribution of
+    the GIS-shaped layers: centres from the same 64-component Gaussian
+    mixture (shared by P and Q, truncated to [0,1]^2) plus 20% uniform
+    background.  Returns float32 [n, 2] (x, y) arrays."""
+    world, gp, gq = _streams(seed)
+    mu, sigma = _mixture_world(world)
+    out = []
+    for g, n in ((gp, n_p), (gq, n_q)):
+        cx, cy = _mixture_centres(g, n, mu, sigma, background)
+        out.append(np.stack([cx, cy], 1).astype(np.float32))
+    return out[0], out[1]
+
+
+def lattice_points(n: int, pitch: float, x0: float, y0: float) -> np.ndarray:
+    """n x n points (x0 + i * pitch, y0 + j * pitch), index i * n + j, as
+    float32 [n*n, 2] (exact when pitch and the offsets are binary fractions)."""
+    i = np.arange(n)
+    gx, gy = np.meshgrid(i, i, indexing="ij")
+    return np.stack([x0 + gx.ravel() * pitch, y0 + gy.ravel() * pitch], 1).astype(np.float32)
+
+
 def zipf_pair(n_r: int = 20_000_000, n_s: int = 20_000_000, seed: int = 3,
               rho: float = 0.0, zipf_s: float = 1.2, lattice: int = 1024,
               r_max_extent: float = 1e-4, s_max_extent: float = 1e-3):

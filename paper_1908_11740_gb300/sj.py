@@ -49,7 +49,7 @@ class sj_part_view(ctypes.Structure):
 
 
 class sj_timing(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64), ("n", ctypes.c_int64 * 12), ("ms", ctypes.c_double * 12)]
+    _fields_ = [("launches", ctypes.c_int64), ("n", ctypes.c_int64 * 13), ("ms", ctypes.c_double * 13)]
 
 
 class sj_stats(ctypes.Structure):
@@ -107,6 +107,11 @@ SIGNATURES = [
     ("sj_set_tuning", I32, [P, I32]),
     ("sj_join_batch", I32, [P, I32, P, P, P, P, P, ctypes.POINTER(sj_opts), P, I64, P]),
     ("sj_join_noalloc", I32, [P, I64, P, I64, ctypes.POINTER(sj_grid), P, I64, ctypes.POINTER(I64), P]),
+    ("sj_distance_join", I32, [P, P, I64, P, I64, ctypes.c_float, ctypes.POINTER(sj_grid),
+                               ctypes.POINTER(sj_opts), ctypes.POINTER(P), ctypes.POINTER(I64),
+                               ctypes.POINTER(I64)]),
+    ("sj_distance_join_into", I32, [P, P, I64, P, I64, ctypes.c_float, ctypes.POINTER(sj_grid),
+                                    ctypes.POINTER(sj_opts), P, I64, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
 ]
 
 
@@ -245,6 +250,59 @@ def sj_join_into(ctx: Context, R, S, grid: sj_grid, out: torch.Tensor,
     return n.value
 
 
+def _points(t: torch.Tensor, device) -> tuple[int, int]:
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or t.dim() != 2 or t.shape[1] != 2:
+        raise TypeError("points must be a float32 tensor of shape [n, 2]")
+    if t.device != device:
+        raise ValueError(f"points on {t.device}, context on {device}")
+    if not t.is_contiguous():
+        raise ValueError("points must be contiguous")
+    return (t.data_ptr() if t.shape[0] else 0), int(t.shape[0])
+
+
+def sj_distance_join(ctx: Context, P: torch.Tensor, Q: torch.Tensor, eps: float, grid: sj_grid,
+                     opts: sj_opts | None = None, return_candidates: bool = False):
+    """All (i, j) with |P[i] - Q[j]| <= eps as an int32[n, 2] CUDA tensor;
+    with ``return_candidates`` also the number of intersecting squares."""
+    lib = load()
+    pp, npn = _points(P, ctx.device)
+    pq, nq = _points(Q, ctx.device)
+    out = ctypes.c_void_p()
+    n = ctypes.c_int64()
+    nc = ctypes.c_int64()
+    st = lib.sj_distance_join(ctx.handle, pp, npn, pq, nq, float(eps), ctypes.byref(grid),
+                              ctypes.byref(opts) if opts is not None else None, ctypes.byref(out),
+                              ctypes.byref(n), ctypes.byref(nc))
+    _check(ctx.handle, st)
+    if n.value == 0:
+        res = torch.empty((0, 2), dtype=torch.int32, device=ctx.device)
+    else:
+        res = ctx.allocator.take(out.value)[: 8 * n.value].view(torch.int32).view(n.value, 2)
+    return (res, nc.value) if return_candidates else res
+
+
+def sj_distance_join_into(ctx: Context, P, Q, eps: float, grid: sj_grid, out: torch.Tensor,
+                          opts: sj_opts | None = None) -> int:
+    """Write the pairs within distance eps into ``out`` (int32[cap, 2]);
+    returns their number.  SJError(SJ_EOVERFLOW) with ``required`` when short."""
+    lib = load()
+    pp, npn = _points(P, ctx.device)
+    pq, nq = _points(Q, ctx.device)
+    if out.dtype != torch.int32 or out.dim() != 2 or out.shape[1] != 2 or not out.is_contiguous():
+        raise TypeError("out must be a contiguous int32 tensor of shape [cap, 2]")
+    n = ctypes.c_int64()
+    st = lib.sj_distance_join_into(ctx.handle, pp, npn, pq, nq, float(eps), ctypes.byref(grid),
+                                   ctypes.byref(opts) if opts is not None else None,
+                                   out.data_ptr() if out.numel() else None, int(out.shape[0]),
+                                   ctypes.byref(n), None)
+    if st == SJ_EOVERFLOW:
+        err = SJError(st, load().sj_last_error(ctx.handle).decode())
+        err.required = n.value
+        raise err
+    _check(ctx.handle, st)
+    return n.value
+
+
 def sj_count(ctx: Context, R, S, grid: sj_grid) -> int:
     lib = load()
     pr, nr = _rects(R, ctx.device)
@@ -318,7 +376,7 @@ def sj_timing_read(ctx: Context) -> dict:
     t = sj_timing()
     _check(ctx.handle, lib.sj_timing_read(ctx.handle, ctypes.byref(t)))
     out = {"launches": int(t.launches)}
-    for i in range(12):
+    for i in range(13):
         name = lib.sj_timing_phase_name(i).decode()
         if name:
             out[name] = (int(t.n[i]), float(t.ms[i]))
