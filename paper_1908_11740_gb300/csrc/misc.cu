@@ -38,10 +38,6 @@ cudaError_t launch_reset_counters(Stats *st, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Not yet available: filled in by the sorting source.
-int sort_pairs(sj_ctx *ctx, Workspace &, int2 *, unsigned long long) {
-    return fail(ctx, SJ_EINVAL, "sort_output is not available in this build");
-}
 // Models belong to their creator (sj_mlp_free); the context only forgets its reference.
 void mlp_release(sj_ctx *ctx) {
     ctx->model = nullptr;

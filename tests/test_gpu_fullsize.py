@@ -46,5 +46,8 @@ def test_gis_full_size_exact(sj, data, K):
         if K == 3000:
             host = sj.sj_join_host(ctx, R, S, g).numpy()
             np.testing.assert_array_equal(sorted_pairs(host), want)
+            # sorted on the device: equal to the oracle without a host sort
+            srt = sj.sj_join(ctx, dR, dS, g, sj.make_opts("two_pass", sort_output=True)).cpu().numpy()
+            np.testing.assert_array_equal(srt, want)
     finally:
         sj.sj_destroy(ctx)

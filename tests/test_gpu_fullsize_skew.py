@@ -71,7 +71,11 @@ def test_skew_full_size(sj, ctx, rho):
     key = pairs[:, 0].to(torch.int64) * (1 << 32) + pairs[:, 1].to(torch.int64)
     key, _ = torch.sort(key)
     assert int((key[1:] == key[:-1]).sum().item()) == 0
-    del key
+    # the device-sorted output (sort_output) is exactly this set in (r, s) order
+    srt = sj.sj_join(ctx, dR, dS, g, sj.make_opts("two_pass", sort_output=True))
+    skey = srt[:, 0].to(torch.int64) * (1 << 32) + srt[:, 1].to(torch.int64)
+    assert torch.equal(skey, key)
+    del key, srt, skey
 
     rng = np.random.default_rng(17)
     hx, hy = hottest_cell(R)
