@@ -76,7 +76,10 @@ typedef struct { int32_t nx, ny; float x0, y0, x1, y1; } sj_grid;
 #define SJ_TWO_PASS      0   /* count pairs, allocate exactly, sweep again and write   */
 #define SJ_ONE_PASS      1   /* sweep once into a buffer sized by the learned
                                 per-tile predictor; exact two-pass rerun of the
-                                chunks that do not fit                                 */
+                                chunks that do not fit.  A join that found more
+                                pairs than its plan held scales the capacities of
+                                later joins on the context by the shortfall (+10 %,
+                                at most 8x; reset by sj_set_model)                     */
 #define SJ_ONE_PASS_HEUR 2   /* as SJ_ONE_PASS, sized by the Eq. 2 histogram estimate  */
 #define SJ_AUTO          3   /* SJ_ONE_PASS when a model is loaded, else SJ_TWO_PASS   */
 

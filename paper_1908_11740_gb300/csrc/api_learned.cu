@@ -214,6 +214,7 @@ extern "C" int sj_set_model(sj_ctx *ctx, const sj_mlp *m) {
     if (m && m->ctx != ctx) return fail(ctx, SJ_EINVAL, "model belongs to another context");
     ctx->model = m;
     ctx->mlp_loaded = m != nullptr;
+    ctx->onepass_scale = 1.0f;   // a new model starts uncalibrated
     return SJ_OK;
 }
 
@@ -305,6 +306,25 @@ extern "C" int sj_block_features(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, co
 // ---------------------------------------------------------------------------
 // the one-pass join
 // ---------------------------------------------------------------------------
+// Upward-only calibration of the one-pass capacity.  Blocks reserve their
+// ranges heaviest first until the planned total is used up; every block after
+// that is re-run exactly.  So only the predicted total matters, and a model
+// that meets data unlike its training joins (the squares of the distance
+// join have other extents than the rectangles it learned from) under-sizes
+// every call the same way.  When a join finds more pairs than its plan held,
+// later joins on this context scale their capacities by the shortfall (plus
+// 10 %); when the plan holds more than twice the pairs, the factor decays
+// back towards 1.  Bounded to [1, 8], so that one odd join (or a model that
+// predicts nothing) cannot inflate later buffers without limit.  Exactness
+// never depends on it.
+static void calibrate_capacity(sj_ctx *ctx, unsigned long long P, unsigned long long planned) {
+    const double c = (double)std::max<unsigned long long>(planned, 1);
+    double f = ctx->onepass_scale;
+    if ((double)P > c) f *= 1.1 * (double)P / c;
+    else if (f > 1.0 && 2.0 * (double)P < c) f *= 1.5 * (double)P / c;
+    ctx->onepass_scale = (float)std::min(8.0, std::max(1.0, f));
+}
+
 // Partition (with sampled features) -> predict every block's pairs (model,
 // or the Eq. 2 estimate) -> capacity = sum of ceil(pred * (1 + margin)) + slack,
 // heaviest-first order -> (copy of the capacity to the host overlaps the L1
@@ -318,7 +338,8 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
     if (!heuristic && !ctx->model) return fail(ctx, SJ_EINVAL, "SJ_ONE_PASS needs a model (sj_set_model)");
     BPlan p;
     if (!plan_blocked(ctx, gd, nR, nS, p)) return ONE_PASS_UNSUITED;
-    const float margin = o ? o->margin : 0.25f;
+    // capacity of a block = ceil(pred * (1 + margin) * calibration) + slack
+    const float margin = (o ? 1.0f + o->margin : 1.25f) * ctx->onepass_scale - 1.0f;
     const unsigned slack = 2;
     w.bcap_r = std::max<unsigned long long>(w.bcap_r, (unsigned long long)nR + nR / 8 + 1024);
     w.bcap_s = std::max<unsigned long long>(w.bcap_s, (unsigned long long)nS + nS / 8 + 1024);
@@ -374,6 +395,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         // the capacity reached the host while the write kernel runs
         if ((e = cudaEventSynchronize(ctx->ev_aux))) return cuda_fail(ctx, e, "event sync");
         unsigned long long C = *(volatile unsigned long long *)ctx->h_aux;
+        const unsigned long long planned = C;
         if (os.kind == OutSpec::INTO) {
             C = (unsigned long long)os.cap;
             os.got = (int2 *)os.into;
@@ -424,6 +446,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         }
         const unsigned long long P = stats.npairs;
         *npairs = (int64_t)P;
+        calibrate_capacity(ctx, P, planned);
         ctx->last = sj_stats{};
         ctx->last.path = 1;
         ctx->last.block_side = p.G;

@@ -160,6 +160,7 @@ struct sj_ctx {
     int use_blocked = 1;      // the two-level path when the grid allows it
     int shared_cursors = 1;   // L1 write through shared per-block cursors
     int block_target = 1536;  // L1 entries a block should hold (two-level plan)
+    float onepass_scale = 1.0f;   // one-pass capacity calibration (api_learned.cu), in [1, 8]
     sj_alloc_fn alloc = nullptr;
     sj_free_fn free_fn = nullptr;
     void *user = nullptr;

@@ -209,6 +209,15 @@ def test_full_size_gis_points(sj):
         sj.sj_set_model(c, model)
         got1 = sj.sj_distance_join(c, dP, dQ, 5e-5, g, sj.make_opts("one_pass"))
         np.testing.assert_array_equal(srt(got1), want)
+        first = sj.sj_last_stats(c)
+        # the model learned rectangle joins and under-sizes these squares;
+        # the context's capacity calibration removes the re-runs on later calls
+        for _ in range(2):
+            got1 = sj.sj_distance_join(c, dP, dQ, 5e-5, g, sj.make_opts("one_pass"))
+            np.testing.assert_array_equal(srt(got1), want)
+        st = sj.sj_last_stats(c)
+        assert st["one_pass"] == 1 and st["capacity"] >= len(want), (first, st)
+        assert st["refit_items"] == 0, (first, st)
         sj.sj_set_model(c, None)
         model.free()
     finally:
