@@ -190,6 +190,27 @@ int sj_join_host(sj_ctx *ctx, const sj_rect *h_R, int64_t nR, const sj_rect *h_S
                  const sj_grid *g, const sj_opts *o, sj_pair *h_out, int64_t cap,
                  int64_t *npairs);
 
+/* A sequence of n independent joins from HOST buffers (the serving case: a
+ * stream of host-resident requests).  Join i is R_i join S_i on grid g[i]
+ * with options o, exactly as sj_join_host; the difference is the schedule:
+ * the host -> device copy of join i+1's inputs runs on a second (copy)
+ * stream, into the other of two device staging buffers, while join i runs,
+ * so each join costs about max(copy, join) instead of copy + join.
+ *   h_R[i], h_S[i], nR[i], nS[i] : host rectangles (page-locked memory makes
+ *       the copies asynchronous; pageable memory works but does not overlap)
+ *   g : n grids;  o : options for every join (may be NULL)
+ *   h_out[i], cap[i] : host output of join i, cap[i] pairs
+ *   npairs : host, n values: the pairs of each join (also on SJ_EOVERFLOW)
+ * Every argument is checked before any work.  If a join has more pairs than
+ * its cap, its output is left untouched, the other joins complete, and
+ * SJ_EOVERFLOW is returned.  The staging buffers (16 bytes per rectangle,
+ * twice) and the copy stream belong to the context until sj_destroy.
+ * Synchronises the context's stream (inside each join, as sj_join_host)
+ * and both streams at the end. */
+int sj_join_host_many(sj_ctx *ctx, int n, const sj_rect *const *h_R, const int64_t *nR,
+                      const sj_rect *const *h_S, const int64_t *nS, const sj_grid *g, const sj_opts *o,
+                      sj_pair *const *h_out, const int64_t *cap, int64_t *npairs);
+
 /* ---- tuning ------------------------------------------------------------------ */
 /* Sums of the widths and heights of R and S (device inputs; host out[4] =
  * sum w_R, sum h_R, sum w_S, sum h_S, float64): the statistics behind the

@@ -263,6 +263,7 @@ extern "C" int sj_destroy(sj_ctx *ctx) {
     if (!ctx) return SJ_EINVAL;
     DeviceGuard g(ctx->device);
     batch_release(ctx);
+    hoststream_release(ctx);
     release(ctx, ctx->ws);
     mlp_release(ctx);
     cudaStreamSynchronize(ctx->stream);
@@ -283,6 +284,7 @@ extern "C" int sj_set_allocator(sj_ctx *ctx, sj_alloc_fn alloc, sj_free_fn free_
         return fail(ctx, SJ_EINVAL, "allocator needs both alloc and free (or neither)");
     DeviceGuard g(ctx->device);
     batch_release(ctx);   // cached graphs point into the workspace
+    hoststream_release(ctx);
     release(ctx, ctx->ws);
     mlp_release(ctx);
     ctx->alloc = alloc;
@@ -677,6 +679,8 @@ BArgs sj::blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long 
     a.scan_part = (unsigned long long *)w.bScanPart.p;
     a.jd = (const JoinDesc *)w.bJd.p;   // filled by enqueue_blocked_partition
     a.nj = 1;
+    a.pts = w.in_pts;
+    a.h = w.in_h;
     a.nbt = p.nb;
     a.st = (Stats *)w.stats.p;
     return a;
@@ -719,6 +723,7 @@ int sj::upload_single_join(sj_ctx *ctx, Workspace &w, const BArgs &a) {
     d.bx = a.bx;
     d.by = a.by;
     d.boff = 0;
+    d.h = a.h;
     return upload_joins(ctx, w, &d, 1);
 }
 
@@ -842,6 +847,7 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
             return SJ_OK;
         }
     }
+    if (w.in_pts) return PTS_UNSUITED;   // the single-level path reads rectangles only
     st = partition_and_count(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &stats, true);
     if (st) return st;
     return write_pass(ctx, w, stats, o, os, npairs);

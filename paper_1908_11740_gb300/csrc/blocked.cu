@@ -40,6 +40,7 @@ __device__ __forceinline__ unsigned lanemask_lt_b() {
 // L1 count: per-CTA block histograms (shared memory), slice c of the input.
 // H is CTA-major: H[c * 2NB + side * NB + b].
 // ---------------------------------------------------------------------------
+template <int PTS>
 __global__ void __launch_bounds__(kL1Threads) k_bcount(BArgs a) {
     extern __shared__ unsigned hist[];   // 2 * NB
     const int NB2 = 2 * a.nb;
@@ -55,7 +56,10 @@ __global__ void __launch_bounds__(kL1Threads) k_bcount(BArgs a) {
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const long long i = base + (long long)u * kL1Threads;
-            if (i < i1) m[u] = ld_stream(i < a.nR ? a.R + i : a.S + (i - a.nR));
+            if (i < i1) {
+                if constexpr (PTS) m[u] = load_square(i < a.nR ? a.R : a.S, i < a.nR ? i : i - a.nR, a.h);
+                else m[u] = ld_stream(i < a.nR ? a.R + i : a.S + (i - a.nR));
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
@@ -344,6 +348,7 @@ __global__ void k_join_offsets(BArgs a, const unsigned long long *__restrict__ p
 
 // L1 write: the same slice per CTA as k_bcount; shared cursors start at
 // block start + this CTA's prefix.
+template <int PTS>
 __global__ void __launch_bounds__(kL1Threads) k_bscatter(BArgs a) {
     extern __shared__ unsigned cur[];   // 2 * NB
     if (block_skip_blocked(a.st)) return;
@@ -360,7 +365,10 @@ __global__ void __launch_bounds__(kL1Threads) k_bscatter(BArgs a) {
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const long long i = base + (long long)u * kL1Threads;
-            if (i < i1) m[u] = ld_stream(i < a.nR ? a.R + i : a.S + (i - a.nR));
+            if (i < i1) {
+                if constexpr (PTS) m[u] = load_square(i < a.nR ? a.R : a.S, i < a.nR ? i : i - a.nR, a.h);
+                else m[u] = ld_stream(i < a.nR ? a.R + i : a.S + (i - a.nR));
+            }
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
@@ -421,6 +429,7 @@ __device__ __forceinline__ int div_gj(int x, const JoinDesc &d) {
 // the first blocks, then the stores, so that the DRAM loads and the L2
 // atomic round trips of the kScatterU rectangles overlap.
 constexpr int kScatterU = 4;
+template <int PTS>
 __global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
     extern __shared__ long long s_jin[];   // nj + 1
     if (block_skip_blocked(a.st)) return;
@@ -445,7 +454,10 @@ __global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
             const int side = li >= d.nR;
             idx[u] = (unsigned)(side ? li - d.nR : li) | ((unsigned)side << 31);
             v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (ok[u]) v[u] = ld_stream(side ? d.S + (li - d.nR) : d.R + li);
+            if (ok[u]) {
+                if constexpr (PTS) v[u] = load_square(side ? d.S : d.R, side ? li - d.nR : li, d.h);
+                else v[u] = ld_stream(side ? d.S + (li - d.nR) : d.R + li);
+            }
         }
         unsigned cxp[kScatterU], cyp[kScatterU], key[kScatterU], pos0[kScatterU], peers[kScatterU];
 #pragma unroll
@@ -1273,12 +1285,15 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
 
 // Feature sampling for the learned sizing: rectangles 0, kPhi, 2 kPhi, ... of
 // each side add their bucket ranges to every block they overlap.
+template <int PTS>
 __global__ void __launch_bounds__(256) k_bfeat_sample(BArgs a) {
     const long long mr = (a.nR + kPhi - 1) / kPhi, ms = (a.nS + kPhi - 1) / kPhi;
     for (long long k = blockIdx.x * 256ll + threadIdx.x; k < mr + ms; k += 256ll * gridDim.x) {
         const int side = k >= mr;
         const long long i = (side ? k - mr : k) * kPhi;
-        const float4 v = ld_stream(side ? a.S + i : a.R + i);
+        float4 v;
+        if constexpr (PTS) v = load_square(side ? a.S : a.R, i, a.h);
+        else v = ld_stream(side ? a.S + i : a.R + i);
         if (!rect_ok(v)) continue;
         const int cx0 = cell_of(v.x, a.g.x0, a.g.gx, a.g.nx), cx1 = cell_of(v.z, a.g.x0, a.g.gx, a.g.nx);
         const int cy0 = cell_of(v.y, a.g.y0, a.g.gy, a.g.ny), cy1 = cell_of(v.w, a.g.y0, a.g.gy, a.g.ny);
@@ -1330,7 +1345,8 @@ __global__ void __launch_bounds__(256) k_extent_stats(BArgs a, double *__restric
 
 // ---- launchers -------------------------------------------------------------
 cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s) {
-    k_bfeat_sample<<<grid, 256, 0, s>>>(a);
+    if (a.pts) k_bfeat_sample<1><<<grid, 256, 0, s>>>(a);
+    else k_bfeat_sample<0><<<grid, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1349,8 +1365,10 @@ cudaError_t blocked_setup() {
     if ((e = cudaFuncSetAttribute(k_bjoin<MODE_RESERVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
     if ((e = cudaFuncSetAttribute(k_bjoin<MODE_TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
     const int l1 = 8 * kMaxBlocks;
-    if ((e = cudaFuncSetAttribute(k_bcount, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
-    if ((e = cudaFuncSetAttribute(k_bscatter, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
+    if ((e = cudaFuncSetAttribute(k_bcount<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
+    if ((e = cudaFuncSetAttribute(k_bcount<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
+    if ((e = cudaFuncSetAttribute(k_bscatter<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
+    if ((e = cudaFuncSetAttribute(k_bscatter<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
     return cudaSuccess;
 }
 
@@ -1362,12 +1380,13 @@ int bjoin_blocks_per_sm() {
 
 int l1_blocks_per_sm(int nb_blocks) {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bscatter, kL1Threads, 8ull * nb_blocks);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bscatter<0>, kL1Threads, 8ull * nb_blocks);
     return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_bcount(const BArgs &a, int nc, cudaStream_t s) {
-    k_bcount<<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
+    if (a.pts) k_bcount<1><<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
+    else k_bcount<0><<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -1398,8 +1417,13 @@ cudaError_t launch_join_offsets(const BArgs &a, const unsigned long long *poff, 
 }
 
 cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s) {
-    if (a.cur) k_bscatter_shared<<<nc * 8, 256, 8ull * (a.nj + 1), s>>>(a);
-    else k_bscatter<<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
+    if (a.cur) {
+        if (a.pts) k_bscatter_shared<1><<<nc * 8, 256, 8ull * (a.nj + 1), s>>>(a);
+        else k_bscatter_shared<0><<<nc * 8, 256, 8ull * (a.nj + 1), s>>>(a);
+    } else {
+        if (a.pts) k_bscatter<1><<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
+        else k_bscatter<0><<<nc, kL1Threads, 8ull * a.nb, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

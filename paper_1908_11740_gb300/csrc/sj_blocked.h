@@ -45,6 +45,7 @@ struct JoinDesc {
     int bx, by;             // blocks per axis
     int boff;               // first global block id
     int pad;
+    float h;                // point inputs (BArgs::pts): half-width of their squares
 };
 
 struct BArgs {
@@ -73,8 +74,22 @@ struct BArgs {
     unsigned long long *scan_part;   // block scan: 3 sums per chunk of blocks (bscan_chunks(nbt))
     unsigned *lpool;            // optional: row lists of blocks staged in several bands
     unsigned long long lpool_cap;
+    int pts;                    // 1: R, S hold float2 points, read as squares of half-width h
+    float h;
     Stats *st;
 };
+
+// Point i of one side read as its square (the point inputs of the distance
+// join): half-width h around the point, corners rounded outward.  The
+// kernels that read inputs take it when their template parameter PTS is 1;
+// with PTS = 0 they keep the plain rectangle load.
+__device__ __forceinline__ float4 load_square(const float4 *base, long long i, float h) {
+    float2 p;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0,%1}, [%2];"
+                 : "=f"(p.x), "=f"(p.y)
+                 : "l"(reinterpret_cast<const float2 *>(base) + i));
+    return make_float4(__fsub_rd(p.x, h), __fsub_rd(p.y, h), __fadd_ru(p.x, h), __fadd_ru(p.y, h));
+}
 
 struct BJoinOut {
     int work_slot;

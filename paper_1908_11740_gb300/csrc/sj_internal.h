@@ -41,10 +41,15 @@ struct Workspace {
     long long T = 0;
     unsigned nch_cap = 0, nl_cap = 0, vb_cap = 0;
     unsigned long long items_cap = 0;
+    // point inputs (the distance join): R, S of the current join are float2
+    // points that the two-level kernels read as squares of half-width in_h
+    int in_pts = 0;
+    float in_h = 0.0f;
 };
 
 struct MlpState;   // learned per-tile result-count predictor (mlp.cu)
 void batch_release(sj_ctx *ctx);
+void hoststream_release(sj_ctx *ctx);
 
 // Phases of a join, for the device-side timing of sj_timing_*.
 enum Phase {
@@ -94,6 +99,9 @@ struct OutSpec;
 // returned by join_one_pass_spec when the grid or the data do not suit the
 // two-level path; the caller then runs the exact two-pass join
 constexpr int ONE_PASS_UNSUITED = -1;
+// returned by join_core for point inputs when the two-level path does not
+// suit the data (the caller then materialises the squares)
+constexpr int PTS_UNSUITED = -2;
 int join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S, long long nS,
                        const GridDev &gd, const sj_opts *o, int heuristic, OutSpec &os, int64_t *npairs,
                        sj_pair **lib_out);
@@ -150,6 +158,7 @@ struct PhaseScope {
 }  // namespace sj
 
 struct sj_batch_state;
+struct sj_hoststream_state;
 
 struct sj_ctx {
     int device = 0;
@@ -175,6 +184,7 @@ struct sj_ctx {
     void *h_jd = nullptr;               // pinned: join table staging (kMaxJoins)
     void *h_joff = nullptr;             // pinned: per-join pair offsets of a batch
     sj_batch_state *batch = nullptr;    // internal stream and cached graphs of sj_join_batch
+    sj_hoststream_state *hs = nullptr;  // copy stream and staging of sj_join_host_many
     cudaEvent_t ev_aux = nullptr;
     char msg[512];
 };

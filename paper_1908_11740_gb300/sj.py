@@ -107,6 +107,7 @@ SIGNATURES = [
     ("sj_set_tuning", I32, [P, I32]),
     ("sj_join_batch", I32, [P, I32, P, P, P, P, P, ctypes.POINTER(sj_opts), P, I64, P]),
     ("sj_join_noalloc", I32, [P, I64, P, I64, ctypes.POINTER(sj_grid), P, I64, ctypes.POINTER(I64), P]),
+    ("sj_join_host_many", I32, [P, I32, P, P, P, P, P, ctypes.POINTER(sj_opts), P, P, P]),
     ("sj_distance_join", I32, [P, P, I64, P, I64, ctypes.c_float, ctypes.POINTER(sj_grid),
                                ctypes.POINTER(sj_opts), ctypes.POINTER(P), ctypes.POINTER(I64),
                                ctypes.POINTER(I64)]),
@@ -324,6 +325,43 @@ def sj_tile_stats(ctx: Context, R, S, grid: sj_grid):
     _check(ctx.handle, lib.sj_tile_stats(ctx.handle, pr, nr, ps, ns, ctypes.byref(grid),
                                          cr.data_ptr(), cs.data_ptr(), tp.data_ptr()))
     return cr, cs, tp
+
+
+def sj_join_host_many(ctx: Context, Rs, Ss, grids, outs, opts: sj_opts | None = None) -> list[int]:
+    """Join the host arrays (Rs[i], Ss[i]) on grids[i] one after the other,
+    each join's input copy overlapping the previous join; the pairs of join i
+    go to outs[i] (CPU int32[cap_i, 2] tensors, ideally pinned).  Returns the
+    pair counts.  SJError(SJ_EOVERFLOW) carries ``required`` (all counts)."""
+    lib = load()
+    n = len(Rs)
+    if not (len(Ss) == len(grids) == len(outs) == n):
+        raise ValueError("Rs, Ss, grids and outs must have the same length")
+    keep = []
+
+    def host(a, cols, dtype):
+        if not isinstance(a, torch.Tensor) or a.device.type != "cpu" or a.dtype != dtype or a.dim() != 2 \
+                or a.shape[1] != cols or not a.is_contiguous():
+            raise TypeError(f"host arrays must be contiguous CPU {dtype} tensors [n, {cols}]")
+        keep.append(a)
+        return a.data_ptr() if a.shape[0] else None, a.shape[0]
+
+    P = ctypes.c_void_p
+    pr, nr, ps, ns, po, cp = (P * n)(), (ctypes.c_int64 * n)(), (P * n)(), (ctypes.c_int64 * n)(), (P * n)(), \
+        (ctypes.c_int64 * n)()
+    for i in range(n):
+        pr[i], nr[i] = host(Rs[i], 4, torch.float32)
+        ps[i], ns[i] = host(Ss[i], 4, torch.float32)
+        po[i], cp[i] = host(outs[i], 2, torch.int32)
+    g = (sj_grid * n)(*grids)
+    counts = (ctypes.c_int64 * n)()
+    st = lib.sj_join_host_many(ctx.handle, n, pr, nr, ps, ns, g, ctypes.byref(opts) if opts is not None else None,
+                               po, cp, counts)
+    if st == SJ_EOVERFLOW:
+        err = SJError(st, lib.sj_last_error(ctx.handle).decode())
+        err.required = list(counts)
+        raise err
+    _check(ctx.handle, st)
+    return list(counts)
 
 
 def sj_join_host(ctx: Context, R, S, grid: sj_grid, out=None, opts: sj_opts | None = None):

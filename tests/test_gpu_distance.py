@@ -116,6 +116,30 @@ def test_duplicates_and_dense_tiles(sj, ctx):
         np.testing.assert_array_equal(srt(got), want)
 
 
+def test_path_points_on_the_fly_and_materialised(sj, ctx):
+    """The two-level path reads the points and forms the squares as it loads
+    them; a tile beyond shared memory sends the join to the single-level
+    path, which gets materialised squares.  Both give the oracle's set."""
+    P, Q = inputs.gis_points(100_000, 150_000, seed=44)
+    want = oracle.dist_pbsm(P, Q, 5e-4, 200)
+    got, _ = gpu_dist(sj, ctx, P, Q, 5e-4, 400)
+    assert sj.sj_last_stats(ctx)["path"] == 1
+    np.testing.assert_array_equal(srt(got), want)
+    rng = np.random.default_rng(45)
+    base = rng.random((12, 2)).astype(np.float32)
+    Ph = np.concatenate([base[rng.integers(0, 12, 60_000)], P[:20_000]])
+    Qh = np.concatenate([base[rng.integers(0, 12, 40_000)], Q[:20_000]])
+    for mode in ("two_pass", "one_pass_heur"):
+        want = oracle.dist_pbsm(Ph, Qh, 2e-3, 50)
+        got, _ = gpu_dist(sj, ctx, Ph, Qh, 2e-3, 64, mode=mode)
+        assert sj.sj_last_stats(ctx)["path"] == 0
+        np.testing.assert_array_equal(srt(got), want)
+    # the context's next rectangle join reads rectangles again
+    R, S = inputs.gis_pair(30_000, 40_000, seed=46)
+    got = sj.sj_join(ctx, dev(R), dev(S), sj.make_grid(100))
+    np.testing.assert_array_equal(srt(got), oracle.pbsm(R, S, 100))
+
+
 def test_tiny_and_negative_coordinates(sj, ctx):
     rng = np.random.default_rng(12)
     P = np.concatenate([rng.random((300, 2)) * 1e-30, -rng.random((300, 2)) * 1e-3,
