@@ -353,8 +353,8 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         cudaError_t e;
         {
             PhaseScope ph(ctx, PH_RESET, 0);
-            if ((e = cudaMemsetAsync(w.stats.p, 0, sizeof(Stats), s)) ||
-                (e = cudaMemsetAsync(w.bFeatRaw.p, 0, 4ull * kRawPerBlock * p.nb, s)))
+            if ((e = zero_words_async(w.stats.p, sizeof(Stats), s)) ||
+                (e = zero_words_async(w.bFeatRaw.p, 4ull * kRawPerBlock * p.nb, s)))
                 return cuda_fail(ctx, e, "memset");
         }
         if ((st = upload_single_join(ctx, w, a))) return st;
@@ -384,7 +384,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
             if ((e = launch_plan((const float *)w.bPred.p, a.imeta, a.ins, a.st, margin, slack, d_cap,
                                  (unsigned *)w.bOrder.p, ctx->num_sms, s)))
                 return cuda_fail(ctx, e, "plan");
-            if ((e = cudaMemcpyAsync(ctx->h_aux, d_cap, 8, cudaMemcpyDeviceToHost, s)) ||
+            if ((e = copy_words_async(ctx->h_aux, d_cap, 8, s)) ||
                 (e = cudaEventRecord(ctx->ev_aux, s)))
                 return cuda_fail(ctx, e, "capacity copy");
         }

@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 
 #include "sj_learned.h"
+#include "sj_kernels.h"
 
 namespace sj {
 
@@ -476,7 +477,7 @@ cudaError_t launch_heur_pred(const float *feat, const unsigned *items, const uns
 // histogram and cursors.  grid: CTAs of 256 over the items.
 cudaError_t launch_plan(const float *pred, const uint4 *imeta, const unsigned *ins, const Stats *st, float margin,
                         unsigned slack, unsigned long long *cap_total, unsigned *order, int grid, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(cap_total, 0, kPlanScratch, s);
+    cudaError_t e = zero_words_async(cap_total, kPlanScratch, s);
     if (e) return e;
     unsigned *scratch = reinterpret_cast<unsigned *>(cap_total + 1);
     k_plan_count<<<grid, 256, 0, s>>>(pred, imeta, ins, st, margin, slack, cap_total, scratch);

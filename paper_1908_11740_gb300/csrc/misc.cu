@@ -22,6 +22,37 @@ cudaError_t launch_tile_counts(const uint2 *off, long long T, unsigned *cnt_r, u
     return cudaGetLastError();
 }
 
+__global__ void k_zero_words(unsigned *__restrict__ p, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = 0u;
+}
+
+__global__ void k_copy_words(const unsigned *__restrict__ src, unsigned *__restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+static unsigned words_grid(size_t n) {
+    const size_t g = (n + 255) / 256;
+    return (unsigned)(g < 1024 ? (g ? g : 1) : 1024);
+}
+
+static_assert(sizeof(Stats) % 4 == 0 && sizeof(JoinDesc) % 4 == 0, "word-wise copies");
+
+cudaError_t zero_words_async(void *p, size_t bytes, cudaStream_t s) {
+    const size_t n = bytes / 4;
+    if (!n) return cudaSuccess;
+    k_zero_words<<<words_grid(n), 256, 0, s>>>((unsigned *)p, n);
+    return cudaGetLastError();
+}
+
+cudaError_t copy_words_async(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    const size_t n = bytes / 4;
+    if (!n) return cudaSuccess;
+    k_copy_words<<<words_grid(n), 256, 0, s>>>((const unsigned *)src, (unsigned *)dst, n);
+    return cudaGetLastError();
+}
+
 // Clear the per-call counters of a partition's stats, keep its totals.
 __global__ void k_reset_counters(Stats *st) {
     if (threadIdx.x == 0) {

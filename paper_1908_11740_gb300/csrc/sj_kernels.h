@@ -9,6 +9,17 @@
 
 namespace sj {
 
+// Stream-ordered zeroing and small copies done by the SMs instead of a copy
+// engine (misc.cu).  A join issues them between its kernels; a copy engine
+// that is busy with a large transfer on another stream (the next join's
+// inputs in sj_join_host_many) would hold them, and with them the join,
+// until that transfer ends.  bytes: a multiple of 4; pointers 4-byte
+// aligned; either side of a copy may be page-locked host memory, which the
+// device reaches directly (its writes are visible to the host once the
+// kernel has completed, e.g. after a stream or event synchronisation).
+cudaError_t zero_words_async(void *p, size_t bytes, cudaStream_t s);
+cudaError_t copy_words_async(void *dst, const void *src, size_t bytes, cudaStream_t s);
+
 enum { MODE_COUNT = 0, MODE_WRITE = 1, MODE_RESERVE = 2, MODE_TILES = 3 };
 
 // Arguments of the sweep kernels (small-tile chunks and large tiles).
