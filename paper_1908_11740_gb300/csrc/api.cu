@@ -436,8 +436,8 @@ int sj::enqueue_partition(sj_ctx *ctx, Workspace &w, const float4 *R, long long 
     Stats *st = (Stats *)w.stats.p;
     {
         PhaseScope ph(ctx, PH_RESET, 0);
-        if ((e = zero_words_async(w.stats.p, sizeof(Stats), s))) return cuda_fail(ctx, e, "memset");
-        if ((e = zero_words_async(w.cnt.p, 8ull * w.T, s))) return cuda_fail(ctx, e, "memset");
+        if ((e = zero_async(ctx, w.stats.p, sizeof(Stats)))) return cuda_fail(ctx, e, "memset");
+        if ((e = zero_async(ctx, w.cnt.p, 8ull * w.T))) return cuda_fail(ctx, e, "memset");
     }
     const int grid_stream = ctx->num_sms * 8;
     const bool any = nR + nS > 0;
@@ -500,7 +500,7 @@ int sj::enqueue_sweep(sj_ctx *ctx, Workspace &w, int mode, int2 *out, unsigned l
 
 int sj::read_stats(sj_ctx *ctx, Workspace &w, Stats *out) {
     cudaError_t e;
-    if ((e = copy_words_async(ctx->h_stats, w.stats.p, sizeof(Stats), ctx->stream)))
+    if ((e = copy_async(ctx, ctx->h_stats, w.stats.p, sizeof(Stats))))
         return cuda_fail(ctx, e, "stats copy");
     if ((e = cudaStreamSynchronize(ctx->stream))) return cuda_fail(ctx, e, "stream sync");
     memcpy(out, ctx->h_stats, sizeof(Stats));
@@ -523,7 +523,7 @@ int sj::partition_and_count(sj_ctx *ctx, Workspace &w, const float4 *R, long lon
         if (count_pass) {
             cudaError_t e;
             const unsigned nslots = w.nch_cap + w.vb_cap;
-            if ((e = zero_words_async(w.pc.p, 4ull * nslots, ctx->stream)))
+            if ((e = zero_async(ctx, w.pc.p, 4ull * nslots)))
                 return cuda_fail(ctx, e, "memset");
             if ((st = enqueue_sweep(ctx, w, MODE_COUNT, nullptr, 0, nullptr, nullptr, 0))) return st;
             PhaseScope ph(ctx, PH_PAIRSCAN, 1);
@@ -704,7 +704,7 @@ int sj::upload_joins(sj_ctx *ctx, Workspace &w, const JoinDesc *h, int nj) {
     int st = ensure(ctx, w.bJd, sizeof(JoinDesc) * (nj + 1));
     if (st) return st;
     memcpy(ctx->h_jd, h, sizeof(JoinDesc) * nj);
-    cudaError_t e = copy_words_async(w.bJd.p, ctx->h_jd, sizeof(JoinDesc) * nj, ctx->stream);
+    cudaError_t e = copy_async(ctx, w.bJd.p, ctx->h_jd, sizeof(JoinDesc) * nj);
     return e ? cuda_fail(ctx, e, "join table copy") : SJ_OK;
 }
 
@@ -736,8 +736,8 @@ int sj::enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, con
     }
     {
         PhaseScope ph(ctx, PH_RESET, 0);
-        if ((e = zero_words_async(w.stats.p, sizeof(Stats), s))) return cuda_fail(ctx, e, "memset");
-        if ((e = zero_words_async(w.bPc.p, 4ull * (p.nb + 1), s))) return cuda_fail(ctx, e, "memset");
+        if ((e = zero_async(ctx, w.stats.p, sizeof(Stats)))) return cuda_fail(ctx, e, "memset");
+        if ((e = zero_async(ctx, w.bPc.p, 4ull * (p.nb + 1)))) return cuda_fail(ctx, e, "memset");
     }
     {
         PhaseScope ph(ctx, PH_COUNT, 1);
@@ -1051,7 +1051,7 @@ extern "C" int sj_part_join(sj_ctx *ctx, sj_part *p, const sj_opts *o, sj_pair *
     {
         PhaseScope ph(ctx, PH_RESET, 1);
         if ((e = launch_reset_counters((Stats *)w.stats.p, ctx->stream))) return cuda_fail(ctx, e, "reset");
-        if ((e = zero_words_async(w.pc.p, 4ull * nslots, ctx->stream))) return cuda_fail(ctx, e, "memset");
+        if ((e = zero_async(ctx, w.pc.p, 4ull * nslots))) return cuda_fail(ctx, e, "memset");
     }
     if ((st = enqueue_sweep(ctx, w, MODE_COUNT, nullptr, 0, nullptr, nullptr, 0))) return st;
     {

@@ -353,8 +353,8 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         cudaError_t e;
         {
             PhaseScope ph(ctx, PH_RESET, 0);
-            if ((e = zero_words_async(w.stats.p, sizeof(Stats), s)) ||
-                (e = zero_words_async(w.bFeatRaw.p, 4ull * kRawPerBlock * p.nb, s)))
+            if ((e = zero_async(ctx, w.stats.p, sizeof(Stats))) ||
+                (e = zero_async(ctx, w.bFeatRaw.p, 4ull * kRawPerBlock * p.nb)))
                 return cuda_fail(ctx, e, "memset");
         }
         if ((st = upload_single_join(ctx, w, a))) return st;
@@ -381,10 +381,11 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
                                        (float *)w.bPred.p, mlp_infer_grid(ctx, p.nb), s);
             }
             if (e) return cuda_fail(ctx, e, "prediction");
-            if ((e = launch_plan((const float *)w.bPred.p, a.imeta, a.ins, a.st, margin, slack, d_cap,
+            if ((e = zero_async(ctx, d_cap, kPlanScratch)) ||
+                (e = launch_plan((const float *)w.bPred.p, a.imeta, a.ins, a.st, margin, slack, d_cap,
                                  (unsigned *)w.bOrder.p, ctx->num_sms, s)))
                 return cuda_fail(ctx, e, "plan");
-            if ((e = copy_words_async(ctx->h_aux, d_cap, 8, s)) ||
+            if ((e = copy_async(ctx, ctx->h_aux, d_cap, 8)) ||
                 (e = cudaEventRecord(ctx->ev_aux, s)))
                 return cuda_fail(ctx, e, "capacity copy");
         }

@@ -240,7 +240,7 @@ static int dist_core(sj_ctx *ctx, const sj_point *d_P, int64_t nP, const sj_poin
             return cuda_fail(ctx, e, "refinement kernels");
     }
     Stats *hs = (Stats *)ctx->h_stats;
-    if ((e = copy_words_async(&hs->npairs, &dst->npairs, sizeof(unsigned long long), ctx->stream)))
+    if ((e = copy_async(ctx, &hs->npairs, &dst->npairs, sizeof(unsigned long long))))
         return cuda_fail(ctx, e, "copy of the refined count");
     if ((e = cudaStreamSynchronize(ctx->stream))) return cuda_fail(ctx, e, "stream sync");
     const unsigned long long P = hs->npairs;

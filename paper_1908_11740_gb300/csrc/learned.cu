@@ -16,7 +16,6 @@
 #include <cuda_bf16.h>
 
 #include "sj_learned.h"
-#include "sj_kernels.h"
 
 namespace sj {
 
@@ -473,12 +472,10 @@ cudaError_t launch_heur_pred(const float *feat, const unsigned *items, const uns
     return cudaGetLastError();
 }
 
-// cap_total points to kPlanScratch bytes: the total, then the class
-// histogram and cursors.  grid: CTAs of 256 over the items.
+// cap_total points to kPlanScratch bytes, zeroed by the caller: the total,
+// then the class histogram and cursors.  grid: CTAs of 256 over the items.
 cudaError_t launch_plan(const float *pred, const uint4 *imeta, const unsigned *ins, const Stats *st, float margin,
                         unsigned slack, unsigned long long *cap_total, unsigned *order, int grid, cudaStream_t s) {
-    cudaError_t e = zero_words_async(cap_total, kPlanScratch, s);
-    if (e) return e;
     unsigned *scratch = reinterpret_cast<unsigned *>(cap_total + 1);
     k_plan_count<<<grid, 256, 0, s>>>(pred, imeta, ins, st, margin, slack, cap_total, scratch);
     k_plan_order<<<grid, 256, 0, s>>>(pred, imeta, ins, st, scratch, order);

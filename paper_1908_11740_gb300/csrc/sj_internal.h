@@ -189,6 +189,19 @@ struct sj_ctx {
     char msg[512];
 };
 
+namespace sj {
+// zero_words_async / copy_words_async on the context's stream, counted among
+// the library's kernel launches (sj_timing.launches).
+inline cudaError_t zero_async(sj_ctx *ctx, void *p, size_t bytes) {
+    if (bytes >= 4) ctx->launches++;
+    return zero_words_async(p, bytes, ctx->stream);
+}
+inline cudaError_t copy_async(sj_ctx *ctx, void *dst, const void *src, size_t bytes) {
+    if (bytes >= 4) ctx->launches++;
+    return copy_words_async(dst, src, bytes, ctx->stream);
+}
+}  // namespace sj
+
 struct sj_part {
     sj_ctx *ctx = nullptr;
     sj::GridDev grid;
