@@ -102,6 +102,13 @@ extern "C" int sj_join_host_many(sj_ctx *ctx, int n, const sj_rect *const *h_R, 
         if ((st = ensure(ctx, h->in_r[b], need_r[b])) || (st = ensure(ctx, h->in_s[b], need_s[b]))) return st;
     }
     cudaError_t e;
+    // a failed call returns only after both streams are idle, so that no copy
+    // still reads or writes the caller's host buffers
+    auto drain = [&](int status) {
+        cudaStreamSynchronize(h->cs);
+        cudaStreamSynchronize(ctx->stream);
+        return status;
+    };
     auto h2d = [&](int i) -> int {
         const int b = i & 1;
         if ((e = cudaStreamWaitEvent(h->cs, h->ev_free[b], 0))) return cuda_fail(ctx, e, "copy stream wait");
@@ -113,27 +120,24 @@ extern "C" int sj_join_host_many(sj_ctx *ctx, int n, const sj_rect *const *h_R, 
         return SJ_OK;
     };
     int result = SJ_OK;
-    if ((st = h2d(0))) return st;
+    if ((st = h2d(0))) return drain(st);
     for (int i = 0; i < n; i++) {
         const int b = i & 1;
-        if (i + 1 < n && (st = h2d(i + 1))) return st;
-        if ((e = cudaStreamWaitEvent(ctx->stream, h->ev_in[b], 0))) return cuda_fail(ctx, e, "stream wait");
+        if (i + 1 < n && (st = h2d(i + 1))) return drain(st);
+        if ((e = cudaStreamWaitEvent(ctx->stream, h->ev_in[b], 0))) return drain(cuda_fail(ctx, e, "stream wait"));
         OutSpec os{OutSpec::WS};
         int64_t np = 0;
         st = join_core(ctx, ctx->ws, (const sj_rect *)h->in_r[b].p, nR[i], (const sj_rect *)h->in_s[b].p, nS[i],
                        gd[i], o, os, &np);
-        if ((e = cudaEventRecord(h->ev_free[b], ctx->stream))) return cuda_fail(ctx, e, "event");
-        if (st) {
-            cudaStreamSynchronize(h->cs);
-            return st;
-        }
+        if ((e = cudaEventRecord(h->ev_free[b], ctx->stream))) return drain(cuda_fail(ctx, e, "event"));
+        if (st) return drain(st);
         npairs[i] = np;
         if (np > cap[i]) {
             result = SJ_EOVERFLOW;
             continue;
         }
         if (np && (e = cudaMemcpyAsync(h_out[i], os.got, 8ull * np, cudaMemcpyDeviceToHost, ctx->stream)))
-            return cuda_fail(ctx, e, "copy of the pairs to the host");
+            return drain(cuda_fail(ctx, e, "copy of the pairs to the host"));
     }
     if ((e = cudaStreamSynchronize(ctx->stream)) || (e = cudaStreamSynchronize(h->cs)))
         return cuda_fail(ctx, e, "stream sync");

@@ -69,3 +69,13 @@ def test_null_context_is_rejected(lib):
     assert lib.sj_join(None, None, 0, None, 0, None, None, None, None) == 1
     assert lib.sj_count(None, None, 0, None, 0, None, None) == 1
     assert lib.sj_destroy(None) == 1
+
+
+def test_null_context_is_rejected_by_every_join_entry(lib):
+    P, I64, F = ctypes.c_void_p, ctypes.c_int64, ctypes.c_float
+    lib.sj_distance_join.argtypes = [P, P, I64, P, I64, F, P, P, P, P, P]
+    lib.sj_distance_join_into.argtypes = [P, P, I64, P, I64, F, P, P, P, I64, P, P]
+    lib.sj_join_host_many.argtypes = [P, ctypes.c_int, P, P, P, P, P, P, P, P, P]
+    assert lib.sj_distance_join(None, None, 0, None, 0, 0.1, None, None, None, None, None) == 1
+    assert lib.sj_distance_join_into(None, None, 0, None, 0, 0.1, None, None, None, 0, None, None) == 1
+    assert lib.sj_join_host_many(None, 0, None, None, None, None, None, None, None, None, None) == 1
