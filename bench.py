@@ -172,6 +172,43 @@ def run_cpu_oracle(R, S, args, reps=1):
                        f"{t:.2f} s per run")}, t
 
 
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def run_cpu_parallel(R, S, args, reps=3):
+    """The paper's multi-core PBSM (Sec. 3.4, OpenMP) on every host core,
+    on the same strip as the oracle's sample: context for the GPU numbers,
+    beside the single-core oracle.  Never fails the benchmark."""
+    try:
+        import oracle
+
+        r, s = cpu_sample(R, S, args.cpu_frac)
+        ny = max(1, int(round(args.grid * args.cpu_frac)))
+        threads = oracle.parallel_threads()
+        oracle.pbsm_parallel(r, s, args.grid, ny, 0.0, 0.0, 1.0, args.cpu_frac, pairs=False)   # warm
+        times, npairs = [], 0
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            npairs = oracle.pbsm_parallel(r, s, args.grid, ny, 0.0, 0.0, 1.0, args.cpu_frac, pairs=False)
+            times.append(time.perf_counter() - t0)
+        t = statistics.median(times)
+        return {"value": npairs / t, "unit": UNIT, "cores": threads, "kind": "paper Sec. 3.4 multi-core PBSM (OpenMP)",
+                "cpu_model": cpu_model(),
+                "sample": f"the oracle's strip ({len(r):,} x {len(s):,} rectangles, {npairs:,} pairs), "
+                          f"{t * 1e3:.1f} ms per run on {threads} threads"}
+    except Exception as e:  # noqa: BLE001 - a baseline must never break the benchmark
+        return {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -329,9 +366,10 @@ def ours(args):
     traffic = load_traffic().get(kern[dom])
     b_join = 16 * n_in + 40 * E + 8 * P
 
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0 and not args.no_cpu:
         cpu, _ = run_cpu_oracle(R, S, args)
+        cpu_par = run_cpu_parallel(R, S, args)
 
     if rank == 0:
         line = {
@@ -357,6 +395,7 @@ def ours(args):
             "phases_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in phases.items()},
             "compare": compare,
             "cpu_baseline": cpu,
+            "cpu_parallel_baseline": cpu_par,
             "e2e": {"value": p_all / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": 16 * n_in, "d2h_bytes_per_step": 8 * P,
                     "api": f"sj_join_host_many ({e2e_steps} joins from pinned host buffers, each input copy "

@@ -12,6 +12,10 @@ written from the paper ("Parallel In-Memory Evaluation of Spatial Joins"):
 * ``dist_brute`` / ``dist_pbsm`` -- the eps-distance join on points of Sec. 1
   (the definition; squares of side eps joined by PBSM, then refined) (C).
 
+``pbsm_parallel`` (``pbsm_parallel.c``) is not part of the oracle: it is the
+paper's multi-core evaluation (Sec. 3.4) with OpenMP, a CPU timing baseline
+whose pairs the tests check against the oracle.
+
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA
 library and never imports it.
@@ -36,13 +40,79 @@ CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-st
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no OpenMP, no vector intrinsics)."""
+    """Compile the oracle with gcc (no OpenMP, no vector intrinsics), and
+    the multi-core baseline if the compiler supports OpenMP."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+    try:
+        build_parallel(force)
+    except (OSError, subprocess.CalledProcessError):
+        pass   # no OpenMP: the baseline is reported as unavailable
     return _LIB
+
+
+_PAR_SRC = os.path.join(_HERE, "pbsm_parallel.c")
+_PAR_LIB = os.path.join(_BUILD, "libpbsm_parallel.so")
+_par = None
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile the multi-core PBSM baseline (gcc -fopenmp)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_PAR_LIB) or os.path.getmtime(_PAR_LIB) < os.path.getmtime(_PAR_SRC):
+        tmp = _PAR_LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, "-fopenmp", "-o", tmp, _PAR_SRC, "-lm"],
+                              stderr=subprocess.DEVNULL)
+        os.replace(tmp, _PAR_LIB)
+    return _PAR_LIB
+
+
+def _load_parallel():
+    global _par
+    with _lock:
+        if _par is None:
+            lib = ctypes.CDLL(build_parallel())
+            P, I64, I, F = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_float
+            lib.pp_pbsm.restype = I64
+            lib.pp_pbsm.argtypes = [P, I64, P, I64, I, I, F, F, F, F, I, P]
+            lib.pp_free.restype = None
+            lib.pp_free.argtypes = [P]
+            lib.pp_max_threads.restype = I
+            lib.pp_max_threads.argtypes = []
+            _par = lib
+        return _par
+
+
+def parallel_threads() -> int:
+    """Threads the multi-core baseline uses by default."""
+    return _load_parallel().pp_max_threads()
+
+
+def pbsm_parallel(R, S, nx: int, ny: int | None = None, x0: float = 0.0, y0: float = 0.0,
+                  x1: float = 1.0, y1: float = 1.0, threads: int = 0, pairs: bool = True):
+    """The paper's multi-core PBSM (Sec. 3.4) on ``threads`` threads (0 = all):
+    the sorted int32[P, 2] pairs, or only their number with ``pairs=False``."""
+    lib = _load_parallel()
+    ny = nx if ny is None else ny
+    R, S = _rects(R), _rects(S)
+    out = ctypes.c_void_p()
+    n = lib.pp_pbsm(R.ctypes.data, len(R), S.ctypes.data, len(S), nx, ny, x0, y0, x1, y1, threads,
+                    ctypes.byref(out) if pairs else None)
+    if n < 0:
+        raise MemoryError("multi-core baseline: allocation failed or bad arguments")
+    if not pairs:
+        return int(n)
+    try:
+        a = np.ctypeslib.as_array(ctypes.cast(out, ctypes.POINTER(ctypes.c_int32)), shape=(n * 2,)).copy() \
+            if n else np.zeros(0, np.int32)
+    finally:
+        if out.value:
+            lib.pp_free(out)
+    a = a.reshape(-1, 2)
+    return a[np.lexsort((a[:, 1], a[:, 0]))] if len(a) else a
 
 
 def _load():
