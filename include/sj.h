@@ -235,7 +235,8 @@ int sj_set_tuning(sj_ctx *ctx, int block_target);
  *       are d_out[h_offsets[j] .. h_offsets[j+1]) (ids local to the join)
  *   h_offsets : host, nj + 1 values (also filled on SJ_EOVERFLOW, which is
  *       returned when cap < h_offsets[nj]; nothing is written then)
- * Exact two-pass join (o->mode is ignored); synchronises once after counting.
+ * Exact two-pass join (o->mode and o->sort_output are ignored: each join's
+ * range is unsorted); synchronises once after counting.
  * Joins whose tiles exceed shared memory fall back to sj_join_into each. */
 int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const int64_t *nR,
                   const sj_rect *const *d_S, const int64_t *nS, const sj_grid *g, const sj_opts *o,
