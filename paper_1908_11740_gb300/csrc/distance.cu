@@ -193,11 +193,18 @@ static int dist_core(sj_ctx *ctx, const sj_point *d_P, int64_t nP, const sj_poin
     GridDev gd;
     if ((st = check_inputs(ctx, nullptr, 0, nullptr, 0, g, &gd))) return st;   // the grid alone
     const float h = square_half_width(eps);
+    // the candidates need no order: only the refined pairs are sorted (sort_output)
+    sj_opts oc{};
+    if (o) {
+        oc = *o;
+        oc.sort_output = 0;
+    }
+    const sj_opts *po = o ? &oc : nullptr;
     OutSpec cs{OutSpec::WS};
     int64_t C = 0;
     {   // squares on the fly (two-level path)
         PointInputs in(w, h);
-        st = join_core(ctx, w, (const sj_rect *)d_P, nP, (const sj_rect *)d_Q, nQ, gd, o, cs, &C);
+        st = join_core(ctx, w, (const sj_rect *)d_P, nP, (const sj_rect *)d_Q, nQ, gd, po, cs, &C);
     }
     cudaError_t e;
     if (st == PTS_UNSUITED) {   // the single-level path: write the squares out
@@ -211,7 +218,7 @@ static int dist_core(sj_ctx *ctx, const sj_point *d_P, int64_t nP, const sj_poin
             if ((e = cudaGetLastError())) return cuda_fail(ctx, e, "square kernel");
         }
         cs = OutSpec{OutSpec::WS};
-        st = join_core(ctx, w, (const sj_rect *)w.dsq_r.p, nP, (const sj_rect *)w.dsq_s.p, nQ, gd, o, cs, &C);
+        st = join_core(ctx, w, (const sj_rect *)w.dsq_r.p, nP, (const sj_rect *)w.dsq_s.p, nQ, gd, po, cs, &C);
     }
     if (st) return st;
     if (ncand) *ncand = C;
