@@ -79,3 +79,43 @@ def test_null_context_is_rejected_by_every_join_entry(lib):
     assert lib.sj_distance_join(None, None, 0, None, 0, 0.1, None, None, None, None, None) == 1
     assert lib.sj_distance_join_into(None, None, 0, None, 0, 0.1, None, None, None, 0, None, None) == 1
     assert lib.sj_join_host_many(None, 0, None, None, None, None, None, None, None, None, None) == 1
+
+
+def test_plain_c_program_compiles_links_and_runs(lib, tmp_path):
+    """include/sj.h is a C header: a C11 program includes it, links the
+    library and calls it (calls that need no GPU)."""
+    import shutil
+    import subprocess
+
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_1908_11740_gb300 import build
+
+    so = build.build()
+    src = tmp_path / "use_sj.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "sj.h"
+int main(void) {
+    sj_ctx *ctx = NULL;
+    sj_grid g = {16, 16, 0.0f, 0.0f, 1.0f, 1.0f};
+    sj_opts o = {SJ_TWO_PASS, 1, 0.25f, 0};
+    sj_point p = {0.5f, 0.5f};
+    int64_t n = 0;
+    if (strcmp(sj_strerror(SJ_OK), "ok") != 0) return 1;
+    if (sj_create(&ctx, -1, NULL) != SJ_EINVAL || ctx != NULL) return 2;
+    if (sj_join(NULL, NULL, 0, NULL, 0, &g, &o, NULL, &n) != SJ_EINVAL) return 3;
+    if (sj_distance_join(NULL, &p, 1, &p, 1, 0.1f, &g, &o, NULL, &n, NULL) != SJ_EINVAL) return 4;
+    if (sizeof(sj_rect) != 16 || sizeof(sj_pair) != 8 || sizeof(sj_point) != 8) return 5;
+    printf("ok\n");
+    return 0;
+}
+''')
+    exe = tmp_path / "use_sj"
+    inc = os.path.join(ROOT, "include")
+    libdir = os.path.dirname(so)
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Werror", "-I", inc, str(src), "-o", str(exe),
+                           "-L", libdir, "-l:" + os.path.basename(so), "-Wl,-rpath," + libdir])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.returncode, out.stdout, out.stderr)
