@@ -371,10 +371,10 @@ int sj_distance_join_into(sj_ctx *ctx, const sj_point *d_P, int64_t nP, const sj
 
 /* ---- a join that allocates nothing --------------------------------------- */
 /* The paper has no counterpart to this entry point; it exists for callers
- * that cannot allocate device memory: code that runs while someone else is
- * capturing a CUDA graph, plug-ins whose host process owns every device
- * allocation (a fixed budget or a custom pool), and callers that cannot
- * afford an allocation's latency or implicit synchronisation.
+ * that cannot allocate device memory: plug-ins whose host process owns every
+ * device allocation (a fixed budget or a custom pool that nothing may
+ * bypass), and callers on a latency-critical path that cannot afford an
+ * allocation's latency or the device-wide synchronisation of cudaFree.
  *
  * Same result as sj_join_into (two-pass, exact), but every scratch buffer is
  * carved from one fixed device array of 20 MiB inside this library.  Every
@@ -388,15 +388,18 @@ int sj_distance_join_into(sj_ctx *ctx, const sj_point *d_P, int64_t nP, const sj
  * Limits: nR, nS <= 65536 and at most 131072 replicated entries per side;
  * beyond them SJ_EINVAL (sizes are checked first, the entry count on the
  * device, in which case nothing is written).  If cap is too small, *npairs
- * gets the required count and SJ_EOVERFLOW is returned.
+ * gets the required count and SJ_EOVERFLOW is returned.  SJ_ETIMEOUT if a
+ * bounded device-side wait gave up, SJ_EINTERNAL for an internal table
+ * overflow, SJ_ECUDA for a failed runtime call.
  * Uses the current device.  The first call on a device resolves the array's
  * address (cudaGetSymbolAddress) and the launch parameters: make that first
  * call before any stream capture.  Calls share the array: two calls whose
  * work overlaps on the GPU (different streams, or different host threads)
  * race and corrupt each other; serialise them.  Each call clears the
  * counters it needs, so stale contents of an earlier call do no harm.
- * Synchronises the stream once (after counting); the pairs are written
- * asynchronously afterwards.  Status codes only (no sj_last_error). */
+ * The call waits for the stream once, after the count pass (it reads the
+ * pair count back into host memory); the pairs are written asynchronously
+ * afterwards.  Status codes only (no sj_last_error). */
 int sj_join_noalloc(const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
                     const sj_grid *g, sj_pair *d_out, int64_t cap, int64_t *npairs,
                     void *cuda_stream);

@@ -7,6 +7,9 @@ written from the paper ("Parallel In-Memory Evaluation of Spatial Joins"):
 * ``sweep``  -- Algorithm 1, forward-scan plane sweep over the whole space (C);
 * ``pbsm``   -- uniform-grid PBSM with replication, per-tile sort by x_l,
   Algorithm 1 per tile and the reference-point test of Eq. 1 (C);
+* ``pbsm_digest`` -- the same PBSM with the pairs folded into an
+  order-independent digest (count, sum and xor of the SplitMix64 output
+  function of each pair) instead of stored: the check of 1e9-pair joins;
 * ``tile_counts`` / ``cell`` -- the partitioning counts of Sec. 3.4 step 2;
 * ``features`` / ``mlp``    -- in :mod:`oracle.learned` (numpy, float64);
 * ``dist_brute`` / ``dist_pbsm`` -- the eps-distance join on points of Sec. 1
@@ -129,6 +132,8 @@ def _load():
         lib.orc_sweep.argtypes = [P, I64, P, I64, P]
         lib.orc_pbsm_ex.restype = P
         lib.orc_pbsm_ex.argtypes = [P, I64, P, I64, I, I, F, F, F, F, P, P, P, P]
+        lib.orc_pbsm_digest.restype = I
+        lib.orc_pbsm_digest.argtypes = [P, I64, P, I64, I, I, F, F, F, F, P]
         lib.orc_res_count.restype = I64
         lib.orc_res_count.argtypes = [P]
         lib.orc_res_failed.restype = I
@@ -215,6 +220,22 @@ def pbsm(R, S, nx: int, ny: int | None = None, x0: float = 0.0, y0: float = 0.0,
     if per_tile:
         return out, {"cnt_r": cr, "cnt_s": cs, "pairs": tp, "cand": nc.value}
     return out
+
+
+def pbsm_digest(R, S, nx: int, ny: int | None = None, x0: float = 0.0, y0: float = 0.0,
+                x1: float = 1.0, y1: float = 1.0) -> tuple[int, int, int]:
+    """PBSM as :func:`pbsm`, returning only the digest of its pair set:
+    (pairs, sum mod 2^64, xor) of mix(r << 32 | s) over the pairs, with mix
+    the output function of SplitMix64 (Steele, Lea and Flood, 2014).  The
+    digest does not depend on the order of the pairs; no pair is stored."""
+    lib = _load()
+    ny = nx if ny is None else ny
+    R, S = _rects(R), _rects(S)
+    out = np.zeros(3, np.uint64)
+    if lib.orc_pbsm_digest(R.ctypes.data, len(R), S.ctypes.data, len(S), nx, ny, x0, y0, x1, y1,
+                           out.ctypes.data) != 0:
+        raise MemoryError("oracle: allocation failed or bad arguments")
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def cell(v: float, g0: float, g1: float, n: int) -> int:

@@ -143,10 +143,11 @@ def mlp_loss_grad(params, X, Y):
 
 
 def eq2_estimate(feat):
-    """Pairs of a block from its histograms: I_x = sum_i H_R^x[i] H_S^x[i]
-    (Eq. 2) and I_y alike; with x and y independent, I_x I_y / (n_R n_S),
-    where n_side = the block's entries (sum of a histogram is >= n; the
-    entry counts are passed through the features' scaling)."""
+    """(I_x, I_y) of every row of block features: I_x = sum_i H_R^x[i] H_S^x[i]
+    (Eq. 2), the pairs that share an x bucket (an upper bound on the pairs
+    whose x-projections intersect), and I_y alike.  The sizing estimate of a
+    block is I_x I_y / (n_R n_S) (x and y taken as independent); the cheaper
+    sweep axis of a block is the one with the smaller estimate (Sec. 3.3)."""
     h = np.expm1(np.asarray(feat, np.float64))
     ix = (h[:, 0:8] * h[:, 16:24]).sum(1)
     iy = (h[:, 8:16] * h[:, 24:32]).sum(1)

@@ -22,7 +22,10 @@
  *                 first, then written, Sec. 3.4 steps 2-4), each tile is
  *                 sorted by x_l and joined with Algorithm 1, and a pair is
  *                 reported only where its reference point lies (Eq. 1).
- * All three return the pairs sorted by (r, s).
+ * All three return the pairs sorted by (r, s).  orc_pbsm_digest runs orc_pbsm
+ * but folds every reported pair into an order-independent digest (count,
+ * sum and xor of a 64-bit mix of the pair) instead of storing it, for
+ * result sets too large to hold on the host (1e9 pairs).
  *
  * Readings of the paper used here:
  *  - Tile membership: cell(v) = clamp(floor((v - g0) * ginv), 0, n-1), with
@@ -52,12 +55,34 @@ typedef struct {
     orc_pair *p;
     int64_t n, cap;
     int failed;
+    int digest;        /* 1: pairs are folded into (n, sum, xr), not stored */
+    uint64_t sum, xr;
 } orc_res;
 
 /* ---- result buffer --------------------------------------------------- */
+/* The output function of SplitMix64 (Steele, Lea and Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014): a bijective 64-bit mixer.
+ * The digest of a pair set is (count, sum of mix(key) mod 2^64, xor of
+ * mix(key)) with key = (uint32)r << 32 | (uint32)s: it does not depend on the
+ * order of the pairs, and a changed, missing or repeated pair changes it. */
+static uint64_t mix64(uint64_t z)
+{
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
 static void res_push(orc_res *res, int32_t r, int32_t s)
 {
     if (res->failed) return;
+    if (res->digest) {
+        uint64_t h = mix64(((uint64_t)(uint32_t)r << 32) | (uint64_t)(uint32_t)s);
+        res->n++;
+        res->sum += h;
+        res->xr ^= h;
+        return;
+    }
     if (res->n == res->cap) {
         int64_t nc = res->cap ? 2 * res->cap : 1024;
         orc_pair *q = (orc_pair *)realloc(res->p, (size_t)nc * sizeof(orc_pair));
@@ -82,7 +107,7 @@ static orc_res *res_new(void) { return (orc_res *)calloc(1, sizeof(orc_res)); }
 
 static orc_res *res_finish(orc_res *res)
 {
-    if (res->n > 1) qsort(res->p, (size_t)res->n, sizeof(orc_pair), cmp_pair);
+    if (!res->digest && res->n > 1) qsort(res->p, (size_t)res->n, sizeof(orc_pair), cmp_pair);
     return res;
 }
 
@@ -270,21 +295,21 @@ static orc_ent *partition(const orc_rect *A, int64_t n, const grid_t *g,
 
 /* Optional per-tile outputs: tile_cnt_r/s (|R_T|, |S_T|) and tile_pairs
  * (pairs reported by tile T); each nx*ny long, or NULL. */
-orc_res *orc_pbsm_ex(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
-                     int nx, int ny, float x0, float y0, float x1, float y1,
-                     int64_t *tile_cnt_r, int64_t *tile_cnt_s, int64_t *tile_pairs,
-                     int64_t *ncand)
+static orc_res *pbsm_into(orc_res *res, const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
+                          int nx, int ny, float x0, float y0, float x1, float y1,
+                          int64_t *tile_cnt_r, int64_t *tile_cnt_s, int64_t *tile_pairs,
+                          int64_t *ncand)
 {
-    if (nx < 1 || ny < 1 || !(x1 > x0) || !(y1 > y0)) return NULL;
+    if (!res) return NULL;
+    if (nx < 1 || ny < 1 || !(x1 > x0) || !(y1 > y0)) { orc_res_free(res); return NULL; }
     grid_t g = make_grid(nx, ny, x0, y0, x1, y1);
     int64_t T = (int64_t)nx * ny;
     int64_t *cr = (int64_t *)malloc((size_t)T * sizeof(int64_t));
     int64_t *cs = (int64_t *)malloc((size_t)T * sizeof(int64_t));
     int64_t *orr = (int64_t *)malloc((size_t)(T + 1) * sizeof(int64_t));
     int64_t *os = (int64_t *)malloc((size_t)(T + 1) * sizeof(int64_t));
-    orc_res *res = res_new();
     orc_ent *er = NULL, *es = NULL;
-    if (!cr || !cs || !orr || !os || !res) goto fail;
+    if (!cr || !cs || !orr || !os) goto fail;
     er = partition(R, nR, &g, cr, orr);
     es = partition(S, nS, &g, cs, os);
     if (!er || !es) goto fail;
@@ -317,6 +342,34 @@ fail:
     free(cr); free(cs); free(orr); free(os); free(er); free(es);
     orc_res_free(res);
     return NULL;
+}
+
+orc_res *orc_pbsm_ex(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
+                     int nx, int ny, float x0, float y0, float x1, float y1,
+                     int64_t *tile_cnt_r, int64_t *tile_cnt_s, int64_t *tile_pairs,
+                     int64_t *ncand)
+{
+    return pbsm_into(res_new(), R, nR, S, nS, nx, ny, x0, y0, x1, y1, tile_cnt_r, tile_cnt_s, tile_pairs,
+                     ncand);
+}
+
+/* PBSM as above, with the pairs folded into their digest (see mix64) instead
+ * of stored: out[0] = pairs, out[1] = sum, out[2] = xor.  For result sets too
+ * large to hold (the 1e9-pair joins).  Returns 0, or -1 on bad arguments or
+ * allocation failure. */
+int orc_pbsm_digest(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
+                    int nx, int ny, float x0, float y0, float x1, float y1, uint64_t *out)
+{
+    orc_res *res = res_new();
+    if (!res) return -1;
+    res->digest = 1;
+    res = pbsm_into(res, R, nR, S, nS, nx, ny, x0, y0, x1, y1, NULL, NULL, NULL, NULL);
+    if (!res) return -1;
+    out[0] = (uint64_t)res->n;
+    out[1] = res->sum;
+    out[2] = res->xr;
+    orc_res_free(res);
+    return 0;
 }
 
 orc_res *orc_pbsm(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,

@@ -1,9 +1,10 @@
 // noalloc.cu -- a join entry point that never allocates device memory.
 //
-// Some callers cannot call cudaMalloc: code running inside a CUDA graph
-// being captured by someone else, plug-ins whose host process owns every
-// allocation (a fixed memory budget, a custom pool), or callers that must not
-// pay the latency or synchronisation of an allocation.  sj_join_noalloc runs
+// Some callers cannot call cudaMalloc: plug-ins whose host process owns every
+// device allocation (a fixed memory budget or a custom pool that nothing may
+// bypass), and callers on a latency-critical path that cannot pay an
+// allocation's latency or the device-wide synchronisation cudaFree implies.
+// sj_join_noalloc runs
 // the same two-pass join as sj_join_into, but every scratch buffer it needs
 // lives in the file-scope device array below, which the CUDA runtime creates
 // when this library's module is loaded on a device and keeps until exit.
@@ -162,8 +163,10 @@ extern "C" int sj_join_noalloc(const sj_rect *d_R, int64_t nR, const sj_rect *d_
     if ((e = cudaMemcpyAsync(&stats, w.stats.p, sizeof stats, cudaMemcpyDeviceToHost, c.stream))) return SJ_ECUDA;
     if ((e = cudaStreamSynchronize(c.stream))) return SJ_ECUDA;
     if (stats.err & sj::kErrBadRect) return SJ_EINVAL;
-    if (stats.err & sj::kErrFatal) return SJ_EINVAL;   // more entries than the scratch holds
-    if (stats.err) return SJ_EINTERNAL;
+    // more replicated entries than the scratch holds: the input is too large
+    if (stats.err & (sj::kErrEntCap | sj::kErrTooMany)) return SJ_EINVAL;
+    if (stats.err & sj::kErrTimeout) return SJ_ETIMEOUT;   // a bounded device wait gave up
+    if (stats.err) return SJ_EINTERNAL;                   // a table sized from the limits overflowed
     *npairs = (int64_t)stats.npairs;
     if ((unsigned long long)cap < stats.npairs) return SJ_EOVERFLOW;
     if (stats.npairs == 0) return SJ_OK;

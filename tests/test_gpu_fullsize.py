@@ -1,8 +1,17 @@
 """Parity at the benchmark's full size and launch configuration: the
-GIS-shaped join |R| = 10M, |S| = 20M on a 3000 x 3000 grid (and 1000 x 1000),
-the complete sorted pair set against the single-threaded oracle, plus the
-properties that hold at any size (no duplicates, count == sj_count, the
-host-buffer entry point returns the same set)."""
+GIS-shaped join |R| = 10M, |S| = 20M, the complete sorted pair set against the
+single-threaded oracle, for every grid of the workload's sweep (500^2 to
+4000^2) and for both the plain two-pass join and the learned one-pass join
+with the packaged model (the benchmark's headline mode), plus the properties
+that hold at any size (no duplicates, count == sj_count, the host-buffer entry
+point and the device-sorted output return the same set).  The pair set does
+not depend on the grid (every pair is reported by exactly one tile), so one
+oracle run serves every grid.
+
+A fresh seed (29, never seen in training) checks the learned join against the
+oracle again and shows what the trained network gains: its one-pass buffer
+holds at most twice the exact result with no block re-run, while the Eq. 2
+estimate from the same histograms reserves over a hundred times the result."""
 import numpy as np
 import pytest
 
@@ -12,10 +21,7 @@ from paper_1908_11740_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-
-@pytest.fixture(scope="module")
-def data():
-    return inputs.gis_pair()          # 10M x 20M, seed 2
+GRIDS = [500, 1000, 2000, 3000, 4000]
 
 
 @pytest.fixture(scope="module")
@@ -26,28 +32,72 @@ def sj():
     return binding
 
 
+@pytest.fixture(scope="module")
+def data():
+    R, S = inputs.gis_pair()          # 10M x 20M, seed 2
+    return R, S, oracle.pbsm(R, S, 3000)
+
+
+@pytest.fixture(scope="module")
+def ctx(sj):
+    from paper_1908_11740_gb300 import learn
+
+    c = sj.sj_create(0)
+    model, _ = learn.load(c)
+    yield c, model
+    sj.sj_set_model(c, None)
+    model.free()
+    sj.sj_destroy(c)
+
+
 def sorted_pairs(a):
     a = np.asarray(a, np.int32)
     return a[np.lexsort((a[:, 1], a[:, 0]))]
 
 
-@pytest.mark.parametrize("K", [3000, 1000])
-def test_gis_full_size_exact(sj, data, K):
-    R, S = data
-    want = oracle.pbsm(R, S, K)
-    ctx = sj.sj_create(0)
-    try:
-        dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
-        g = sj.make_grid(K)
-        got = sj.sj_join(ctx, dR, dS, g, sj.make_opts("two_pass")).cpu().numpy()
-        assert len(np.unique(got.view(np.int64))) == len(got)          # no duplicates
-        np.testing.assert_array_equal(sorted_pairs(got), want)
-        assert sj.sj_count(ctx, dR, dS, g) == len(want)
-        if K == 3000:
-            host = sj.sj_join_host(ctx, R, S, g).numpy()
-            np.testing.assert_array_equal(sorted_pairs(host), want)
-            # sorted on the device: equal to the oracle without a host sort
-            srt = sj.sj_join(ctx, dR, dS, g, sj.make_opts("two_pass", sort_output=True)).cpu().numpy()
-            np.testing.assert_array_equal(srt, want)
-    finally:
-        sj.sj_destroy(ctx)
+@pytest.mark.parametrize("mode", ["two_pass", "one_pass"])
+@pytest.mark.parametrize("K", GRIDS)
+def test_gis_full_size_exact(sj, data, ctx, K, mode):
+    R, S, want = data
+    c, model = ctx
+    sj.sj_set_model(c, model if mode == "one_pass" else None)
+    dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
+    g = sj.make_grid(K)
+    opts = sj.make_opts(mode)
+    got = sj.sj_join(c, dR, dS, g, opts).cpu().numpy()
+    st = sj.sj_last_stats(c)
+    assert len(np.unique(got.view(np.int64))) == len(got)          # no duplicates
+    np.testing.assert_array_equal(sorted_pairs(got), want)
+    if mode == "one_pass" and st["path"] == 1:
+        assert st["one_pass"] == 1
+    if K == 3000:
+        assert sj.sj_count(c, dR, dS, g) == len(want)
+        host = sj.sj_join_host(c, R, S, g, opts=opts).numpy()
+        np.testing.assert_array_equal(sorted_pairs(host), want)
+        # sorted on the device: equal to the oracle without a host sort
+        srt = sj.sj_join(c, dR, dS, g, sj.make_opts(mode, sort_output=True)).cpu().numpy()
+        np.testing.assert_array_equal(srt, want)
+
+
+def test_fresh_seed_learned_vs_eq2(sj, ctx):
+    """Config 5's evaluation: a fresh seed of the GIS-shaped layers, grid 3000."""
+    c, model = ctx
+    R, S = inputs.gis_pair(seed=29)
+    want = oracle.pbsm(R, S, 3000)
+    dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
+    g = sj.make_grid(3000)
+    P = len(want)
+    sj.sj_set_model(c, model)
+    got = sj.sj_join(c, dR, dS, g, sj.make_opts("one_pass")).cpu().numpy()
+    learned = sj.sj_last_stats(c)
+    np.testing.assert_array_equal(sorted_pairs(got), want)
+    got = sj.sj_join(c, dR, dS, g, sj.make_opts("one_pass_heur")).cpu().numpy()
+    heur = sj.sj_last_stats(c)
+    np.testing.assert_array_equal(sorted_pairs(got), want)
+    print(f"\nfresh seed 29: P = {P}, learned capacity {learned['capacity']} "
+          f"({learned['capacity'] / P:.2f} P, {learned['refit_items']} re-run blocks), "
+          f"Eq. 2 capacity {heur['capacity']} ({heur['capacity'] / P:.0f} P)")
+    assert learned["one_pass"] == 1 and heur["one_pass"] == 1
+    assert P <= learned["capacity"] <= 2 * P
+    assert learned["refit_items"] == 0
+    assert heur["capacity"] >= 100 * P

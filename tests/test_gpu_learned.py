@@ -9,7 +9,9 @@
   relative to its largest component, 1e-4 relative on outputs;
 * training lowers the loss on a fixed set;
 * the one-pass join (learned and Eq. 2 sizing, and a model forced to
-  under-size so that blocks are re-run) returns exactly the two-pass pairs.
+  under-size so that blocks are re-run) returns exactly the oracle's pairs,
+  through the library buffer, the host-buffer entry point and a caller
+  buffer.
 """
 import numpy as np
 import pytest
@@ -104,10 +106,10 @@ def test_training_lowers_the_loss(sj, ctx):
 
 
 @pytest.mark.parametrize("kind", ["eq2", "learned", "undersized"])
-def test_one_pass_equals_two_pass(sj, ctx, kind):
+def test_one_pass_equals_oracle(sj, ctx, kind):
     R, S = inputs.gis_pair(500_000, 800_000, seed=34, median_extent=1e-4)
     g = sj.make_grid(800)
-    want = sorted_pairs(sj.sj_join(ctx, dev(R), dev(S), g, sj.make_opts("two_pass")))
+    want = oracle.pbsm(R, S, 800)
     model = None
     try:
         if kind == "eq2":

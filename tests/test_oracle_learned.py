@@ -5,7 +5,9 @@
   other gradients zero) and the all-positive regime where the ReLU network
   is the linear map W3 W2 W1 x + ...;
 * block features against hand-counted buckets on a tiny instance, and the
-  block labels against the pairs of a brute-force join.
+  block labels against the pairs of a brute-force join;
+* the Eq. 2 estimate against brute-force counts of x- (y-) intersecting
+  pairs: equal where every projection is a bucket centre, above otherwise.
 """
 import numpy as np
 
@@ -101,3 +103,51 @@ def test_block_labels_sum_to_the_join():
     R, S = inputs.uniform_pair(2000, 2500, max_extent=0.03, seed=7)
     lab = L.block_labels(R, S, 40, 40, 8)
     assert sum(lab.values()) == len(oracle.brute(R, S))
+
+
+def _x_overlaps(R, S, axis):
+    lo, hi = (0, 2) if axis == 0 else (1, 3)
+    return int(((R[:, None, lo] <= S[None, :, hi]) & (S[None, :, lo] <= R[:, None, hi])).sum())
+
+
+def test_eq2_estimate_counts_bucket_sharing_pairs():
+    """Eq. 2 (Sec. 3.3): I_x = sum_i |R_i^x| |S_i^x| counts the (r, s) pairs
+    sharing an x bucket, an upper bound on the pairs whose x-projections
+    intersect.  On one block of 8 x 8 tiles (bucket i = tile column i) with
+    every rectangle of zero width at a bucket centre, two x-projections
+    intersect exactly when they share the bucket, so I_x equals the
+    brute-force count of x-intersecting pairs; zero-height rectangles pin I_y
+    alike; for general rectangles inside the block I_x and I_y bound the
+    brute-force counts from above."""
+    g = np.random.default_rng(7)
+    n_r, n_s = 40, 55
+
+    def segments(n, axis):
+        c = (g.integers(0, 8, n) + 0.5) / 8.0
+        lo = g.uniform(0.0, 0.9, n)
+        hi = np.minimum(lo + g.uniform(0.0, 0.3, n), 0.999)
+        a = np.empty((n, 4))
+        if axis == 0:   # zero width at bucket centres, random y extent
+            a[:, 0] = a[:, 2] = c
+            a[:, 1], a[:, 3] = lo, hi
+        else:
+            a[:, 1] = a[:, 3] = c
+            a[:, 0], a[:, 2] = lo, hi
+        return a.astype(np.float32)
+
+    for axis in (0, 1):
+        R, S = segments(n_r, axis), segments(n_s, axis)
+        f = L.block_features(R, S, 8, 8, 8, phi=1)
+        assert list(f) == [0]
+        ix, iy = L.eq2_estimate(f[0][None, :])
+        est = (ix if axis == 0 else iy)[0]
+        assert np.isclose(est, _x_overlaps(R, S, axis), rtol=1e-12)
+        other = (iy if axis == 0 else ix)[0]
+        assert other >= _x_overlaps(R, S, 1 - axis) - 1e-9
+
+    R, S = inputs.uniform_pair(60, 70, max_extent=0.3, seed=8)
+    R, S = np.clip(R, 0.0, 0.999).astype(np.float32), np.clip(S, 0.0, 0.999).astype(np.float32)
+    f = L.block_features(R, S, 8, 8, 8, phi=1)
+    ix, iy = L.eq2_estimate(f[0][None, :])
+    assert ix[0] >= _x_overlaps(R, S, 0) - 1e-9 and iy[0] >= _x_overlaps(R, S, 1) - 1e-9
+    assert ix[0] > 0 and iy[0] > 0
