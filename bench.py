@@ -54,9 +54,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
                     help="CPU sample: rectangles whose centre has y < frac")
-    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance"],
+    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance", "aniso"],
                     help="gis: the 10M x 20M GIS-shaped join (default); batch: 256 joins of uneven size; "
-                         "skew: the 20M x 20M Zipf extent / skew stress")
+                         "skew: the 20M x 20M Zipf extent / skew stress; aniso: 10M x 20M elongated "
+                         "rectangles, sweep along x against the adaptive axis of Sec. 3.3")
+    ap.add_argument("--aniso-grids", default="1750,600",
+                    help="aniso: grids to time (1750: the tile-extent rule; 600: coarse tiles)")
     ap.add_argument("--rho", type=float, default=2.1e-4,
                     help="skew: probability that S shares R's hot spots (2.1e-4: about 1e9 pairs)")
     ap.add_argument("--skew-grid", type=int, default=500,
@@ -630,6 +633,84 @@ def distance_arm(args):
     sjdist.teardown(env)
 
 
+def aniso_arm(args):
+    """Adaptive sweep axis (Sec. 3.3): |R| = 10M, |S| = 20M rectangles ten
+    times longer along one axis than the other (half the mixture components
+    wide, half tall), at the grid of the tile-extent rule and at a coarse
+    grid.  Every tile swept along x against every tile swept along the axis
+    with the smaller Eq. 2 estimate (k = 8 divisions per tile axis), in the
+    two-pass and the learned one-pass join; inputs resident."""
+    import torch
+
+    from paper_1908_11740_gb300 import build, learn, sj
+
+    env = sjdist.setup("nccl")
+    torch.cuda.set_device(env.local_rank)
+    build.build()
+    R, S = inputs.aniso_pair(args.n_r, args.n_s, seed=sjdist.instance_seed(5, env))
+    dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
+    ctx = sj.sj_create(env.local_rank)
+    model, _ = learn.load(ctx, args.model or learn.DEFAULT_MODEL)
+    sj.sj_set_model(ctx, model)
+    stream = torch.cuda.current_stream()
+    steps = max(3, min(args.steps, 20))
+
+    def timed(g, o):
+        for _ in range(max(3, args.warmup)):
+            sj.sj_join(ctx, dR, dS, g, o)
+        torch.cuda.synchronize()
+        sjdist.barrier(env)
+        sj.sj_timing_enable(ctx, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            out = sj.sj_join(ctx, dR, dS, g, o)
+            P = out.shape[0]
+            del out
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sjdist.barrier(env)
+        tm = sj.sj_timing_read(ctx)
+        sj.sj_timing_enable(ctx, False)
+        st = sj.sj_last_stats(ctx)
+        ph = {k: round(v[1] / steps, 4) for k, v in tm.items() if k != "launches" and v[0]}
+        return ev0.elapsed_time(ev1) / steps, P, st, ph, tm["launches"]
+
+    clocks = ClockSampler(env.local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    results, head, launches = {}, None, 0
+    for K in [int(k) for k in args.aniso_grids.split(",")]:
+        g = sj.make_grid(K)
+        for mode in ("two_pass", "one_pass"):
+            for axis in ("x", "adaptive"):
+                ms, P, st, ph, nl = timed(g, sj.make_opts(mode, axis=axis))
+                results[f"K{K} {mode} {axis}"] = {
+                    "ms_per_step": round(ms, 4), "pairs": P, "block_join_ms": ph.get("sweep_write"),
+                    "count_pass_ms": ph.get("sweep_count"), "y_sweep_tiles": st["y_sweep_tiles"],
+                    "path": "two-level" if st["path"] == 1 else "single-level"}
+                if head is None and mode == "one_pass" and axis == "adaptive":
+                    head = (K, ms, P)
+                    launches = nl
+    clk = clocks.stop()
+    K, ms, P = head
+    ms, P_all = sjdist.reduce_result(ms, P, env)
+    if env.rank == 0:
+        line = {"metric": METRIC + " (adaptive sweep axis, elongated rectangles)", "value": P_all / (ms / 1e3),
+                "unit": UNIT, "n_gpus": env.world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"elongated rectangles |R|={args.n_r:,} |S|={args.n_s:,}, aspect 10, "
+                                       f"GIS-shaped mixture centres, grid {K}x{K}, learned one-pass, adaptive axis",
+                           "pairs": P},
+                "compare": results, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    sj.sj_set_model(ctx, None)
+    model.free()
+    sj.sj_destroy(ctx)
+    sjdist.teardown(env)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -640,6 +721,8 @@ def main():
         skew_arm(args)
     elif args.workload == "distance":
         distance_arm(args)
+    elif args.workload == "aniso":
+        aniso_arm(args)
     else:
         ours(args)
 

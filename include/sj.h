@@ -83,11 +83,22 @@ typedef struct { int32_t nx, ny; float x0, y0, x1, y1; } sj_grid;
 #define SJ_ONE_PASS_HEUR 2   /* as SJ_ONE_PASS, sized by the Eq. 2 histogram estimate  */
 #define SJ_AUTO          3   /* SJ_ONE_PASS when a model is loaded, else SJ_TWO_PASS   */
 
+/* Option flags (sj_opts.flags). */
+#define SJ_SWEEP_ADAPTIVE 1  /* choose the sweep axis of every tile from the Eq. 2
+                                histograms of Sec. 3.3: the axis with the smaller
+                                estimate of intersecting projections (k = 8 buckets
+                                per tile axis, built from all of the tile's
+                                entries); without it every tile is swept along x
+                                (Algorithm 1).  Two-level path of single joins
+                                only: the single-level path (tiles beyond shared
+                                memory) and batches sweep along x.  The pairs
+                                are the same either way.  See sj_tile_axes.      */
+
 typedef struct {
     int32_t mode;         /* one of the modes above                          */
     int32_t sort_output;  /* nonzero: pairs ascending by (r, s)              */
     float   margin;       /* one-pass capacity = predicted * (1 + margin) + slack */
-    int32_t reserved;     /* must be 0                                      */
+    int32_t flags;        /* SJ_SWEEP_ADAPTIVE or 0; other bits: SJ_EINVAL   */
 } sj_opts;
 
 typedef struct sj_ctx sj_ctx;     /* device, stream, allocator, workspace    */
@@ -179,6 +190,16 @@ int sj_join_into(sj_ctx *ctx, const sj_rect *d_R, int64_t nR,
 int sj_tile_stats(sj_ctx *ctx, const sj_rect *d_R, int64_t nR,
                   const sj_rect *d_S, int64_t nS, const sj_grid *g,
                   uint32_t *d_cnt_r, uint32_t *d_cnt_s, uint32_t *d_pairs_per_tile);
+
+/* The sweep axis SJ_SWEEP_ADAPTIVE gives every tile of a join on grid *g
+ * (Sec. 3.3, Eq. 2 with k = 8 divisions per tile axis): d_axis is a
+ * caller-owned device uint8[nx * ny], row-major; 1 = swept along y, 0 = x
+ * (also for tiles holding no entry of one side).  Runs the partition and the
+ * count pass of the two-level path.  SJ_EINVAL when the grid or the data need
+ * the single-level path (which sweeps every tile along x).  Synchronises
+ * once. */
+int sj_tile_axes(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+                 const sj_grid *g, uint8_t *d_axis);
 
 /* ---- host buffers ------------------------------------------------------ */
 /* sj_join for HOST arrays: copies R and S to the device (into the context's
@@ -313,6 +334,7 @@ typedef struct {
     int32_t pad;
     int64_t capacity;            /* one-pass: pairs the output was sized for */
     int64_t refit_items;         /* one-pass: blocks re-run because they did not fit */
+    int64_t y_sweep_tiles;       /* SJ_SWEEP_ADAPTIVE: tiles swept along y    */
 } sj_stats;
 int sj_last_stats(sj_ctx *ctx, sj_stats *out);
 

@@ -11,6 +11,8 @@ written from the paper ("Parallel In-Memory Evaluation of Spatial Joins"):
   order-independent digest (count, sum and xor of the SplitMix64 output
   function of each pair) instead of stored: the check of 1e9-pair joins;
 * ``tile_counts`` / ``cell`` -- the partitioning counts of Sec. 3.4 step 2;
+* ``tile_axes`` -- the sweep axis of every tile from the Eq. 2 histograms of
+  Sec. 3.3 (k = 8 divisions per tile axis, all rectangles counted);
 * ``features`` / ``mlp``    -- in :mod:`oracle.learned` (numpy, float64);
 * ``dist_brute`` / ``dist_pbsm`` -- the eps-distance join on points of Sec. 1
   (the definition; squares of side eps joined by PBSM, then refined) (C).
@@ -118,44 +120,51 @@ def pbsm_parallel(R, S, nx: int, ny: int | None = None, x0: float = 0.0, y0: flo
     return a[np.lexsort((a[:, 1], a[:, 0]))] if len(a) else a
 
 
+def _configure(lib):
+    """Set the argument and result types of every oracle function on a
+    loaded copy of the library (also used for planted-mistake copies)."""
+    P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    F = ctypes.c_float
+    lib.orc_brute.restype = P
+    lib.orc_brute.argtypes = [P, I64, P, I64]
+    lib.orc_sweep.restype = P
+    lib.orc_sweep.argtypes = [P, I64, P, I64, P]
+    lib.orc_pbsm_ex.restype = P
+    lib.orc_pbsm_ex.argtypes = [P, I64, P, I64, I, I, F, F, F, F, P, P, P, P]
+    lib.orc_pbsm_digest.restype = I
+    lib.orc_pbsm_digest.argtypes = [P, I64, P, I64, I, I, F, F, F, F, P]
+    lib.orc_res_count.restype = I64
+    lib.orc_res_count.argtypes = [P]
+    lib.orc_res_failed.restype = I
+    lib.orc_res_failed.argtypes = [P]
+    lib.orc_res_copy.restype = None
+    lib.orc_res_copy.argtypes = [P, P]
+    lib.orc_res_free.restype = None
+    lib.orc_res_free.argtypes = [P]
+    lib.orc_cell.restype = I
+    lib.orc_cell.argtypes = [F, F, F, I]
+    lib.orc_cells.restype = None
+    lib.orc_cells.argtypes = [P, I64, I, I, F, F, F, F, P]
+    lib.orc_tile_axes.restype = I
+    lib.orc_tile_axes.argtypes = [P, I64, P, I64, I, I, F, F, F, F, P, P, P]
+    lib.orc_tile_counts.restype = None
+    lib.orc_tile_counts.argtypes = [P, I64, I, I, F, F, F, F, P]
+    lib.orc_dist_brute.restype = P
+    lib.orc_dist_brute.argtypes = [P, I64, P, I64, F]
+    lib.orc_dist_squares.restype = None
+    lib.orc_dist_squares.argtypes = [P, I64, F, P]
+    lib.orc_dist_pbsm.restype = P
+    lib.orc_dist_pbsm.argtypes = [P, I64, P, I64, F, I, I, F, F, F, F, P]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        lib = ctypes.CDLL(build())
-        P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
-        F = ctypes.c_float
-        lib.orc_brute.restype = P
-        lib.orc_brute.argtypes = [P, I64, P, I64]
-        lib.orc_sweep.restype = P
-        lib.orc_sweep.argtypes = [P, I64, P, I64, P]
-        lib.orc_pbsm_ex.restype = P
-        lib.orc_pbsm_ex.argtypes = [P, I64, P, I64, I, I, F, F, F, F, P, P, P, P]
-        lib.orc_pbsm_digest.restype = I
-        lib.orc_pbsm_digest.argtypes = [P, I64, P, I64, I, I, F, F, F, F, P]
-        lib.orc_res_count.restype = I64
-        lib.orc_res_count.argtypes = [P]
-        lib.orc_res_failed.restype = I
-        lib.orc_res_failed.argtypes = [P]
-        lib.orc_res_copy.restype = None
-        lib.orc_res_copy.argtypes = [P, P]
-        lib.orc_res_free.restype = None
-        lib.orc_res_free.argtypes = [P]
-        lib.orc_cell.restype = I
-        lib.orc_cell.argtypes = [F, F, F, I]
-        lib.orc_cells.restype = None
-        lib.orc_cells.argtypes = [P, I64, I, I, F, F, F, F, P]
-        lib.orc_tile_counts.restype = None
-        lib.orc_tile_counts.argtypes = [P, I64, I, I, F, F, F, F, P]
-        lib.orc_dist_brute.restype = P
-        lib.orc_dist_brute.argtypes = [P, I64, P, I64, F]
-        lib.orc_dist_squares.restype = None
-        lib.orc_dist_squares.argtypes = [P, I64, F, P]
-        lib.orc_dist_pbsm.restype = P
-        lib.orc_dist_pbsm.argtypes = [P, I64, P, I64, F, I, I, F, F, F, F, P]
-        _lib = lib
-        return lib
+        _lib = _configure(ctypes.CDLL(build()))
+        return _lib
 
 
 def _rects(a) -> np.ndarray:
@@ -241,6 +250,22 @@ def pbsm_digest(R, S, nx: int, ny: int | None = None, x0: float = 0.0, y0: float
 def cell(v: float, g0: float, g1: float, n: int) -> int:
     """Tile index of coordinate v on an n-tile axis over [g0, g1]."""
     return _load().orc_cell(v, g0, g1, n)
+
+
+def tile_axes(R, S, nx: int, ny: int | None = None, x0=0.0, y0=0.0, x1=1.0, y1=1.0):
+    """Sweep axis of every tile (uint8[ny*nx], row-major, 1 = y) from Eq. 2
+    with k = 8 divisions per tile axis, and the estimates I^x, I^y
+    (int64[ny*nx] each): y where I^y < I^x and the tile holds both sides."""
+    lib = _load()
+    ny = nx if ny is None else ny
+    R, S = _rects(R), _rects(S)
+    ax = np.zeros(nx * ny, np.uint8)
+    ix = np.zeros(nx * ny, np.int64)
+    iy = np.zeros(nx * ny, np.int64)
+    if lib.orc_tile_axes(R.ctypes.data, len(R), S.ctypes.data, len(S), nx, ny, x0, y0, x1, y1,
+                         ax.ctypes.data, ix.ctypes.data, iy.ctypes.data) != 0:
+        raise MemoryError("oracle: allocation failed or bad arguments")
+    return ax, ix, iy
 
 
 def tile_counts(A, nx: int, ny: int | None = None, x0=0.0, y0=0.0, x1=1.0, y1=1.0):

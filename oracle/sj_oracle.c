@@ -378,6 +378,73 @@ orc_res *orc_pbsm(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
     return orc_pbsm_ex(R, nR, S, nS, nx, ny, x0, y0, x1, y1, NULL, NULL, NULL, NULL);
 }
 
+/* ---- sweep axis of a tile (Sec. 3.3, Eq. 2) ---------------------------
+ * The x-projection of tile T is split into k = 8 equal divisions (and the
+ * y-projection alike).  H_R^x[i] counts the rectangles of R_T whose
+ * x-projection intersects division i; I^x_T = sum_i H_R^x[i] * H_S^x[i]
+ * estimates the x-intersecting pairs of R_T x S_T (Eq. 2, read with i = 0..k-1).
+ * The tile is swept along y when I^y_T < I^x_T, else along x (ties and tiles
+ * without both sides: x).  All of the tile's rectangles are counted (no
+ * sampling).
+ * Reading: division i of tile column c is the set of coordinates v whose
+ * cell-function value t(v) = (v - g0) * ginv (float32, as in cell_of) lies in
+ * [c + i/8, c + (i+1)/8); the projection [xl, xu] intersects it when
+ * 8 t(xl) < 8c + i + 1 and 8 t(xu) >= 8c + i (8 t is exact in float32).  A
+ * rectangle assigned to the tile always intersects at least one division. */
+static void tile_histogram(const orc_ent *E, int64_t n, int col, float g0, float ginv, int axis,
+                           int64_t *h)
+{
+    for (int i = 0; i < 8; i++) h[i] = 0;
+    for (int64_t k = 0; k < n; k++) {
+        float lo = axis ? E[k].yl : E[k].xl, hi = axis ? E[k].yu : E[k].xu;
+        float tl = (lo - g0) * ginv, tu = (hi - g0) * ginv;
+        for (int i = 0; i < 8; i++) {
+            float a = (float)(8 * col + i);
+            if (8.0f * tl < a + 1.0f && 8.0f * tu >= a) h[i]++;
+        }
+    }
+}
+
+/* Per tile (row-major, nx*ny): axis[t] = 1 when tile t is swept along y;
+ * ix / iy (optional, int64) receive I^x_T and I^y_T. */
+int orc_tile_axes(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
+                  int nx, int ny, float x0, float y0, float x1, float y1,
+                  uint8_t *axis, int64_t *ix, int64_t *iy)
+{
+    if (nx < 1 || ny < 1 || !(x1 > x0) || !(y1 > y0)) return -1;
+    grid_t g = make_grid(nx, ny, x0, y0, x1, y1);
+    int64_t T = (int64_t)nx * ny;
+    int64_t *cr = (int64_t *)malloc((size_t)T * sizeof(int64_t));
+    int64_t *cs = (int64_t *)malloc((size_t)T * sizeof(int64_t));
+    int64_t *orr = (int64_t *)malloc((size_t)(T + 1) * sizeof(int64_t));
+    int64_t *os = (int64_t *)malloc((size_t)(T + 1) * sizeof(int64_t));
+    orc_ent *er = NULL, *es = NULL;
+    int rc = -1;
+    if (!cr || !cs || !orr || !os) goto done;
+    er = partition(R, nR, &g, cr, orr);
+    es = partition(S, nS, &g, cs, os);
+    if (!er || !es) goto done;
+    for (int64_t t = 0; t < T; t++) {
+        int col = (int)(t % nx), row = (int)(t / nx);
+        int64_t hrx[8], hsx[8], hry[8], hsy[8], sx = 0, sy = 0;
+        tile_histogram(er + orr[t], cr[t], col, g.gx0, g.ginvx, 0, hrx);
+        tile_histogram(es + os[t], cs[t], col, g.gx0, g.ginvx, 0, hsx);
+        tile_histogram(er + orr[t], cr[t], row, g.gy0, g.ginvy, 1, hry);
+        tile_histogram(es + os[t], cs[t], row, g.gy0, g.ginvy, 1, hsy);
+        for (int i = 0; i < 8; i++) {
+            sx += hrx[i] * hsx[i];
+            sy += hry[i] * hsy[i];
+        }
+        axis[t] = (uint8_t)(cr[t] > 0 && cs[t] > 0 && sy < sx);
+        if (ix) ix[t] = sx;
+        if (iy) iy[t] = sy;
+    }
+    rc = 0;
+done:
+    free(cr); free(cs); free(orr); free(os); free(er); free(es);
+    return rc;
+}
+
 /* The cell function alone, for tests of the per-tile counts. */
 int orc_cell(float v, float g0, float g1, int n)
 {

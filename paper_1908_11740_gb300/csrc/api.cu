@@ -14,6 +14,7 @@
 #include "../../include/sj.h"
 #include "sj_common.cuh"
 #include "sj_internal.h"
+#include "sj_learned.h"
 #include "sj_kernels.h"
 
 using namespace sj;
@@ -758,7 +759,7 @@ int sj::enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, con
 // entries than shared memory (the caller then runs the single-level path).
 int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const float4 *R,
                                    long long nR, const float4 *S, long long nS, const GridDev &g,
-                                   Stats *stats, bool *use_direct) {
+                                   Stats *stats, bool *use_direct, bool adaptive, unsigned char *tile_axis) {
     *use_direct = false;
     w.bcap_r = std::max<unsigned long long>(w.bcap_r, (unsigned long long)nR + nR / 8 + 1024);
     w.bcap_s = std::max<unsigned long long>(w.bcap_s, (unsigned long long)nS + nS / 8 + 1024);
@@ -767,11 +768,14 @@ int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const
         if ((st = size_blocked(ctx, w, p))) return st;
         BArgs a = blocked_args(w, p, R, nR, S, nS, g);
         if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
+        a.adaptive = adaptive;
         if ((st = enqueue_blocked_partition(ctx, w, p, a))) return st;
         cudaError_t e;
         {
             PhaseScope ph(ctx, PH_SWEEP_COUNT, 1);
-            if ((e = launch_bjoin(MODE_COUNT, a, bjoin_out(w, 0), ctx->num_sms * ctx->bjoin_bps, ctx->stream)))
+            BJoinOut bo = bjoin_out(w, 0);
+            bo.tile_axis = tile_axis;
+            if ((e = launch_bjoin(MODE_COUNT, a, bo, ctx->num_sms * ctx->bjoin_bps, ctx->stream)))
                 return cuda_fail(ctx, e, "block join kernel");
         }
         {
@@ -798,6 +802,7 @@ int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const
         ctx->last.l1_entries_r = (int64_t)stats->e_r;
         ctx->last.l1_entries_s = (int64_t)stats->e_s;
         ctx->last.npairs = (int64_t)stats->npairs;
+        ctx->last.y_sweep_tiles = adaptive ? (int64_t)stats->naxis_y : 0;
         return SJ_OK;
     }
     return fail(ctx, SJ_EINTERNAL, "blocked workspace did not converge");
@@ -817,10 +822,11 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
     Stats stats;
     int st;
     BPlan bp;
+    const bool adaptive = o && (o->flags & SJ_SWEEP_ADAPTIVE);
     if (plan_blocked(ctx, gd, nR, nS, bp)) {
         bool direct = false;
         if ((st = blocked_partition_count(ctx, w, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd,
-                                          &stats, &direct)))
+                                          &stats, &direct, adaptive)))
             return st;
         if (!direct) {
             const unsigned long long P = stats.npairs;
@@ -829,6 +835,7 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
             if (P == 0) return SJ_OK;
             BArgs a = blocked_args(w, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd);
             if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
+            a.adaptive = adaptive;
             BJoinOut bo = bjoin_out(w, 1);
             bo.out = os.got;
             bo.cap = P;
@@ -855,7 +862,7 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
 
 int sj::check_opts(sj_ctx *ctx, const sj_opts *o) {
     if (!o) return SJ_OK;
-    if (o->reserved != 0) return fail(ctx, SJ_EINVAL, "sj_opts.reserved must be 0");
+    if (o->flags & ~SJ_SWEEP_ADAPTIVE) return fail(ctx, SJ_EINVAL, "unknown sj_opts.flags bits 0x%x", o->flags);
     if (o->mode < SJ_TWO_PASS || o->mode > SJ_AUTO) return fail(ctx, SJ_EINVAL, "unknown mode %d", o->mode);
     if (!(o->margin >= 0.0f) || !(o->margin < 1e6f)) return fail(ctx, SJ_EINVAL, "margin out of range");
     return SJ_OK;
@@ -946,7 +953,7 @@ extern "C" int sj_count(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_re
     if (plan_blocked(ctx, gd, nR, nS, bp)) {
         bool direct = false;
         if ((st = blocked_partition_count(ctx, ctx->ws, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd,
-                                          &stats, &direct)))
+                                          &stats, &direct, false)))
             return st;
         if (!direct) {
             *out_npairs = (int64_t)stats.npairs;
@@ -957,6 +964,29 @@ extern "C" int sj_count(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_re
                                   &stats, true)))
         return st;
     *out_npairs = (int64_t)stats.npairs;
+    return SJ_OK;
+}
+
+// The per-tile sweep axes of SJ_SWEEP_ADAPTIVE (partition + count pass of the
+// two-level path with the adaptive kernel, which also writes the axes).
+extern "C" int sj_tile_axes(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+                            const sj_grid *g, uint8_t *d_axis) {
+    GridDev gd;
+    int st = check_inputs(ctx, d_R, nR, d_S, nS, g, &gd);
+    if (st) return st;
+    if (!d_axis) return fail(ctx, SJ_EINVAL, "null d_axis");
+    DeviceGuard dg(ctx->device);
+    ctx->msg[0] = 0;
+    BPlan bp;
+    if (!plan_blocked(ctx, gd, nR, nS, bp)) return fail(ctx, SJ_EINVAL, "grid does not suit the two-level path");
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(d_axis, 0, (size_t)gd.nx * (size_t)gd.ny, ctx->stream))) return cuda_fail(ctx, e, "memset");
+    Stats stats;
+    bool direct = false;
+    if ((st = blocked_partition_count(ctx, ctx->ws, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &stats,
+                                      &direct, true, (unsigned char *)d_axis)))
+        return st;
+    if (direct) return fail(ctx, SJ_EINVAL, "a tile exceeds shared memory: the single-level path sweeps along x");
     return SJ_OK;
 }
 

@@ -350,6 +350,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         BArgs a = blocked_args(w, p, R, nR, S, nS, gd);
         a.feat_raw = (unsigned *)w.bFeatRaw.p;
         if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
+        a.adaptive = o && (o->flags & SJ_SWEEP_ADAPTIVE);
         cudaError_t e;
         {
             PhaseScope ph(ctx, PH_RESET, 0);
@@ -459,6 +460,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         ctx->last.one_pass = 1;
         ctx->last.capacity = (int64_t)C;
         ctx->last.refit_items = stats.nfail;
+        ctx->last.y_sweep_tiles = a.adaptive ? (int64_t)stats.naxis_y : 0;
         if (os.kind == OutSpec::INTO && P > C)
             return fail(ctx, SJ_EOVERFLOW, "need %llu pairs, cap %llu", P, C);
         if (stats.nfail) {

@@ -17,6 +17,8 @@
 // The pairs reported are exactly those of single-level PBSM on the same
 // nx x ny grid: a pair is reported by the tile that holds its reference
 // point, and that tile belongs to exactly one block.
+#include <cstddef>
+
 #include "sj_blocked.h"
 #include "sj_learned.h"
 
@@ -561,7 +563,33 @@ struct BJSmem {
     unsigned short tile[kFineCap];   // band-local tile of each position
     unsigned short band[kMaxFine + 2];
     int2 pbuf[kPairBuf];             // one-pass: the block's pairs before its reservation
+    unsigned axis[kMaxFine / 32];    // adaptive sweep axis: bit per tile, 1 = y
 };
+
+// Adaptive sweep axis (Sec. 3.3, Eq. 2): during the count step, before any
+// entry is placed, key[] .. id[] hold the histograms of every tile of the
+// block: [tile][side][axis][k = 8 buckets] as 16-bit counters, two to a word
+// (16 words per tile).  A tile holds at most kFineCap entries when it is
+// joined (a larger one sends the join to the single-level path), so no
+// counter of a joined tile can carry into its neighbour.
+constexpr int kAxisBuckets = 8;
+constexpr int kHistWords = 16;
+static_assert(offsetof(BJSmem, id) + sizeof(BJSmem::id) - offsetof(BJSmem, key) >=
+                  sizeof(unsigned) * kHistWords * kMaxFine,
+              "per-tile histograms must fit in key[] .. id[]");
+static_assert(kFineCap < 65536, "16-bit histogram counters");
+
+// Bucket index at 8x the tile resolution: floor(8 t) for the cell-function
+// value t = (v - g0) * ginv (both rounded to float32, as in cell_of; 8 t is
+// exact), clamped like the cells to [0, 8 n - 1].  Within tile c the bucket
+// is this minus 8 c.
+__device__ __forceinline__ int cell8_of(float v, float g0, float ginv, int n) {
+    const float t = __fmul_rn(__fsub_rn(v, g0), ginv);
+    const float f = floorf(t * 8.0f);
+    if (!(f >= 0.0f)) return 0;
+    if (f >= (float)(8 * n - 1)) return 8 * n - 1;
+    return (int)f;
+}
 
 // Per-row entry lists of a block staged in several bands: entry e (R: e <
 // nr1, S: e - nr1) appears in the list of every tile row it covers.  Row y
@@ -578,6 +606,7 @@ struct RowLists {
 
 struct BlockCtx {
     int cxb, cyb, gw, gh, ntl;
+    const unsigned *axis;  // adaptive sweep axis: bit lt set = tile lt swept along y (else nullptr)
     unsigned r0, nr1, s0, ns1;
     const BEnt *er, *es;   // the block's R and S entries (shared-memory copy or global)
 };
@@ -585,16 +614,19 @@ struct BlockCtx {
 // Write an entry of the block (side, MBR words hd, tail words t) into every
 // tile of [ta, tb) it overlaps (rows row_a..row_b of the block).  With
 // row >= 0 the entry comes from the list of that row and is taken only there
-// if it is its first row in the band.
+// if it is its first row in the band.  A tile swept along y (adaptive axis)
+// gets its MBRs with the axes exchanged: the sort key, the forward scan and
+// the test then run along y unchanged, and the intersection test is
+// symmetric in the two axes, so the pairs are the same.
 __device__ __forceinline__ void place_entry(BJSmem &sm, const BlockCtx &bc, int side, const uint4 &hd,
                                             const uint4 &t, int ta, int tb, int row_a, int row_b, int row) {
     const int cx0 = t.y & 0xffff, cx1 = t.y >> 16, cy0 = t.z & 0xffff, cy1 = t.z >> 16;
     const int ly0 = max(cy0 - bc.cyb, row_a), ly1 = min(cy1 - bc.cyb, row_b);
     if (ly0 > ly1 || (row >= 0 && ly0 != row)) return;
     const int lx0 = max(cx0 - bc.cxb, 0), lx1 = min(cx1 - bc.cxb, bc.gw - 1);
-    const float4 mb = make_float4(__uint_as_float(hd.x), __uint_as_float(hd.y), __uint_as_float(hd.z),
+    const float4 mx = make_float4(__uint_as_float(hd.x), __uint_as_float(hd.y), __uint_as_float(hd.z),
                                   __uint_as_float(hd.w));
-    const unsigned k = xkey(mb.x);
+    const float4 my = make_float4(mx.y, mx.x, mx.w, mx.z);
     for (int ly = ly0; ly <= ly1; ly++)
         for (int lx = lx0; lx <= lx1; lx++) {
             const int lt = ly * bc.gw + lx;
@@ -602,7 +634,9 @@ __device__ __forceinline__ void place_entry(BJSmem &sm, const BlockCtx &bc, int 
             const int j = lt - ta;
             const unsigned pos = atomicAdd(&sm.off[side][j], 1u);
             const unsigned flags = (lx + bc.cxb == cx0 ? kFlagCol : 0u) | (ly + bc.cyb == cy0 ? kFlagRow : 0u);
-            sm.key[pos] = k;
+            const bool swap = bc.axis && ((bc.axis[lt >> 5] >> (lt & 31)) & 1u);
+            const float4 mb = swap ? my : mx;
+            sm.key[pos] = xkey(mb.x);
             sm.mbr[pos] = mb;
             sm.id[pos] = t.x | flags;
             sm.tile[pos] = (unsigned short)j;
@@ -1076,7 +1110,7 @@ __device__ void band_split(BJSmem &sm, int ntl, unsigned *s_nbands, int *s_huge)
     __syncthreads();
 }
 
-template <int MODE>
+template <int MODE, int ADAPT>
 __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BJSmem &sm = *reinterpret_cast<BJSmem *>(smem_raw);
@@ -1144,33 +1178,91 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
         bc.er = a.bent_r + bc.r0;
         bc.es = a.bent_s + bc.s0;
 
-        // step 1: entries per tile of the block
+        // step 1: entries per tile of the block (and, for the adaptive sweep
+        // axis, the Eq. 2 histograms of every tile: k = 8 buckets per axis)
+        unsigned *hist = reinterpret_cast<unsigned *>(sm.key);
         for (int k = threadIdx.x; k < bc.ntl; k += kBJThreads) {
             sm.cnt[0][k] = 0;
             sm.cnt[1][k] = 0;
         }
+        if (ADAPT)
+            for (int k = threadIdx.x; k < bc.ntl * kHistWords; k += kBJThreads) hist[k] = 0;
         __syncthreads();
         const int n1 = (int)(bc.nr1 + bc.ns1);
         constexpr int kCountU = 2;   // entries a thread loads before counting them
         for (int eb = threadIdx.x; eb < n1; eb += kCountU * kBJThreads) {
-            uint4 t[kCountU];
+            uint4 t[kCountU], hd[kCountU];
 #pragma unroll
             for (int u = 0; u < kCountU; u++)
-                if (eb + u * kBJThreads < n1) t[u] = entry_words(bc, eb + u * kBJThreads)[1];
+                if (eb + u * kBJThreads < n1) {
+                    const uint4 *w = entry_words(bc, eb + u * kBJThreads);
+                    t[u] = w[1];
+                    if (ADAPT) hd[u] = w[0];
+                }
 #pragma unroll
             for (int u = 0; u < kCountU; u++) {
                 const int e = eb + u * kBJThreads;
                 if (e >= n1) break;
                 const int side = e >= (int)bc.nr1;
-                const int lx0 = max((int)(t[u].y & 0xffff) - bc.cxb, 0);
-                const int lx1 = min((int)(t[u].y >> 16) - bc.cxb, bc.gw - 1);
-                const int ly0 = max((int)(t[u].z & 0xffff) - bc.cyb, 0);
-                const int ly1 = min((int)(t[u].z >> 16) - bc.cyb, bc.gh - 1);
+                const int cx0 = (int)(t[u].y & 0xffff), cx1 = (int)(t[u].y >> 16);
+                const int cy0 = (int)(t[u].z & 0xffff), cy1 = (int)(t[u].z >> 16);
+                const int lx0 = max(cx0 - bc.cxb, 0), lx1 = min(cx1 - bc.cxb, bc.gw - 1);
+                const int ly0 = max(cy0 - bc.cyb, 0), ly1 = min(cy1 - bc.cyb, bc.gh - 1);
+                int fx0 = 0, fx1 = 0, fy0 = 0, fy1 = 0;
+                if (ADAPT) {
+                    fx0 = cell8_of(__uint_as_float(hd[u].x), a.g.x0, a.g.gx, a.g.nx);
+                    fx1 = cell8_of(__uint_as_float(hd[u].z), a.g.x0, a.g.gx, a.g.nx);
+                    fy0 = cell8_of(__uint_as_float(hd[u].y), a.g.y0, a.g.gy, a.g.ny);
+                    fy1 = cell8_of(__uint_as_float(hd[u].w), a.g.y0, a.g.gy, a.g.ny);
+                }
                 for (int ly = ly0; ly <= ly1; ly++)
-                    for (int lx = lx0; lx <= lx1; lx++) atomicAdd(&sm.cnt[side][ly * bc.gw + lx], 1u);
+                    for (int lx = lx0; lx <= lx1; lx++) {
+                        const int lt = ly * bc.gw + lx;
+                        atomicAdd(&sm.cnt[side][lt], 1u);
+                        if (ADAPT) {
+                            // buckets of the projections inside this tile
+                            const int col = bc.cxb + lx, row = bc.cyb + ly;
+                            const int bx0 = col == cx0 ? fx0 - 8 * col : 0, bx1 = col == cx1 ? fx1 - 8 * col : 7;
+                            const int by0 = row == cy0 ? fy0 - 8 * row : 0, by1 = row == cy1 ? fy1 - 8 * row : 7;
+                            unsigned *hx = hist + lt * kHistWords + side * 8, *hy = hx + 4;
+                            for (int b = bx0; b <= bx1; b++) atomicAdd(hx + (b >> 1), 1u << ((b & 1) << 4));
+                            for (int b = by0; b <= by1; b++) atomicAdd(hy + (b >> 1), 1u << ((b & 1) << 4));
+                        }
+                    }
             }
         }
         __syncthreads();
+        bc.axis = nullptr;
+        if (ADAPT) {
+            // Eq. 2: I = sum_i H_R[i] H_S[i] per axis; sweep along y when
+            // I_y < I_x (ties and tiles missing a side keep x)
+            for (int l0 = 0; l0 < bc.ntl; l0 += kBJThreads) {
+                const int lt = l0 + threadIdx.x;
+                bool y = false;
+                if (lt < bc.ntl && sm.cnt[0][lt] && sm.cnt[1][lt]) {
+                    const unsigned *h = hist + lt * kHistWords;
+                    unsigned long long ix = 0, iy = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const unsigned rx = h[q], ry = h[4 + q], sx = h[8 + q], sy = h[12 + q];
+                        ix += (unsigned long long)(rx & 0xffffu) * (sx & 0xffffu) +
+                              (unsigned long long)(rx >> 16) * (sx >> 16);
+                        iy += (unsigned long long)(ry & 0xffffu) * (sy & 0xffffu) +
+                              (unsigned long long)(ry >> 16) * (sy >> 16);
+                    }
+                    y = iy < ix;
+                }
+                const unsigned bits = __ballot_sync(kFullMask, y);
+                if ((threadIdx.x & 31) == 0 && lt < bc.ntl) {
+                    sm.axis[lt >> 5] = bits;
+                    if ((MODE == MODE_COUNT || MODE == MODE_RESERVE) && bits)
+                        atomicAdd(&a.st->naxis_y, (unsigned)__popc(bits));
+                }
+                if (MODE == MODE_COUNT && o.tile_axis && lt < bc.ntl)
+                    o.tile_axis[(size_t)(bc.cyb + lt / bc.gw) * jnx + bc.cxb + lt % bc.gw] = y ? 1 : 0;
+            }
+            bc.axis = sm.axis;   // read in the placement, after the barriers of step 2
+        }
         // step 2: bands of consecutive tiles that fit in shared memory.
         // Usually the whole block fits (one band): the offsets of the whole
         // block computed here are then its band's.  Otherwise, with h = half
@@ -1360,10 +1452,13 @@ size_t bjoin_smem_bytes() { return sizeof(BJSmem); }
 cudaError_t blocked_setup() {
     cudaError_t e;
     const int sm = (int)sizeof(BJSmem);
-    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_COUNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
-    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
-    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_RESERVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
-    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_TILES>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_COUNT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_WRITE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_RESERVE, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_TILES, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_COUNT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_WRITE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_RESERVE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
     const int l1 = 8 * kMaxBlocks;
     if ((e = cudaFuncSetAttribute(k_bcount<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
     if ((e = cudaFuncSetAttribute(k_bcount<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
@@ -1374,7 +1469,7 @@ cudaError_t blocked_setup() {
 
 int bjoin_blocks_per_sm() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bjoin<MODE_WRITE>, kBJThreads, sizeof(BJSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bjoin<MODE_WRITE, 0>, kBJThreads, sizeof(BJSmem));
     return nb > 0 ? nb : 1;
 }
 
@@ -1429,11 +1524,20 @@ cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s) {
 
 cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, cudaStream_t s) {
     const size_t sm = sizeof(BJSmem);
+    if (a.adaptive && a.nj == 1) {
+        switch (mode) {
+            case MODE_COUNT: k_bjoin<MODE_COUNT, 1><<<grid, kBJThreads, sm, s>>>(a, o); break;
+            case MODE_WRITE: k_bjoin<MODE_WRITE, 1><<<grid, kBJThreads, sm, s>>>(a, o); break;
+            case MODE_RESERVE: k_bjoin<MODE_RESERVE, 1><<<grid, kBJThreads, sm, s>>>(a, o); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (mode) {
-        case MODE_COUNT: k_bjoin<MODE_COUNT><<<grid, kBJThreads, sm, s>>>(a, o); break;
-        case MODE_WRITE: k_bjoin<MODE_WRITE><<<grid, kBJThreads, sm, s>>>(a, o); break;
-        case MODE_RESERVE: k_bjoin<MODE_RESERVE><<<grid, kBJThreads, sm, s>>>(a, o); break;
-        default: k_bjoin<MODE_TILES><<<grid, kBJThreads, sm, s>>>(a, o); break;
+        case MODE_COUNT: k_bjoin<MODE_COUNT, 0><<<grid, kBJThreads, sm, s>>>(a, o); break;
+        case MODE_WRITE: k_bjoin<MODE_WRITE, 0><<<grid, kBJThreads, sm, s>>>(a, o); break;
+        case MODE_RESERVE: k_bjoin<MODE_RESERVE, 0><<<grid, kBJThreads, sm, s>>>(a, o); break;
+        default: k_bjoin<MODE_TILES, 0><<<grid, kBJThreads, sm, s>>>(a, o); break;
     }
     return cudaGetLastError();
 }

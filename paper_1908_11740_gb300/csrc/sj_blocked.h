@@ -76,6 +76,7 @@ struct BArgs {
     unsigned long long lpool_cap;
     int pts;                    // 1: R, S hold float2 points, read as squares of half-width h
     float h;
+    int adaptive;               // single join: sweep axis per tile from Eq. 2 histograms (Sec. 3.3)
     Stats *st;
 };
 
@@ -104,6 +105,7 @@ struct BJoinOut {
     unsigned long long cap;
     unsigned *tile_pairs;       // MODE_TILES
     int2 *spill;                // MODE_RESERVE, optional: kPairSpill pairs per CTA
+    unsigned char *tile_axis;   // MODE_COUNT with adaptive axes, optional: axis of every tile (1 = y)
 };
 
 cudaError_t blocked_setup();

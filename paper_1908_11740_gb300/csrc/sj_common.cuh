@@ -69,7 +69,7 @@ struct Stats {
     int need_direct;                    // blocked path: a tile exceeds shared memory
     int pad;
     unsigned int nlch;                  // candidate chunks of the large-tile sweep
-    unsigned int pad2;
+    unsigned int naxis_y;               // blocked path: work items swept along y (adaptive axis)
 };
 
 // ---- the cell function (tile index of a coordinate) ------------------------

@@ -86,11 +86,12 @@ def _mixture_world(world, n_comp: int = 64):
     return mu, sigma
 
 
-def _mixture_centres(g, n, mu, sigma, background: float):
+def _mixture_centres(g, n, mu, sigma, background: float, with_comp: bool = False):
     """cx, cy from an equal-weight isotropic Gaussian mixture plus a uniform
     background fraction, truncated to [0,1]^2: a component draw that falls
     outside is redrawn from the same component (clipping instead would pile
-    thousands of centres onto the border lines)."""
+    thousands of centres onto the border lines).  With ``with_comp`` also the
+    component of every centre (-1 for the background)."""
     comp = g.integers(0, mu.shape[0], n)
     is_bg = g.random(n) < background
     z = g.standard_normal((n, 2))
@@ -102,6 +103,8 @@ def _mixture_centres(g, n, mu, sigma, background: float):
         c[idx] = mu[comp[idx]] + sigma[comp[idx], None] * g.standard_normal((len(idx), 2))
         out[idx] = ((c[idx] < 0.0) | (c[idx] > 1.0)).any(axis=1)
     c = np.where(is_bg[:, None], u, c)
+    if with_comp:
+        return c[:, 0], c[:, 1], np.where(is_bg, -1, comp)
     return c[:, 0], c[:, 1]
 
 
@@ -122,6 +125,33 @@ def gis_pair(n_r: int = 10_000_000, n_s: int = 20_000_000, seed: int = 2,
         cx, cy = _mixture_centres(g, n, mu, sigma, background)
         w = np.minimum(np.exp(g.normal(np.log(median_extent), log_sigma, n)), max_extent)
         h = np.minimum(np.exp(g.normal(np.log(median_extent), log_sigma, n)), max_extent)
+        out.append(rects_from_centres(cx, cy, w, h))
+    return out[0], out[1]
+
+
+def aniso_pair(n_r: int = 10_000_000, n_s: int = 20_000_000, seed: int = 5,
+               ratio: float = 10.0, median_extent: float = 2e-5, log_sigma: float = 1.0,
+               max_extent: float = 1e-2, background: float = 0.2):
+    """GIS-shaped layers of elongated objects (roads, rivers): the centres of
+    ``gis_pair`` (64-component Gaussian mixture shared by R and S, plus 20%
+    uniform background), and every rectangle ``ratio`` times longer along one
+    axis than along the other.  Each mixture component has one orientation
+    (wide or tall, drawn once per component from the world stream, shared by R
+    and S); background rectangles draw theirs at random.  The geometric mean
+    of width and height is log-normal with median ``median_extent`` and sigma
+    ``log_sigma``; both are clipped to ``max_extent``."""
+    world, gr, gs = _streams(seed)
+    mu, sigma = _mixture_world(world)
+    wide = world.random(mu.shape[0]) < 0.5
+    out = []
+    k = np.sqrt(ratio)
+    for g, n in ((gr, n_r), (gs, n_s)):
+        cx, cy, comp = _mixture_centres(g, n, mu, sigma, background, with_comp=True)
+        e = np.exp(g.normal(np.log(median_extent), log_sigma, n))
+        bg_wide = g.random(n) < 0.5
+        is_wide = np.where(comp >= 0, wide[np.maximum(comp, 0)], bg_wide)
+        w = np.minimum(np.where(is_wide, e * k, e / k), max_extent)
+        h = np.minimum(np.where(is_wide, e / k, e * k), max_extent)
         out.append(rects_from_centres(cx, cy, w, h))
     return out[0], out[1]
 

@@ -22,6 +22,7 @@ from . import build as _build
 
 SJ_OK, SJ_EINVAL, SJ_ENOMEM, SJ_EOVERFLOW, SJ_ETIMEOUT, SJ_ECUDA, SJ_EINTERNAL = range(7)
 SJ_TWO_PASS, SJ_ONE_PASS, SJ_ONE_PASS_HEUR, SJ_AUTO = range(4)
+SJ_SWEEP_ADAPTIVE = 1
 MODES = {"two_pass": SJ_TWO_PASS, "one_pass": SJ_ONE_PASS, "one_pass_heur": SJ_ONE_PASS_HEUR,
          "auto": SJ_AUTO}
 
@@ -39,7 +40,7 @@ class sj_grid(ctypes.Structure):
 
 class sj_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("sort_output", ctypes.c_int32),
-                ("margin", ctypes.c_float), ("reserved", ctypes.c_int32)]
+                ("margin", ctypes.c_float), ("flags", ctypes.c_int32)]
 
 
 class sj_part_view(ctypes.Structure):
@@ -57,7 +58,8 @@ class sj_stats(ctypes.Structure):
                 ("work_items", ctypes.c_int64), ("l1_entries_r", ctypes.c_int64),
                 ("l1_entries_s", ctypes.c_int64), ("entries_r", ctypes.c_int64),
                 ("entries_s", ctypes.c_int64), ("npairs", ctypes.c_int64), ("one_pass", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("capacity", ctypes.c_int64), ("refit_items", ctypes.c_int64)]
+                ("pad", ctypes.c_int32), ("capacity", ctypes.c_int64), ("refit_items", ctypes.c_int64),
+                ("y_sweep_tiles", ctypes.c_int64)]
 
 
 SJ_MLP_FEATURES = 32
@@ -101,6 +103,7 @@ SIGNATURES = [
     ("sj_mlp_forward", I32, [P, P, P, I64, P]),
     ("sj_mlp_grad", I32, [P, P, P, P, I64, P, P]),
     ("sj_mlp_train_step", I32, [P, P, P, P, I64, ctypes.c_float, P]),
+    ("sj_tile_axes", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), P]),
     ("sj_block_features", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), P, P, P, I64, ctypes.POINTER(I64)]),
     ("sj_set_model", I32, [P, P]),
     ("sj_extent_stats", I32, [P, P, I64, P, I64, P]),
@@ -141,9 +144,13 @@ def make_grid(nx: int, ny: int | None = None, x0=0.0, y0=0.0, x1=1.0, y1=1.0) ->
     return sj_grid(int(nx), int(nx if ny is None else ny), x0, y0, x1, y1)
 
 
-def make_opts(mode="two_pass", sort_output=False, margin=0.25) -> sj_opts:
+def make_opts(mode="two_pass", sort_output=False, margin=0.25, axis="x") -> sj_opts:
+    """axis: "x" (Algorithm 1 along x in every tile) or "adaptive" (per tile,
+    the axis with the smaller Eq. 2 estimate, SJ_SWEEP_ADAPTIVE)."""
     m = MODES[mode] if isinstance(mode, str) else int(mode)
-    return sj_opts(m, int(bool(sort_output)), float(margin), 0)
+    if axis not in ("x", "adaptive"):
+        raise ValueError("axis must be 'x' or 'adaptive'")
+    return sj_opts(m, int(bool(sort_output)), float(margin), SJ_SWEEP_ADAPTIVE if axis == "adaptive" else 0)
 
 
 class _TorchAllocator:
@@ -325,6 +332,16 @@ def sj_tile_stats(ctx: Context, R, S, grid: sj_grid):
     _check(ctx.handle, lib.sj_tile_stats(ctx.handle, pr, nr, ps, ns, ctypes.byref(grid),
                                          cr.data_ptr(), cs.data_ptr(), tp.data_ptr()))
     return cr, cs, tp
+
+
+def sj_tile_axes(ctx: Context, R, S, grid: sj_grid) -> torch.Tensor:
+    """uint8[ny * nx] device tensor: the sweep axis SJ_SWEEP_ADAPTIVE gives
+    every tile (1 = y), from the Eq. 2 histograms of Sec. 3.3."""
+    pr, nr = _rects(R, ctx.device)
+    ps, ns = _rects(S, ctx.device)
+    out = torch.empty(int(grid.nx) * int(grid.ny), dtype=torch.uint8, device=ctx.device)
+    _check(ctx.handle, load().sj_tile_axes(ctx.handle, pr, nr, ps, ns, ctypes.byref(grid), out.data_ptr()))
+    return out
 
 
 def sj_join_host_many(ctx: Context, Rs, Ss, grids, outs, opts: sj_opts | None = None) -> list[int]:
