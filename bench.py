@@ -54,16 +54,21 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
                     help="CPU sample: rectangles whose centre has y < frac")
-    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance", "aniso"],
+    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance", "aniso", "bands"],
                     help="gis: the 10M x 20M GIS-shaped join (default); batch: 256 joins of uneven size; "
                          "skew: the 20M x 20M Zipf extent / skew stress; aniso: 10M x 20M elongated "
-                         "rectangles, sweep along x against the adaptive axis of Sec. 3.3")
+                         "rectangles, sweep along x against the adaptive axis of Sec. 3.3; bands: the gis join "
+                         "split into one band of tile rows per rank (the default for gis with N > 1)")
     ap.add_argument("--aniso-grids", default="1750,600",
                     help="aniso: grids to time (1750: the tile-extent rule; 600: coarse tiles)")
     ap.add_argument("--rho", type=float, default=2.1e-4,
                     help="skew: probability that S shares R's hot spots (2.1e-4: about 1e9 pairs)")
     ap.add_argument("--skew-grid", type=int, default=500,
                     help="skew: tiles per axis (500: fastest of 500-3000 on this workload)")
+    ap.add_argument("--split", default="bands", choices=["bands", "instances"],
+                    help="gis with N > 1 ranks: bands = one join split into N bands of tile rows balanced by "
+                         "entries (strong scaling, each rank stages its band's rectangles); instances = an "
+                         "independent join per rank (weak scaling)")
     ap.add_argument("--joins", type=int, default=256)
     ap.add_argument("--eps", type=float, default=5e-5, help="distance of the eps-distance join")
     ap.add_argument("--dist-grid", type=int, default=2000, help="grid of the eps-distance join")
@@ -633,6 +638,88 @@ def distance_arm(args):
     sjdist.teardown(env)
 
 
+def bands_arm(args):
+    """One GIS-shaped join (10M x 20M, seed 2, grid 3000) split over the N
+    ranks by contiguous bands of tile rows balanced by entries per row
+    (dist.band_plan).  Each rank stages only the rectangles that overlap its
+    band (dist.band_members) on its GPU and joins its band (sj_join_rows,
+    learned one-pass): the pairs whose reference tile lies in the band.  The
+    union over ranks is the join; no pair moves between ranks.  Strong
+    scaling: value = all pairs / the slowest rank's time.  e2e: every step
+    copies the band's rectangles from pinned host memory, joins and copies
+    the pairs back."""
+    import torch
+
+    from paper_1908_11740_gb300 import build, learn, sj
+
+    env = sjdist.setup("nccl")
+    torch.cuda.set_device(env.local_rank)
+    build.build()
+    R, S = inputs.gis_pair(args.n_r, args.n_s, seed=args.seed)
+    ctx = sj.sj_create(env.local_rank)
+    grid = sj.make_grid(args.grid)
+    bands = sjdist.band_plan(sjdist.row_loads(R, S, grid), env.world)
+    row0, row1 = bands[env.rank]
+    ir, is_ = sjdist.band_members(R, S, grid, row0, row1)
+    hR = torch.from_numpy(np.ascontiguousarray(R[ir])).pin_memory()
+    hS = torch.from_numpy(np.ascontiguousarray(S[is_])).pin_memory()
+    dR, dS = hR.cuda(), hS.cuda()
+    model, _ = learn.load(ctx, args.model or learn.DEFAULT_MODEL)
+    sj.sj_set_model(ctx, model)
+    opts = sj.make_opts(args.mode)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        P = sj.sj_join_rows(ctx, dR, dS, grid, row0, row1, opts).shape[0]
+    torch.cuda.synchronize()
+    clocks = ClockSampler(env.local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    sjdist.barrier(env)
+    torch.cuda.synchronize()
+    sj.sj_timing_enable(ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        out = sj.sj_join_rows(ctx, dR, dS, grid, row0, row1, opts)
+        del out
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sjdist.barrier(env)
+    tm = sj.sj_timing_read(ctx)
+    clk = clocks.stop()
+    ms, P_all = sjdist.reduce_result(ev0.elapsed_time(ev1) / args.steps, P, env)
+    # end to end: the band's rectangles host -> device, join, pairs -> host
+    e2e_steps = max(3, min(args.steps, 20))
+    sjdist.barrier(env)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        dR.copy_(hR, non_blocking=True)
+        dS.copy_(hS, non_blocking=True)
+        host = sj.sj_join_rows(ctx, dR, dS, grid, row0, row1, opts).cpu()
+    torch.cuda.synchronize()
+    e2e_ms, _ = sjdist.reduce_result((time.perf_counter() - t0) * 1e3 / e2e_steps, P, env)
+    assert host.shape[0] == P
+    if env.rank == 0:
+        line = {"metric": METRIC, "value": P_all / (ms / 1e3), "unit": UNIT, "n_gpus": env.world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_name(args), "grid": args.grid, "mode": args.mode,
+                           "split": f"{env.world} bands of tile rows balanced by entries: {bands}",
+                           "pairs": P_all, "l2": "inputs 480 MB > 129 MB L2 (no flush needed)"},
+                "e2e": {"value": P_all / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                        "h2d_bytes_per_step": 16 * (len(ir) + len(is_)), "d2h_bytes_per_step": 8 * P,
+                        "api": "rank 0's band: copy of its rectangles, sj_join_rows, copy of its pairs"},
+                "gpu_launches": tm["launches"], "clocks": clk,
+                "phases_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in tm.items()
+                                       if k != "launches" and v[0]}}
+        print(json.dumps(line), flush=True)
+    sj.sj_set_model(ctx, None)
+    model.free()
+    sj.sj_destroy(ctx)
+    sjdist.teardown(env)
+
+
 def aniso_arm(args):
     """Adaptive sweep axis (Sec. 3.3): |R| = 10M, |S| = 20M rectangles ten
     times longer along one axis than the other (half the mixture components
@@ -723,6 +810,8 @@ def main():
         distance_arm(args)
     elif args.workload == "aniso":
         aniso_arm(args)
+    elif args.workload == "bands" or (int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.split == "bands"):
+        bands_arm(args)
     else:
         ours(args)
 

@@ -191,6 +191,26 @@ int sj_tile_stats(sj_ctx *ctx, const sj_rect *d_R, int64_t nR,
                   const sj_rect *d_S, int64_t nS, const sj_grid *g,
                   uint32_t *d_cnt_r, uint32_t *d_cnt_s, uint32_t *d_pairs_per_tile);
 
+/* ---- one band of tile rows (several GPUs on one join) ------------------- */
+/* The pairs of R join S on grid *g whose reference point (Eq. 1) lies in
+ * tile rows [row0, row1) (0 <= row0 <= row1 <= ny).  The tiles are
+ * independent tasks and every pair is reported by exactly one tile (Sec. 1,
+ * Sec. 3.2), so bands that cover the rows once give disjoint pair sets whose
+ * union is the join: one GPU per band joins one input without exchanging
+ * pairs.  Only the rectangles that overlap the band's rows take part (the
+ * call selects them); a caller that stages only those rectangles on a GPU
+ * gets the same pairs in the indices of what it passed.  Ids are indices
+ * into d_R / d_S as given.  Output contract as sj_join / sj_join_into (pair
+ * order unspecified unless sort_output; SJ_EOVERFLOW with the required count
+ * for a too small buffer).  Synchronises twice (band sizes, pair count).
+ * SJ_EINVAL for a band outside the grid. */
+int sj_join_rows(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+                 const sj_grid *g, int32_t row0, int32_t row1, const sj_opts *o,
+                 sj_pair **d_pairs, int64_t *npairs);
+int sj_join_rows_into(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
+                      const sj_grid *g, int32_t row0, int32_t row1, const sj_opts *o,
+                      sj_pair *d_buf, int64_t cap, int64_t *npairs);
+
 /* The sweep axis SJ_SWEEP_ADAPTIVE gives every tile of a join on grid *g
  * (Sec. 3.3, Eq. 2 with k = 8 divisions per tile axis): d_axis is a
  * caller-owned device uint8[nx * ny], row-major; 1 = swept along y, 0 = x

@@ -36,6 +36,7 @@ struct Workspace {
     Buf bScanPart;                                 // block scan: sums per chunk of blocks
     Buf lstart, lcoff, lvb;                        // candidate-parallel sweep of the large tiles
     Buf dsq_r, dsq_s, dmask, dcnt, doff, dstats;   // eps-distance join: squares, refinement
+    Buf band_r, band_s, band_ir, band_is;          // row band of a join: its rectangles and their indices
     unsigned long long bcap_r = 0, bcap_s = 0;
     unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
     long long T = 0;

@@ -90,6 +90,10 @@ SIGNATURES = [
     ("sj_join_into", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), ctypes.POINTER(sj_opts),
                            P, I64, ctypes.POINTER(I64)]),
     ("sj_tile_stats", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), P, P, P]),
+    ("sj_join_rows", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), I32, I32, ctypes.POINTER(sj_opts),
+                           ctypes.POINTER(P), ctypes.POINTER(I64)]),
+    ("sj_join_rows_into", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), I32, I32, ctypes.POINTER(sj_opts),
+                                P, I64, ctypes.POINTER(I64)]),
     ("sj_join_host", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), ctypes.POINTER(sj_opts),
                            P, I64, ctypes.POINTER(I64)]),
     ("sj_timing_enable", I32, [P, I32]),
@@ -235,6 +239,39 @@ def sj_join(ctx: Context, R: torch.Tensor, S: torch.Tensor, grid: sj_grid,
         return torch.empty((0, 2), dtype=torch.int32, device=ctx.device)
     buf = ctx.allocator.take(out.value)
     return buf[: 8 * n.value].view(torch.int32).view(n.value, 2)
+
+
+def sj_join_rows(ctx: Context, R: torch.Tensor, S: torch.Tensor, grid: sj_grid, row0: int, row1: int,
+                 opts: sj_opts | None = None) -> torch.Tensor:
+    """The pairs whose reference tile (Eq. 1) lies in tile rows [row0, row1):
+    one band's share of the join, int32[P, 2] CUDA tensor (ids into R, S)."""
+    lib = load()
+    pr, nr = _rects(R, ctx.device)
+    ps, ns = _rects(S, ctx.device)
+    out = ctypes.c_void_p()
+    n = ctypes.c_int64()
+    st = lib.sj_join_rows(ctx.handle, pr, nr, ps, ns, ctypes.byref(grid), int(row0), int(row1),
+                          ctypes.byref(opts) if opts is not None else None, ctypes.byref(out), ctypes.byref(n))
+    _check(ctx.handle, st)
+    if n.value == 0:
+        return torch.empty((0, 2), dtype=torch.int32, device=ctx.device)
+    buf = ctx.allocator.take(out.value)
+    return buf[: 8 * n.value].view(torch.int32).view(n.value, 2)
+
+
+def sj_join_rows_into(ctx: Context, R, S, grid: sj_grid, row0: int, row1: int, out: torch.Tensor,
+                      opts: sj_opts | None = None) -> int:
+    """sj_join_rows into a caller buffer (int32[cap, 2] CUDA tensor); returns
+    the pair count, raises SJError(SJ_EOVERFLOW) when cap is too small."""
+    lib = load()
+    pr, nr = _rects(R, ctx.device)
+    ps, ns = _rects(S, ctx.device)
+    n = ctypes.c_int64()
+    st = lib.sj_join_rows_into(ctx.handle, pr, nr, ps, ns, ctypes.byref(grid), int(row0), int(row1),
+                               ctypes.byref(opts) if opts is not None else None,
+                               out.data_ptr() if out.shape[0] else None, int(out.shape[0]), ctypes.byref(n))
+    _check(ctx.handle, st)
+    return n.value
 
 
 def sj_join_into(ctx: Context, R, S, grid: sj_grid, out: torch.Tensor,

@@ -79,6 +79,25 @@ def test_gis_full_size_exact(sj, data, ctx, K, mode):
         np.testing.assert_array_equal(srt, want)
 
 
+def test_gis_full_size_bands(sj, data, ctx):
+    """The 10M x 20M join split into 4 bands of tile rows balanced by entries
+    (one band per GPU when four GPUs share the join), run band after band:
+    the union of the bands is the oracle's join, no pair twice."""
+    from paper_1908_11740_gb300 import dist
+
+    R, S, want = data
+    c, model = ctx
+    sj.sj_set_model(c, model)
+    g = sj.make_grid(3000)
+    bands = dist.band_plan(dist.row_loads(R, S, g), 4)
+    dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
+    parts = [sj.sj_join_rows(c, dR, dS, g, r0, r1, sj.make_opts("one_pass")).cpu().numpy() for r0, r1 in bands]
+    assert all(len(p) for p in parts)
+    union = np.concatenate(parts)
+    np.testing.assert_array_equal(sorted_pairs(union), want)
+    assert len(union) == len(want)
+
+
 def test_fresh_seed_learned_vs_eq2(sj, ctx):
     """Config 5's evaluation: a fresh seed of the GIS-shaped layers, grid 3000."""
     c, model = ctx
