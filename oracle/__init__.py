@@ -7,6 +7,9 @@ written from the paper ("Parallel In-Memory Evaluation of Spatial Joins"):
 * ``sweep``  -- Algorithm 1, forward-scan plane sweep over the whole space (C);
 * ``pbsm``   -- uniform-grid PBSM with replication, per-tile sort by x_l,
   Algorithm 1 per tile and the reference-point test of Eq. 1 (C);
+* ``pbsm_gbda`` -- PBSM with grouping-based duplicate avoidance: four
+  classes per tile by where the projections begin, 9 of the 16 group-group
+  joins, no duplicate test (C);
 * ``pbsm_digest`` -- the same PBSM with the pairs folded into an
   order-independent digest (count, sum and xor of the SplitMix64 output
   function of each pair) instead of stored: the check of 1e9-pair joins;
@@ -131,6 +134,8 @@ def _configure(lib):
     lib.orc_sweep.argtypes = [P, I64, P, I64, P]
     lib.orc_pbsm_ex.restype = P
     lib.orc_pbsm_ex.argtypes = [P, I64, P, I64, I, I, F, F, F, F, P, P, P, P]
+    lib.orc_pbsm_gbda.restype = P
+    lib.orc_pbsm_gbda.argtypes = [P, I64, P, I64, I, I, F, F, F, F]
     lib.orc_pbsm_digest.restype = I
     lib.orc_pbsm_digest.argtypes = [P, I64, P, I64, I, I, F, F, F, F, P]
     lib.orc_res_count.restype = I64
@@ -229,6 +234,17 @@ def pbsm(R, S, nx: int, ny: int | None = None, x0: float = 0.0, y0: float = 0.0,
     if per_tile:
         return out, {"cnt_r": cr, "cnt_s": cs, "pairs": tp, "cand": nc.value}
     return out
+
+
+def pbsm_gbda(R, S, nx: int, ny: int | None = None, x0: float = 0.0, y0: float = 0.0,
+              x1: float = 1.0, y1: float = 1.0) -> np.ndarray:
+    """PBSM with grouping-based duplicate avoidance (classes A-D per tile,
+    the 9 group-group joins that can report a pair first, no duplicate
+    test); int32[P, 2] sorted."""
+    lib = _load()
+    ny = nx if ny is None else ny
+    R, S = _rects(R), _rects(S)
+    return _take(lib, lib.orc_pbsm_gbda(R.ctypes.data, len(R), S.ctypes.data, len(S), nx, ny, x0, y0, x1, y1))
 
 
 def pbsm_digest(R, S, nx: int, ny: int | None = None, x0: float = 0.0, y0: float = 0.0,

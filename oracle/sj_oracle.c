@@ -22,7 +22,10 @@
  *                 first, then written, Sec. 3.4 steps 2-4), each tile is
  *                 sorted by x_l and joined with Algorithm 1, and a pair is
  *                 reported only where its reference point lies (Eq. 1).
- * All three return the pairs sorted by (r, s).  orc_pbsm_digest runs orc_pbsm
+ * All three return the pairs sorted by (r, s).  orc_pbsm_gbda is PBSM with the
+ * grouping-based duplicate avoidance instead of the test of Eq. 1 (class
+ * groups per tile, 9 of the 16 group-group joins, no duplicate test).
+ * orc_pbsm_digest runs orc_pbsm
  * but folds every reported pair into an order-independent digest (count,
  * sum and xor of a 64-bit mix of the pair) instead of storing it, for
  * result sets too large to hold on the host (1e9 pairs).
@@ -376,6 +379,92 @@ orc_res *orc_pbsm(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
                   int nx, int ny, float x0, float y0, float x1, float y1)
 {
     return orc_pbsm_ex(R, nR, S, nS, nx, ny, x0, y0, x1, y1, NULL, NULL, NULL, NULL);
+}
+
+/* ---- GBDA: duplicate avoidance by mini-joins of rectangle classes --------
+ * Each tile's rectangles of R (and of S) are divided into four classes by
+ * where their projections begin (the section on grouping-based duplicate
+ * avoidance that follows Eq. 1):
+ *   A: x_l >= T.x_l and y_l >= T.y_l     B: x_l >= T.x_l and y_l < T.y_l
+ *   C: x_l <  T.x_l and y_l >= T.y_l     D: x_l <  T.x_l and y_l < T.y_l
+ * ("v >= T.x_l" read as cell(v) >= the tile's column, as for Eq. 1).  Of the
+ * 16 group-group joins, the 7 that can only produce pairs reported in an
+ * earlier tile are not evaluated; the 9 below are, each with Algorithm 1 on
+ * the two groups sorted by x_l, and with no duplicate test. */
+enum { CL_A = 0, CL_B = 1, CL_C = 2, CL_D = 3 };
+static const int gbda_joins[][2] = {
+    {CL_A, CL_A}, {CL_A, CL_B}, {CL_A, CL_C}, {CL_A, CL_D},
+    {CL_B, CL_A}, {CL_C, CL_A}, {CL_D, CL_A},
+    {CL_B, CL_C}, {CL_C, CL_B},
+};
+
+static int gbda_class(const orc_ent *e, int col, int row, const grid_t *g)
+{
+    int xin = cell_of(e->xl, g->gx0, g->ginvx, g->nx) >= col;
+    int yin = cell_of(e->yl, g->gy0, g->ginvy, g->ny) >= row;
+    if (xin && yin) return CL_A;
+    if (xin) return CL_B;
+    if (yin) return CL_C;
+    return CL_D;
+}
+
+/* Stable split of one tile's entries into the four class groups (written to
+ * out, group k at out + start[k], start[4] = n). */
+static void gbda_groups(const orc_ent *E, int64_t n, int col, int row, const grid_t *g,
+                        orc_ent *out, int64_t *start)
+{
+    int64_t cnt[4] = {0, 0, 0, 0};
+    for (int64_t k = 0; k < n; k++) cnt[gbda_class(&E[k], col, row, g)]++;
+    start[0] = 0;
+    for (int c = 0; c < 4; c++) start[c + 1] = start[c] + cnt[c];
+    int64_t cur[4] = {start[0], start[1], start[2], start[3]};
+    for (int64_t k = 0; k < n; k++) out[cur[gbda_class(&E[k], col, row, g)]++] = E[k];
+}
+
+orc_res *orc_pbsm_gbda(const orc_rect *R, int64_t nR, const orc_rect *S, int64_t nS,
+                       int nx, int ny, float x0, float y0, float x1, float y1)
+{
+    if (nx < 1 || ny < 1 || !(x1 > x0) || !(y1 > y0)) return NULL;
+    grid_t g = make_grid(nx, ny, x0, y0, x1, y1);
+    int64_t T = (int64_t)nx * ny;
+    int64_t *cr = (int64_t *)malloc((size_t)T * sizeof(int64_t));
+    int64_t *cs = (int64_t *)malloc((size_t)T * sizeof(int64_t));
+    int64_t *orr = (int64_t *)malloc((size_t)(T + 1) * sizeof(int64_t));
+    int64_t *os = (int64_t *)malloc((size_t)(T + 1) * sizeof(int64_t));
+    orc_res *res = res_new();
+    orc_ent *er = NULL, *es = NULL, *gr = NULL, *gs = NULL;
+    if (!cr || !cs || !orr || !os || !res) goto fail;
+    er = partition(R, nR, &g, cr, orr);
+    es = partition(S, nS, &g, cs, os);
+    if (!er || !es) goto fail;
+    gr = (orc_ent *)malloc((size_t)(orr[T] ? orr[T] : 1) * sizeof(orc_ent));
+    gs = (orc_ent *)malloc((size_t)(os[T] ? os[T] : 1) * sizeof(orc_ent));
+    if (!gr || !gs) goto fail;
+    dedup_ctx none;
+    memset(&none, 0, sizeof none);   /* no duplicate test */
+    for (int64_t t = 0; t < T; t++) {
+        int64_t nr = cr[t], ns = cs[t];
+        if (!nr || !ns) continue;
+        int col = (int)(t % nx), row = (int)(t / nx);
+        int64_t sr[5], ss[5];
+        orc_ent *rt = gr + orr[t], *st = gs + os[t];
+        gbda_groups(er + orr[t], nr, col, row, &g, rt, sr);
+        gbda_groups(es + os[t], ns, col, row, &g, st, ss);
+        for (int c = 0; c < 4; c++) {
+            qsort(rt + sr[c], (size_t)(sr[c + 1] - sr[c]), sizeof(orc_ent), cmp_ent_xl);
+            qsort(st + ss[c], (size_t)(ss[c + 1] - ss[c]), sizeof(orc_ent), cmp_ent_xl);
+        }
+        for (size_t k = 0; k < sizeof gbda_joins / sizeof gbda_joins[0]; k++) {
+            int a = gbda_joins[k][0], b = gbda_joins[k][1];
+            alg1(rt + sr[a], sr[a + 1] - sr[a], st + ss[b], ss[b + 1] - ss[b], &none, res, NULL);
+        }
+    }
+    free(cr); free(cs); free(orr); free(os); free(er); free(es); free(gr); free(gs);
+    return res_finish(res);
+fail:
+    free(cr); free(cs); free(orr); free(os); free(er); free(es); free(gr); free(gs);
+    orc_res_free(res);
+    return NULL;
 }
 
 /* ---- sweep axis of a tile (Sec. 3.3, Eq. 2) ---------------------------
