@@ -54,11 +54,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
                     help="CPU sample: rectangles whose centre has y < frac")
-    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance", "aniso", "bands"],
+    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance", "aniso", "bands", "gbda"],
                     help="gis: the 10M x 20M GIS-shaped join (default); batch: 256 joins of uneven size; "
                          "skew: the 20M x 20M Zipf extent / skew stress; aniso: 10M x 20M elongated "
                          "rectangles, sweep along x against the adaptive axis of Sec. 3.3; bands: the gis join "
-                         "split into one band of tile rows per rank (the default for gis with N > 1)")
+                         "split into one band of tile rows per rank (the default for gis with N > 1); gbda: "
+                         "the gis join with Eq. 1 against GBDA duplicate avoidance")
     ap.add_argument("--aniso-grids", default="1750,600",
                     help="aniso: grids to time (1750: the tile-extent rule; 600: coarse tiles)")
     ap.add_argument("--rho", type=float, default=2.1e-4,
@@ -720,6 +721,49 @@ def bands_arm(args):
     sjdist.teardown(env)
 
 
+def _variant_table(args, env, ctx, dR, dS, grids, variants):
+    """ms per join of every (grid, mode, variant) with inputs resident, CUDA
+    events on the stream; returns ({name: result}, launches of the first)."""
+    import torch
+
+    from paper_1908_11740_gb300 import sj
+
+    stream = torch.cuda.current_stream()
+    steps = max(3, min(args.steps, 20))
+    results, first_launches = {}, None
+    for K in grids:
+        g = sj.make_grid(K)
+        for mode in ("two_pass", "one_pass"):
+            for vname, kw in variants:
+                o = sj.make_opts(mode, **kw)
+                for _ in range(max(3, args.warmup)):
+                    sj.sj_join(ctx, dR, dS, g, o)
+                torch.cuda.synchronize()
+                sjdist.barrier(env)
+                sj.sj_timing_enable(ctx, True)
+                ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                for _ in range(steps):
+                    out = sj.sj_join(ctx, dR, dS, g, o)
+                    P = out.shape[0]
+                    del out
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                sjdist.barrier(env)
+                tm = sj.sj_timing_read(ctx)
+                sj.sj_timing_enable(ctx, False)
+                st = sj.sj_last_stats(ctx)
+                ph = {k: round(v[1] / steps, 4) for k, v in tm.items() if k != "launches" and v[0]}
+                if first_launches is None:
+                    first_launches = tm["launches"] // steps
+                results[f"K{K} {mode} {vname}"] = {
+                    "ms_per_step": round(ev0.elapsed_time(ev1) / steps, 4), "pairs": P,
+                    "block_join_ms": ph.get("sweep_write"), "count_pass_ms": ph.get("sweep_count"),
+                    "y_sweep_tiles": st["y_sweep_tiles"], "gbda": st["dedup"],
+                    "path": "two-level" if st["path"] == 1 else "single-level"}
+    return results, first_launches, steps
+
+
 def aniso_arm(args):
     """Adaptive sweep axis (Sec. 3.3): |R| = 10M, |S| = 20M rectangles ten
     times longer along one axis than the other (half the mixture components
@@ -739,57 +783,63 @@ def aniso_arm(args):
     ctx = sj.sj_create(env.local_rank)
     model, _ = learn.load(ctx, args.model or learn.DEFAULT_MODEL)
     sj.sj_set_model(ctx, model)
-    stream = torch.cuda.current_stream()
-    steps = max(3, min(args.steps, 20))
-
-    def timed(g, o):
-        for _ in range(max(3, args.warmup)):
-            sj.sj_join(ctx, dR, dS, g, o)
-        torch.cuda.synchronize()
-        sjdist.barrier(env)
-        sj.sj_timing_enable(ctx, True)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(steps):
-            out = sj.sj_join(ctx, dR, dS, g, o)
-            P = out.shape[0]
-            del out
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        sjdist.barrier(env)
-        tm = sj.sj_timing_read(ctx)
-        sj.sj_timing_enable(ctx, False)
-        st = sj.sj_last_stats(ctx)
-        ph = {k: round(v[1] / steps, 4) for k, v in tm.items() if k != "launches" and v[0]}
-        return ev0.elapsed_time(ev1) / steps, P, st, ph, tm["launches"]
-
     clocks = ClockSampler(env.local_rank)
     clocks.start()
     time.sleep(0.3)
-    results, head, launches = {}, None, 0
-    for K in [int(k) for k in args.aniso_grids.split(",")]:
-        g = sj.make_grid(K)
-        for mode in ("two_pass", "one_pass"):
-            for axis in ("x", "adaptive"):
-                ms, P, st, ph, nl = timed(g, sj.make_opts(mode, axis=axis))
-                results[f"K{K} {mode} {axis}"] = {
-                    "ms_per_step": round(ms, 4), "pairs": P, "block_join_ms": ph.get("sweep_write"),
-                    "count_pass_ms": ph.get("sweep_count"), "y_sweep_tiles": st["y_sweep_tiles"],
-                    "path": "two-level" if st["path"] == 1 else "single-level"}
-                if head is None and mode == "one_pass" and axis == "adaptive":
-                    head = (K, ms, P)
-                    launches = nl
+    grids = [int(k) for k in args.aniso_grids.split(",")]
+    results, launches, steps = _variant_table(args, env, ctx, dR, dS, grids,
+                                              [("x", {"axis": "x"}), ("adaptive", {"axis": "adaptive"})])
     clk = clocks.stop()
-    K, ms, P = head
-    ms, P_all = sjdist.reduce_result(ms, P, env)
+    head = results[f"K{grids[0]} one_pass adaptive"]
+    ms, P_all = sjdist.reduce_result(head["ms_per_step"], head["pairs"], env)
     if env.rank == 0:
         line = {"metric": METRIC + " (adaptive sweep axis, elongated rectangles)", "value": P_all / (ms / 1e3),
                 "unit": UNIT, "n_gpus": env.world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": f"elongated rectangles |R|={args.n_r:,} |S|={args.n_s:,}, aspect 10, "
-                                       f"GIS-shaped mixture centres, grid {K}x{K}, learned one-pass, adaptive axis",
-                           "pairs": P},
+                                       f"GIS-shaped mixture centres, grid {grids[0]}x{grids[0]}, learned one-pass, "
+                                       f"adaptive axis", "pairs": head["pairs"]},
+                "compare": results, "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    sj.sj_set_model(ctx, None)
+    model.free()
+    sj.sj_destroy(ctx)
+    sjdist.teardown(env)
+
+
+def gbda_arm(args):
+    """Duplicate avoidance: the GIS-shaped 10M x 20M join with the
+    reference-point test of Eq. 1 against GBDA (class mini-joins, no test per
+    pair), two-pass and learned one-pass, at the rule-of-thumb grid and at a
+    coarse grid; inputs resident."""
+    import torch
+
+    from paper_1908_11740_gb300 import build, learn, sj
+
+    env = sjdist.setup("nccl")
+    torch.cuda.set_device(env.local_rank)
+    build.build()
+    R, S = inputs.gis_pair(args.n_r, args.n_s, seed=sjdist.instance_seed(args.seed, env))
+    dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
+    ctx = sj.sj_create(env.local_rank)
+    model, _ = learn.load(ctx, args.model or learn.DEFAULT_MODEL)
+    sj.sj_set_model(ctx, model)
+    clocks = ClockSampler(env.local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    grids = [args.grid, 1000]
+    results, launches, steps = _variant_table(args, env, ctx, dR, dS, grids,
+                                              [("refpoint", {"dedup": "refpoint"}), ("gbda", {"dedup": "gbda"})])
+    clk = clocks.stop()
+    head = results[f"K{grids[0]} one_pass gbda"]
+    ms, P_all = sjdist.reduce_result(head["ms_per_step"], head["pairs"], env)
+    if env.rank == 0:
+        line = {"metric": METRIC + " (GBDA duplicate avoidance)", "value": P_all / (ms / 1e3),
+                "unit": UNIT, "n_gpus": env.world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": workload_name(args) + ", learned one-pass, GBDA", "pairs": head["pairs"]},
                 "compare": results, "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     sj.sj_set_model(ctx, None)
@@ -810,6 +860,8 @@ def main():
         distance_arm(args)
     elif args.workload == "aniso":
         aniso_arm(args)
+    elif args.workload == "gbda":
+        gbda_arm(args)
     elif args.workload == "bands" or (int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.split == "bands"):
         bands_arm(args)
     else:

@@ -93,12 +93,23 @@ typedef struct { int32_t nx, ny; float x0, y0, x1, y1; } sj_grid;
                                 only: the single-level path (tiles beyond shared
                                 memory) and batches sweep along x.  The pairs
                                 are the same either way.  See sj_tile_axes.      */
+#define SJ_DEDUP_GBDA     2  /* grouping-based duplicate avoidance instead of the
+                                reference-point test of Eq. 1: the entries of a
+                                tile are grouped in four classes by where their
+                                projections begin (A: in the tile on x and y,
+                                B: on x only, C: on y only, D: neither), and
+                                only the 9 class pairs that can report a pair
+                                in this tile are joined (A with any, any with A,
+                                B with C, C with B), with no test per pair.  The
+                                pairs are the same.  Two-level path of single
+                                joins; the single-level path and batches use
+                                Eq. 1.  Not combinable with SJ_SWEEP_ADAPTIVE.  */
 
 typedef struct {
     int32_t mode;         /* one of the modes above                          */
     int32_t sort_output;  /* nonzero: pairs ascending by (r, s)              */
     float   margin;       /* one-pass capacity = predicted * (1 + margin) + slack */
-    int32_t flags;        /* SJ_SWEEP_ADAPTIVE or 0; other bits: SJ_EINVAL   */
+    int32_t flags;        /* SJ_SWEEP_ADAPTIVE, SJ_DEDUP_GBDA or 0           */
 } sj_opts;
 
 typedef struct sj_ctx sj_ctx;     /* device, stream, allocator, workspace    */
@@ -351,7 +362,7 @@ typedef struct {
     int64_t entries_r, entries_s;
     int64_t npairs;
     int32_t one_pass;            /* 1 if the last join ran one-pass          */
-    int32_t pad;
+    int32_t dedup;               /* 1 if the two-level join used GBDA, 0: Eq. 1 */
     int64_t capacity;            /* one-pass: pairs the output was sized for */
     int64_t refit_items;         /* one-pass: blocks re-run because they did not fit */
     int64_t y_sweep_tiles;       /* SJ_SWEEP_ADAPTIVE: tiles swept along y    */

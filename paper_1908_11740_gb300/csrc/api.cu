@@ -760,7 +760,8 @@ int sj::enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, con
 // entries than shared memory (the caller then runs the single-level path).
 int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const float4 *R,
                                    long long nR, const float4 *S, long long nS, const GridDev &g,
-                                   Stats *stats, bool *use_direct, bool adaptive, unsigned char *tile_axis) {
+                                   Stats *stats, bool *use_direct, int flags, unsigned char *tile_axis) {
+    const bool adaptive = flags & SJ_SWEEP_ADAPTIVE;
     *use_direct = false;
     w.bcap_r = std::max<unsigned long long>(w.bcap_r, (unsigned long long)nR + nR / 8 + 1024);
     w.bcap_s = std::max<unsigned long long>(w.bcap_s, (unsigned long long)nS + nS / 8 + 1024);
@@ -770,6 +771,7 @@ int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const
         BArgs a = blocked_args(w, p, R, nR, S, nS, g);
         if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
         a.adaptive = adaptive;
+        a.gbda = (flags & SJ_DEDUP_GBDA) != 0;
         if ((st = enqueue_blocked_partition(ctx, w, p, a))) return st;
         cudaError_t e;
         {
@@ -804,6 +806,7 @@ int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const
         ctx->last.l1_entries_s = (int64_t)stats->e_s;
         ctx->last.npairs = (int64_t)stats->npairs;
         ctx->last.y_sweep_tiles = adaptive ? (int64_t)stats->naxis_y : 0;
+        ctx->last.dedup = (flags & SJ_DEDUP_GBDA) ? 1 : 0;
         return SJ_OK;
     }
     return fail(ctx, SJ_EINTERNAL, "blocked workspace did not converge");
@@ -823,11 +826,11 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
     Stats stats;
     int st;
     BPlan bp;
-    const bool adaptive = o && (o->flags & SJ_SWEEP_ADAPTIVE);
+    const int flags = o ? o->flags : 0;
     if (plan_blocked(ctx, gd, nR, nS, bp)) {
         bool direct = false;
         if ((st = blocked_partition_count(ctx, w, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd,
-                                          &stats, &direct, adaptive)))
+                                          &stats, &direct, flags)))
             return st;
         if (!direct) {
             const unsigned long long P = stats.npairs;
@@ -836,7 +839,8 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
             if (P == 0) return SJ_OK;
             BArgs a = blocked_args(w, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd);
             if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
-            a.adaptive = adaptive;
+            a.adaptive = (flags & SJ_SWEEP_ADAPTIVE) != 0;
+            a.gbda = (flags & SJ_DEDUP_GBDA) != 0;
             BJoinOut bo = bjoin_out(w, 1);
             bo.out = os.got;
             bo.cap = P;
@@ -863,7 +867,10 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
 
 int sj::check_opts(sj_ctx *ctx, const sj_opts *o) {
     if (!o) return SJ_OK;
-    if (o->flags & ~SJ_SWEEP_ADAPTIVE) return fail(ctx, SJ_EINVAL, "unknown sj_opts.flags bits 0x%x", o->flags);
+    if (o->flags & ~(SJ_SWEEP_ADAPTIVE | SJ_DEDUP_GBDA))
+        return fail(ctx, SJ_EINVAL, "unknown sj_opts.flags bits 0x%x", o->flags);
+    if ((o->flags & SJ_SWEEP_ADAPTIVE) && (o->flags & SJ_DEDUP_GBDA))
+        return fail(ctx, SJ_EINVAL, "SJ_SWEEP_ADAPTIVE and SJ_DEDUP_GBDA cannot be combined");
     if (o->mode < SJ_TWO_PASS || o->mode > SJ_AUTO) return fail(ctx, SJ_EINVAL, "unknown mode %d", o->mode);
     if (!(o->margin >= 0.0f) || !(o->margin < 1e6f)) return fail(ctx, SJ_EINVAL, "margin out of range");
     return SJ_OK;
@@ -954,7 +961,7 @@ extern "C" int sj_count(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_re
     if (plan_blocked(ctx, gd, nR, nS, bp)) {
         bool direct = false;
         if ((st = blocked_partition_count(ctx, ctx->ws, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd,
-                                          &stats, &direct, false)))
+                                          &stats, &direct, 0)))
             return st;
         if (!direct) {
             *out_npairs = (int64_t)stats.npairs;
@@ -985,7 +992,7 @@ extern "C" int sj_tile_axes(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const s
     Stats stats;
     bool direct = false;
     if ((st = blocked_partition_count(ctx, ctx->ws, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &stats,
-                                      &direct, true, (unsigned char *)d_axis)))
+                                      &direct, SJ_SWEEP_ADAPTIVE, (unsigned char *)d_axis)))
         return st;
     if (direct) return fail(ctx, SJ_EINVAL, "a tile exceeds shared memory: the single-level path sweeps along x");
     return SJ_OK;

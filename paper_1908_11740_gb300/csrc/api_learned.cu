@@ -351,6 +351,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         a.feat_raw = (unsigned *)w.bFeatRaw.p;
         if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
         a.adaptive = o && (o->flags & SJ_SWEEP_ADAPTIVE);
+        a.gbda = o && (o->flags & SJ_DEDUP_GBDA);
         cudaError_t e;
         {
             PhaseScope ph(ctx, PH_RESET, 0);
@@ -461,6 +462,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         ctx->last.capacity = (int64_t)C;
         ctx->last.refit_items = stats.nfail;
         ctx->last.y_sweep_tiles = a.adaptive ? (int64_t)stats.naxis_y : 0;
+        ctx->last.dedup = a.gbda ? 1 : 0;
         if (os.kind == OutSpec::INTO && P > C)
             return fail(ctx, SJ_EOVERFLOW, "need %llu pairs, cap %llu", P, C);
         if (stats.nfail) {

@@ -607,9 +607,26 @@ struct RowLists {
 struct BlockCtx {
     int cxb, cyb, gw, gh, ntl;
     const unsigned *axis;  // adaptive sweep axis: bit lt set = tile lt swept along y (else nullptr)
+    int gbda;              // grouping-based duplicate avoidance instead of the test of Eq. 1
     unsigned r0, nr1, s0, ns1;
     const BEnt *er, *es;   // the block's R and S entries (shared-memory copy or global)
 };
+
+// Grouping-based duplicate avoidance (GBDA, the alternative to Eq. 1 that
+// follows it in the paper): the entries of a tile fall into four classes by
+// the two flag bits, A (first column and first row of the rectangle), B
+// (first column only), C (first row only) and D (neither).  A pair is
+// reported by this tile exactly when one of the two is in its first column
+// and one in its first row, so only the class combinations A-any, any-A, B-C
+// and C-B (9 of 16) are joined, with no test per pair.  Segments are sorted
+// by (class rank, x_l) with the ranks D = 0, B = 1, A = 2, C = 3: the classes
+// a pivot joins are then one contiguous range of ranks, [2, 2] for D, [2, 3]
+// for B, [1, 2] for C and [0, 3] for A.  The rank is kept in bits 14-15 of
+// the entry's tile field.
+__device__ __forceinline__ unsigned gbda_rank(unsigned flags2) { return (0x2310u >> (4 * flags2)) & 3u; }
+__device__ __forceinline__ unsigned gbda_lo(unsigned flags2) { return (0x0122u >> (4 * flags2)) & 3u; }
+__device__ __forceinline__ unsigned gbda_hi(unsigned flags2) { return (0x3232u >> (4 * flags2)) & 3u; }
+constexpr unsigned kTileMask = 0x3FFFu;
 
 // Write an entry of the block (side, MBR words hd, tail words t) into every
 // tile of [ta, tb) it overlaps (rows row_a..row_b of the block).  With
@@ -639,7 +656,7 @@ __device__ __forceinline__ void place_entry(BJSmem &sm, const BlockCtx &bc, int 
             sm.key[pos] = xkey(mb.x);
             sm.mbr[pos] = mb;
             sm.id[pos] = t.x | flags;
-            sm.tile[pos] = (unsigned short)j;
+            sm.tile[pos] = (unsigned short)(bc.gbda ? (unsigned)j | (gbda_rank(flags >> 30) << 14) : (unsigned)j);
         }
 }
 
@@ -770,14 +787,23 @@ __device__ __forceinline__ void band_fill(BJSmem &sm, const BlockCtx &bc, int ta
         dst[q] = -1;
         if (pidx < nb) {
             const int side = pidx >= nRb;
-            const int j = sm.tile[pidx];
+            const unsigned tw = sm.tile[pidx];
+            const int j = (int)(tw & kTileMask);
             const int s0 = j ? (int)sm.off[side][j - 1] : (side ? nRb : 0);
             const int s1 = (int)sm.off[side][j];
             const unsigned k0 = sm.key[pidx];
             int r = 0;
-            for (int qq = s0; qq < s1; qq++) {
-                const unsigned kq = sm.key[qq];
-                r += (kq < k0) | ((kq == k0) & (qq < pidx));
+            if (bc.gbda) {   // order by (class rank, x_l)
+                const unsigned c0 = tw >> 14;
+                for (int qq = s0; qq < s1; qq++) {
+                    const unsigned kq = sm.key[qq], cq = (unsigned)sm.tile[qq] >> 14;
+                    r += (cq < c0) | ((cq == c0) & ((kq < k0) | ((kq == k0) & (qq < pidx))));
+                }
+            } else {
+                for (int qq = s0; qq < s1; qq++) {
+                    const unsigned kq = sm.key[qq];
+                    r += (kq < k0) | ((kq == k0) & (qq < pidx));
+                }
             }
             dst[q] = s0 + r;
         }
@@ -808,7 +834,7 @@ __device__ __forceinline__ void stage_band(BJSmem &sm, const BlockCtx &bc, int t
 __device__ __forceinline__ void band_pivot(const BJSmem &sm, int nRb, int p, float4 &pv, unsigned &pid, int &k,
                                            int &kend, bool &isR) {
     isR = p < nRb;
-    const int j = sm.tile[p];
+    const int j = (int)(sm.tile[p] & kTileMask);
     pv = sm.mbr[p];
     pid = sm.id[p];
     const int o = isR ? 1 : 0;
@@ -846,7 +872,7 @@ __device__ __forceinline__ unsigned band_count(const BJSmem &sm, const BlockCtx 
             if (o.y <= pv.w && pv.y <= o.w && reported_here(pid, sm.id[q])) c++;
         }
         if (tile_pairs && c) {
-            const int lt = ta + sm.tile[p];
+            const int lt = ta + (int)(sm.tile[p] & kTileMask);
             const int gt = (bc.cyb + lt / bc.gw) * nx + bc.cxb + lt % bc.gw;
             atomicAdd(tile_pairs + gt, c);
         }
@@ -939,6 +965,82 @@ __device__ __forceinline__ void band_collect(BJSmem &sm, int nRb, int nSb, unsig
             }
         }
     }
+}
+
+// GBDA sweep of the staged band: every pivot scans, for each class of the
+// other side it is joined with (a contiguous range of ranks), the entries of
+// that class with x_l in (x_l, x_u] (R pivot) or [x_l, x_u] (S pivot), as in
+// the pivot-parallel Algorithm 1, and reports every y-intersecting one with
+// no duplicate test.  OUT: 0 = count (returns this thread's pairs, per-tile
+// counts to tile_pairs if given), 1 = collect into the block's shared buffer
+// and spill area (slot counter *ctr), 2 = write at out[base + *ctr ...].
+template <int OUT>
+__device__ __forceinline__ unsigned gbda_sweep(BJSmem &sm, const BlockCtx &bc, int ta, int nRb, int nSb,
+                                               unsigned *ctr, int2 *spill, int2 *out, unsigned long long base,
+                                               unsigned *tile_pairs, int nx) {
+    unsigned my = 0;
+    const int nb = nRb + nSb;
+    if (nRb == 0 || nSb == 0) return 0;
+    for (int p = threadIdx.x; p < nb; p += kBJThreads) {
+        const bool isR = p < nRb;
+        const unsigned tw = sm.tile[p];
+        const int j = (int)(tw & kTileMask);
+        const float4 pv = sm.mbr[p];
+        const unsigned pid = sm.id[p];
+        const unsigned f = pid >> 30;
+        const int o = isR ? 1 : 0;
+        const int s0 = j ? (int)sm.off[o][j - 1] : (o ? nRb : 0);
+        const int s1 = (int)sm.off[o][j];
+        unsigned c = 0;
+        for (unsigned cl = gbda_lo(f); cl <= gbda_hi(f); cl++) {
+            // first sorted position of class > cl, or of class cl with x_l
+            // past the pivot's start
+            int lo = s0, hi = s1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const unsigned q = sm.key[mid];
+                const unsigned cq = (unsigned)sm.tile[q] >> 14;
+                const float xm = sm.mbr[q].x;
+                const bool right = cq > cl || (cq == cl && (isR ? (xm > pv.x) : (xm >= pv.x)));
+                if (right) hi = mid;
+                else lo = mid + 1;
+            }
+            for (int k = lo; k < s1; k++) {
+                const unsigned q = sm.key[k];
+                if (((unsigned)sm.tile[q] >> 14) != cl) break;
+                const float4 ov = sm.mbr[q];
+                if (ov.x > pv.z) break;
+                if (ov.y <= pv.w && pv.y <= ov.w) {
+                    if (OUT == 0) {
+                        c++;
+                    } else {
+                        const unsigned oid = sm.id[q];
+                        const int2 pr = isR ? make_int2((int)(pid & kIdMask), (int)(oid & kIdMask))
+                                            : make_int2((int)(oid & kIdMask), (int)(pid & kIdMask));
+                        const unsigned m = __activemask();
+                        const int leader = __ffs(m) - 1;
+                        unsigned pos = 0;
+                        if ((int)(threadIdx.x & 31) == leader) pos = atomicAdd(ctr, (unsigned)__popc(m));
+                        pos = __shfl_sync(m, pos, leader) + __popc(m & lanemask_lt_b());
+                        if (OUT == 1) {
+                            if (pos < (unsigned)kPairBuf) sm.pbuf[pos] = pr;
+                            else if (spill && pos < (unsigned)(kPairBuf + kPairSpill)) spill[pos - kPairBuf] = pr;
+                        } else {
+                            out[base + pos] = pr;
+                        }
+                    }
+                }
+            }
+        }
+        if (OUT == 0) {
+            if (tile_pairs && c) {
+                const int lt = ta + j;
+                atomicAdd(tile_pairs + (bc.cyb + lt / bc.gw) * nx + bc.cxb + lt % bc.gw, c);
+            }
+            my += c;
+        }
+    }
+    return my;
 }
 
 // Row lists of a block that needs several bands (see RowLists).  The slice
@@ -1110,8 +1212,10 @@ __device__ void band_split(BJSmem &sm, int ntl, unsigned *s_nbands, int *s_huge)
     __syncthreads();
 }
 
-template <int MODE, int ADAPT>
+template <int MODE, int VARIANT>   // VARIANT: 0 plain, 1 adaptive sweep axis, 2 GBDA
 __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
+    constexpr int ADAPT = VARIANT == 1;
+    constexpr int GBDA = VARIANT == 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BJSmem &sm = *reinterpret_cast<BJSmem *>(smem_raw);
     __shared__ unsigned s_meta[2][12];  // current / next item: item, block, r0, nr, s0, ns, join geometry
@@ -1233,6 +1337,7 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
         }
         __syncthreads();
         bc.axis = nullptr;
+        bc.gbda = GBDA;
         if (ADAPT) {
             // Eq. 2: I = sum_i H_R[i] H_S[i] per axis; sweep along y when
             // I_y < I_x (ties and tiles missing a side keep x)
@@ -1307,12 +1412,17 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
             auto stage = [&](int bi, int &nRb, int &nSb) {
                 stage_band(sm, bc, sm.band[bi], sm.band[bi + 1], nbands == 1, nR0, nS0, rl, nRb, nSb);
             };
+            // pairs of the staged band at out[base + s_cursor ...]
+            auto write = [&](int nRb, int nSb, unsigned long long base) {
+                if (GBDA) gbda_sweep<2>(sm, bc, 0, nRb, nSb, &s_cursor, nullptr, o.out, base, nullptr, 0);
+                else band_write(sm, nRb, nSb, o.out, base, &s_cursor);
+            };
             if (MODE == MODE_WRITE) {
                 const unsigned long long base = o.off_in[it];
                 for (int bi = 0; bi < nbands; bi++) {
                     int nRb, nSb;
                     stage(bi, nRb, nSb);
-                    band_write(sm, nRb, nSb, o.out, base, &s_cursor);
+                    write(nRb, nSb, base);
                     __syncthreads();
                 }
             } else {
@@ -1321,13 +1431,16 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                 for (int bi = 0; bi < nbands; bi++) {
                     stage(bi, nRb, nSb);
                     if (MODE == MODE_RESERVE) {
-                        band_collect(sm, nRb, nSb, &s_pc,
-                                     o.spill ? o.spill + (size_t)blockIdx.x * kPairSpill : nullptr);
+                        int2 *sp = o.spill ? o.spill + (size_t)blockIdx.x * kPairSpill : nullptr;
+                        if (GBDA) gbda_sweep<1>(sm, bc, 0, nRb, nSb, &s_pc, sp, nullptr, 0, nullptr, 0);
+                        else band_collect(sm, nRb, nSb, &s_pc, sp);
                         __syncthreads();
                     } else {
-                        tot += block_sum(band_count(sm, bc, sm.band[bi], nRb, nSb,
-                                                    MODE == MODE_TILES ? o.tile_pairs : nullptr, a.g.nx),
-                                         s_red);
+                        unsigned *tp = MODE == MODE_TILES ? o.tile_pairs : nullptr;
+                        const unsigned c = GBDA ? gbda_sweep<0>(sm, bc, sm.band[bi], nRb, nSb, nullptr, nullptr,
+                                                                nullptr, 0, tp, a.g.nx)
+                                                : band_count(sm, bc, sm.band[bi], nRb, nSb, tp, a.g.nx);
+                        tot += block_sum(c, s_red);
                     }
                 }
                 if (MODE == MODE_RESERVE) tot = s_pc;
@@ -1355,11 +1468,11 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                             for (unsigned i = threadIdx.x; i < tot; i += kBJThreads)
                                 o.out[s_base + i] = i < (unsigned)kPairBuf ? sm.pbuf[i] : sp[i - kPairBuf];
                         } else if (nbands == 1) {
-                            band_write(sm, nRb, nSb, o.out, s_base, &s_cursor);
+                            write(nRb, nSb, s_base);
                         } else {
                             for (int bi = 0; bi < nbands; bi++) {
                                 stage(bi, nRb, nSb);
-                                band_write(sm, nRb, nSb, o.out, s_base, &s_cursor);
+                                write(nRb, nSb, s_base);
                                 __syncthreads();
                             }
                         }
@@ -1459,6 +1572,9 @@ cudaError_t blocked_setup() {
     if ((e = cudaFuncSetAttribute(k_bjoin<MODE_COUNT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
     if ((e = cudaFuncSetAttribute(k_bjoin<MODE_WRITE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
     if ((e = cudaFuncSetAttribute(k_bjoin<MODE_RESERVE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_COUNT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_WRITE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bjoin<MODE_RESERVE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
     const int l1 = 8 * kMaxBlocks;
     if ((e = cudaFuncSetAttribute(k_bcount<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
     if ((e = cudaFuncSetAttribute(k_bcount<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
@@ -1524,6 +1640,15 @@ cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s) {
 
 cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, cudaStream_t s) {
     const size_t sm = sizeof(BJSmem);
+    if (a.gbda && a.nj == 1) {
+        switch (mode) {
+            case MODE_COUNT: k_bjoin<MODE_COUNT, 2><<<grid, kBJThreads, sm, s>>>(a, o); break;
+            case MODE_WRITE: k_bjoin<MODE_WRITE, 2><<<grid, kBJThreads, sm, s>>>(a, o); break;
+            case MODE_RESERVE: k_bjoin<MODE_RESERVE, 2><<<grid, kBJThreads, sm, s>>>(a, o); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     if (a.adaptive && a.nj == 1) {
         switch (mode) {
             case MODE_COUNT: k_bjoin<MODE_COUNT, 1><<<grid, kBJThreads, sm, s>>>(a, o); break;

@@ -77,6 +77,7 @@ struct BArgs {
     int pts;                    // 1: R, S hold float2 points, read as squares of half-width h
     float h;
     int adaptive;               // single join: sweep axis per tile from Eq. 2 histograms (Sec. 3.3)
+    int gbda;                   // single join: grouping-based duplicate avoidance instead of Eq. 1
     Stats *st;
 };
 

@@ -134,7 +134,7 @@ BJoinOut bjoin_out(Workspace &w, int slot);
 int enqueue_blocked_partition(sj_ctx *ctx, Workspace &w, const BPlan &p, const BArgs &a);
 int blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const float4 *R, long long nR,
                             const float4 *S, long long nS, const GridDev &g, Stats *stats, bool *use_direct,
-                            bool adaptive, unsigned char *tile_axis = nullptr);
+                            int flags, unsigned char *tile_axis = nullptr);
 int check_opts(sj_ctx *ctx, const sj_opts *o);
 // The join of sj_join / sj_join_into / sj_join_host on checked inputs.
 int join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,

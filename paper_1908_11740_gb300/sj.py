@@ -23,6 +23,7 @@ from . import build as _build
 SJ_OK, SJ_EINVAL, SJ_ENOMEM, SJ_EOVERFLOW, SJ_ETIMEOUT, SJ_ECUDA, SJ_EINTERNAL = range(7)
 SJ_TWO_PASS, SJ_ONE_PASS, SJ_ONE_PASS_HEUR, SJ_AUTO = range(4)
 SJ_SWEEP_ADAPTIVE = 1
+SJ_DEDUP_GBDA = 2
 MODES = {"two_pass": SJ_TWO_PASS, "one_pass": SJ_ONE_PASS, "one_pass_heur": SJ_ONE_PASS_HEUR,
          "auto": SJ_AUTO}
 
@@ -58,7 +59,7 @@ class sj_stats(ctypes.Structure):
                 ("work_items", ctypes.c_int64), ("l1_entries_r", ctypes.c_int64),
                 ("l1_entries_s", ctypes.c_int64), ("entries_r", ctypes.c_int64),
                 ("entries_s", ctypes.c_int64), ("npairs", ctypes.c_int64), ("one_pass", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("capacity", ctypes.c_int64), ("refit_items", ctypes.c_int64),
+                ("dedup", ctypes.c_int32), ("capacity", ctypes.c_int64), ("refit_items", ctypes.c_int64),
                 ("y_sweep_tiles", ctypes.c_int64)]
 
 
@@ -148,13 +149,18 @@ def make_grid(nx: int, ny: int | None = None, x0=0.0, y0=0.0, x1=1.0, y1=1.0) ->
     return sj_grid(int(nx), int(nx if ny is None else ny), x0, y0, x1, y1)
 
 
-def make_opts(mode="two_pass", sort_output=False, margin=0.25, axis="x") -> sj_opts:
+def make_opts(mode="two_pass", sort_output=False, margin=0.25, axis="x", dedup="refpoint") -> sj_opts:
     """axis: "x" (Algorithm 1 along x in every tile) or "adaptive" (per tile,
-    the axis with the smaller Eq. 2 estimate, SJ_SWEEP_ADAPTIVE)."""
+    the axis with the smaller Eq. 2 estimate, SJ_SWEEP_ADAPTIVE); dedup:
+    "refpoint" (the test of Eq. 1) or "gbda" (class mini-joins,
+    SJ_DEDUP_GBDA)."""
     m = MODES[mode] if isinstance(mode, str) else int(mode)
     if axis not in ("x", "adaptive"):
         raise ValueError("axis must be 'x' or 'adaptive'")
-    return sj_opts(m, int(bool(sort_output)), float(margin), SJ_SWEEP_ADAPTIVE if axis == "adaptive" else 0)
+    if dedup not in ("refpoint", "gbda"):
+        raise ValueError("dedup must be 'refpoint' or 'gbda'")
+    flags = (SJ_SWEEP_ADAPTIVE if axis == "adaptive" else 0) | (SJ_DEDUP_GBDA if dedup == "gbda" else 0)
+    return sj_opts(m, int(bool(sort_output)), float(margin), flags)
 
 
 class _TorchAllocator:
