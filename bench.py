@@ -723,14 +723,14 @@ def bands_arm(args):
 
 def _variant_table(args, env, ctx, dR, dS, grids, variants):
     """ms per join of every (grid, mode, variant) with inputs resident, CUDA
-    events on the stream; returns ({name: result}, launches of the first)."""
+    events on the stream; returns ({name: result}, steps)."""
     import torch
 
     from paper_1908_11740_gb300 import sj
 
     stream = torch.cuda.current_stream()
     steps = max(3, min(args.steps, 20))
-    results, first_launches = {}, None
+    results = {}
     for K in grids:
         g = sj.make_grid(K)
         for mode in ("two_pass", "one_pass"):
@@ -754,14 +754,13 @@ def _variant_table(args, env, ctx, dR, dS, grids, variants):
                 sj.sj_timing_enable(ctx, False)
                 st = sj.sj_last_stats(ctx)
                 ph = {k: round(v[1] / steps, 4) for k, v in tm.items() if k != "launches" and v[0]}
-                if first_launches is None:
-                    first_launches = tm["launches"] // steps
                 results[f"K{K} {mode} {vname}"] = {
+                    "launches": tm["launches"],
                     "ms_per_step": round(ev0.elapsed_time(ev1) / steps, 4), "pairs": P,
                     "block_join_ms": ph.get("sweep_write"), "count_pass_ms": ph.get("sweep_count"),
                     "y_sweep_tiles": st["y_sweep_tiles"], "gbda": st["dedup"],
                     "path": "two-level" if st["path"] == 1 else "single-level"}
-    return results, first_launches, steps
+    return results, steps
 
 
 def aniso_arm(args):
@@ -787,8 +786,8 @@ def aniso_arm(args):
     clocks.start()
     time.sleep(0.3)
     grids = [int(k) for k in args.aniso_grids.split(",")]
-    results, launches, steps = _variant_table(args, env, ctx, dR, dS, grids,
-                                              [("x", {"axis": "x"}), ("adaptive", {"axis": "adaptive"})])
+    results, steps = _variant_table(args, env, ctx, dR, dS, grids,
+                                    [("x", {"axis": "x"}), ("adaptive", {"axis": "adaptive"})])
     clk = clocks.stop()
     head = results[f"K{grids[0]} one_pass adaptive"]
     ms, P_all = sjdist.reduce_result(head["ms_per_step"], head["pairs"], env)
@@ -800,7 +799,7 @@ def aniso_arm(args):
                 "config": {"workload": f"elongated rectangles |R|={args.n_r:,} |S|={args.n_s:,}, aspect 10, "
                                        f"GIS-shaped mixture centres, grid {grids[0]}x{grids[0]}, learned one-pass, "
                                        f"adaptive axis", "pairs": head["pairs"]},
-                "compare": results, "gpu_launches": launches, "clocks": clk}
+                "compare": results, "gpu_launches": head["launches"], "clocks": clk}
         print(json.dumps(line), flush=True)
     sj.sj_set_model(ctx, None)
     model.free()
@@ -829,8 +828,8 @@ def gbda_arm(args):
     clocks.start()
     time.sleep(0.3)
     grids = [args.grid, 1000]
-    results, launches, steps = _variant_table(args, env, ctx, dR, dS, grids,
-                                              [("refpoint", {"dedup": "refpoint"}), ("gbda", {"dedup": "gbda"})])
+    results, steps = _variant_table(args, env, ctx, dR, dS, grids,
+                                    [("refpoint", {"dedup": "refpoint"}), ("gbda", {"dedup": "gbda"})])
     clk = clocks.stop()
     head = results[f"K{grids[0]} one_pass gbda"]
     ms, P_all = sjdist.reduce_result(head["ms_per_step"], head["pairs"], env)
@@ -840,7 +839,7 @@ def gbda_arm(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": workload_name(args) + ", learned one-pass, GBDA", "pairs": head["pairs"]},
-                "compare": results, "gpu_launches": launches, "clocks": clk}
+                "compare": results, "gpu_launches": head["launches"], "clocks": clk}
         print(json.dumps(line), flush=True)
     sj.sj_set_model(ctx, None)
     model.free()

@@ -272,6 +272,11 @@ int sj_extent_stats(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *
 /* Entries per block of the two-level partition (default 1536, >= 64): the
  * knob the autotuner sets next to the grid. */
 int sj_set_tuning(sj_ctx *ctx, int block_target);
+/* Order in which the one-pass join's persistent block-join CTAs take the
+ * blocks: heaviest predicted cost first (entries + predicted pairs, 32 log2
+ * classes; the default, 1) or block order (0).  The pairs are the same; only
+ * the balance of the CTAs changes. */
+int sj_set_schedule(sj_ctx *ctx, int heaviest_first);
 
 /* ---- batches of independent joins ---------------------------------------- */
 /* nj independent joins (R_j join S_j on grid g[j]) in one pass of the

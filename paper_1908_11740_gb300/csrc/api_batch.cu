@@ -391,6 +391,12 @@ extern "C" int sj_extent_stats(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, cons
     return SJ_OK;
 }
 
+extern "C" int sj_set_schedule(sj_ctx *ctx, int heaviest_first) {
+    if (!ctx) return SJ_EINVAL;
+    ctx->lpt = heaviest_first ? 1 : 0;
+    return SJ_OK;
+}
+
 extern "C" int sj_set_tuning(sj_ctx *ctx, int block_target) {
     if (!ctx || block_target < 64) return SJ_EINVAL;
     ctx->block_target = block_target;

@@ -281,8 +281,34 @@ extern "C" int sj_block_features(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, co
             continue;
         }
         if (stats.err) return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", stats.err);
-        if (stats.need_direct) return fail(ctx, SJ_EINVAL, "a tile exceeds the shared-memory capacity");
         const int64_t n = stats.nchunks;
+        if (stats.need_direct) {
+            // a tile exceeds shared memory: the blocks' features stand, and
+            // their labels come from the per-tile pair counts of the
+            // single-level path, added up per block
+            const long long T = (long long)gd.nx * gd.ny;
+            if ((st = ensure(ctx, w.tpairs, 4ull * T + 16)) || (st = ensure(ctx, w.item_of, 4ull * p.nb + 16)) ||
+                (st = ensure(ctx, w.cnt64, 8ull * (n + 1))))
+                return st;
+            Stats s2;
+            if ((st = partition_and_count(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &s2, false)))
+                return st;
+            if ((e = cudaMemsetAsync(w.tpairs.p, 0, 4ull * T, ctx->stream)) ||
+                (e = cudaMemsetAsync(w.item_of.p, 0xff, 4ull * p.nb, ctx->stream)) ||
+                (e = cudaMemsetAsync(w.cnt64.p, 0, 8ull * (n + 1), ctx->stream)))
+                return cuda_fail(ctx, e, "memset");
+            if ((st = enqueue_sweep(ctx, w, MODE_TILES, nullptr, 0, nullptr, (unsigned *)w.tpairs.p, 4))) return st;
+            {
+                PhaseScope ph(ctx, PH_MODEL, 3);
+                if ((e = launch_labels_from_tiles((const unsigned *)w.bItems.p, (unsigned)n, (unsigned *)w.item_of.p,
+                                                  (const unsigned *)w.tpairs.p, gd.nx, T, p.G, p.bx,
+                                                  (unsigned long long *)w.cnt64.p, (float *)w.bPred.p,
+                                                  ctx->num_sms * 4, ctx->stream)))
+                    return cuda_fail(ctx, e, "labels");
+            }
+            if ((st = read_stats(ctx, w, &s2))) return st;
+            if (s2.err) return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", s2.err);
+        }
         *n_items = n;
         ctx->last = sj_stats{};
         ctx->last.path = 1;
@@ -409,7 +435,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
             if ((st = out_acquire(ctx, w, os, C))) return st;
         }
         BJoinOut bo = bjoin_out(w, 2);
-        bo.list = (const unsigned *)w.bOrder.p;
+        bo.list = ctx->lpt ? (const unsigned *)w.bOrder.p : nullptr;   // heaviest first, or item order
         bo.list_n = &a.st->nchunks;
         bo.out = os.got;
         bo.cap = C;

@@ -431,7 +431,42 @@ __global__ void k_labels(const unsigned *__restrict__ cnt, const Stats *__restri
         label[it] = log1pf((float)cnt[it]);
 }
 
+// Labels of the work items from per-tile pair counts (for blocks whose tiles
+// exceed shared memory, counted by the single-level path): item_of[b] =
+// work item of block b (all ones: none), then every tile's pairs are added to
+// its block's item, then log1p.  cnt64 must start at zero.
+__global__ void k_item_of_block(const unsigned *__restrict__ items, unsigned n, unsigned *__restrict__ item_of) {
+    for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x)
+        item_of[items[it]] = it;
+}
+
+__global__ void k_tile_pairs_to_items(const unsigned *__restrict__ tile_pairs, int nx, long long T, int G, int bx,
+                                      const unsigned *__restrict__ item_of,
+                                      unsigned long long *__restrict__ cnt64) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < T; t += (long long)gridDim.x * blockDim.x) {
+        const unsigned p = tile_pairs[t];
+        if (!p) continue;
+        const int row = (int)(t / nx), col = (int)(t % nx);
+        const unsigned it = item_of[(row / G) * bx + col / G];
+        if (it != 0xffffffffu) atomicAdd(cnt64 + it, (unsigned long long)p);
+    }
+}
+
+__global__ void k_labels64(const unsigned long long *__restrict__ cnt64, unsigned n, float *__restrict__ label) {
+    for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < n; it += gridDim.x * blockDim.x)
+        label[it] = log1pf((float)cnt64[it]);
+}
+
 // ---- launchers -------------------------------------------------------------
+cudaError_t launch_labels_from_tiles(const unsigned *items, unsigned n, unsigned *item_of, const unsigned *tile_pairs,
+                                     int nx, long long T, int G, int bx, unsigned long long *cnt64, float *label,
+                                     int grid, cudaStream_t s) {
+    k_item_of_block<<<grid, 256, 0, s>>>(items, n, item_of);
+    k_tile_pairs_to_items<<<grid, 256, 0, s>>>(tile_pairs, nx, T, G, bx, item_of, cnt64);
+    k_labels64<<<grid, 256, 0, s>>>(cnt64, n, label);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_labels(const unsigned *cnt, const Stats *st, float *label, int grid, cudaStream_t s) {
     k_labels<<<grid, 256, 0, s>>>(cnt, st, label);
     return cudaGetLastError();

@@ -37,6 +37,7 @@ struct Workspace {
     Buf lstart, lcoff, lvb;                        // candidate-parallel sweep of the large tiles
     Buf dsq_r, dsq_s, dmask, dcnt, doff, dstats;   // eps-distance join: squares, refinement
     Buf band_r, band_s, band_ir, band_is;          // row band of a join: its rectangles and their indices
+    Buf tpairs, item_of, cnt64;                    // block labels from per-tile pair counts
     unsigned long long bcap_r = 0, bcap_s = 0;
     unsigned long long cap_r = 0, cap_s = 0;   // entry capacities per side
     long long T = 0;
@@ -171,6 +172,7 @@ struct sj_ctx {
     int use_blocked = 1;      // the two-level path when the grid allows it
     int shared_cursors = 1;   // L1 write through shared per-block cursors
     int block_target = 1536;  // L1 entries a block should hold (two-level plan)
+    int lpt = 1;              // one-pass join: blocks heaviest predicted cost first (else item order)
     float onepass_scale = 1.0f;   // one-pass capacity calibration (api_learned.cu), in [1, 8]
     sj_alloc_fn alloc = nullptr;
     sj_free_fn free_fn = nullptr;

@@ -67,6 +67,9 @@ cudaError_t launch_mlp_publish(const MlpParams &p, const MlpWeights &w, cudaStre
 cudaError_t launch_heur_pred(const float *feat, const unsigned *items, const unsigned *btot, int nb,
                              const Stats *st, float *pred, int grid, cudaStream_t s);
 cudaError_t launch_labels(const unsigned *cnt, const Stats *st, float *label, int grid, cudaStream_t s);
+cudaError_t launch_labels_from_tiles(const unsigned *items, unsigned n, unsigned *item_of, const unsigned *tile_pairs,
+                                     int nx, long long T, int G, int bx, unsigned long long *cnt64, float *label,
+                                     int grid, cudaStream_t s);
 constexpr int kPlanScratch = 512;   // capacity total + class histogram + class cursors
 cudaError_t launch_plan(const float *pred, const uint4 *imeta, const unsigned *ins, const Stats *st, float margin,
                         unsigned slack, unsigned long long *cap_total, unsigned *order, int grid, cudaStream_t s);

@@ -9,13 +9,17 @@ forward, backward of the mean squared error, Adam).
     python -m paper_1908_11740_gb300.learn --out paper_1908_11740_gb300/models/block_pairs_mlp.npz
 
 Training joins: the GIS-shaped layers (seeds 20-27, full size, grids 2000,
-3000 and 4000) and batched joins of uneven size (seeds 4100+, grid from the
-tile-extent rule).  The features carry no block size, so the training joins
-use the grid family the model is applied to.  After training, the output
-bias is shifted so that the summed predicted pairs of the training blocks
-equal their summed exact pairs (regressing log counts under-estimates sums).  The extent/skew stress workload is not used:
-its hottest tiles exceed shared memory, so the exact single-level join runs
-there and no block features exist.  Evaluation: a fresh seed (29) of the
+3000 and 4000), batched joins of uneven size (seeds 4100+, grid from the
+tile-extent rule) and the extent / skew stress workload (20M x 20M, seeds
+20-22, rho 0, 5.2e-5 and 2.1e-4, grid 2000).  The features carry no block
+size, so the training joins use the grid family the model is applied to.
+The skew joins' hottest tiles exceed shared memory, so they run on the
+single-level path; their blocks' labels come from its per-tile pair counts
+(sj_block_features does this by itself).  After training, the output bias
+is shifted so that the summed predicted pairs of the GIS-shaped and batched
+training blocks equal their summed exact pairs (regressing log counts
+under-estimates sums); the skew blocks, whose sums run to 1e9 pairs, are
+left out of that calibration.  Evaluation: a fresh seed (29) of the
 GIS-shaped layers at full size.
 """
 from __future__ import annotations
@@ -54,15 +58,24 @@ def grid_rule(R, S) -> int:
     return int(min(8000, max(16, round(1.0 / (10.0 * max(m, 1e-7))))))
 
 
-def training_joins(scale: float = 1.0, n_batch: int = 16, grids=(2000, 3000, 4000)):
+SKEW_RHOS = (0.0, 5.2e-5, 2.1e-4)
+
+
+def training_joins(scale: float = 1.0, n_batch: int = 16, grids=(2000, 3000, 4000), skew: bool = True):
+    """(name, R, S, grid, calibrate) of every training join."""
     for seed in range(20, 28):
         R, S = inputs.gis_pair(int(10_000_000 * scale), int(20_000_000 * scale), seed=seed)
         for K in grids:
-            yield f"gis seed {seed} K {K}", R, S, K
+            yield f"gis seed {seed} K {K}", R, S, K, True
     for j, (R, S) in enumerate(inputs.batch_pairs(n_joins=n_batch, seed0=4100)):
         if len(R) < 2000 or len(S) < 2000:
             continue
-        yield f"batch join {j}", R, S, grid_rule(R, S)
+        yield f"batch join {j}", R, S, grid_rule(R, S), True
+    if skew:
+        for seed, rho in zip(range(20, 23), SKEW_RHOS):
+            n = int(20_000_000 * scale)
+            R, S = inputs.zipf_pair(n, n, seed=seed, rho=rho)
+            yield f"skew seed {seed} rho {rho}", R, S, 2000, False
 
 
 def collect(ctx, joins, verbose=True):
@@ -70,8 +83,8 @@ def collect(ctx, joins, verbose=True):
 
     from . import sj
 
-    Xs, Ys = [], []
-    for name, R, S, K in joins:
+    Xs, Ys, Cs = [], [], []
+    for name, R, S, K, cal in joins:
         dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
         try:
             X, Y = sj.sj_block_features(ctx, dR, dS, sj.make_grid(K))
@@ -81,9 +94,10 @@ def collect(ctx, joins, verbose=True):
             continue
         Xs.append(X.clone())
         Ys.append(Y.clone())
+        Cs.append(torch.full((X.shape[0],), bool(cal), dtype=torch.bool, device=X.device))
         if verbose:
             print(f"{name}: {X.shape[0]} blocks")
-    return torch.cat(Xs), torch.cat(Ys)
+    return torch.cat(Xs), torch.cat(Ys), torch.cat(Cs)
 
 
 def train(ctx, X, Y, epochs=60, batch=4096, lr=2e-3, seed=0, verbose=True):
@@ -171,6 +185,7 @@ def main(argv=None):
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--eval-seed", type=int, default=29)
+    ap.add_argument("--no-skew", action="store_true", help="leave the skew stress joins out of training")
     a = ap.parse_args(argv)
 
     import torch
@@ -180,10 +195,10 @@ def main(argv=None):
     build.build()
     ctx = sj.sj_create(0)
     t0 = time.time()
-    X, Y = collect(ctx, training_joins(a.scale))
+    X, Y, C = collect(ctx, training_joins(a.scale, skew=not a.no_skew))
     t1 = time.time()
     model, hist = train(ctx, X, Y, epochs=a.epochs)
-    delta = calibrate(model, X, Y)
+    delta = calibrate(model, X[C].contiguous(), Y[C].contiguous())
     torch.cuda.synchronize()
     t2 = time.time()
     R, S = inputs.gis_pair(seed=a.eval_seed)
@@ -193,7 +208,10 @@ def main(argv=None):
     rep = sizing_report(ctx, model, R, S, 3000)
     header = {"features": FEATURE_VERSION, "arch": "32-64-64-1 relu, bf16 weights, fp32 accumulate",
               "train_samples": int(X.shape[0]), "train_mse": hist[-1], "epochs": a.epochs,
-              "train_joins": "gis seeds 20-27 at scale %g, grids 2000/3000/4000; batch joins seeds 4100-4115" % a.scale,
+              "train_joins": ("gis seeds 20-27 at scale %g, grids 2000/3000/4000; batch joins seeds 4100-4115" % a.scale)
+              + ("" if a.no_skew else "; skew 20M x 20M seeds 20-22, rho %s, grid 2000" % (SKEW_RHOS,)),
+              "train_skew_samples": int((~C).sum().item()),
+              "calibrated_on": "gis and batch blocks",
               "bias_calibration": delta,
               "eval": {"workload": "gis 10M x 20M seed %d grid 3000" % a.eval_seed, "block_mae_log1p": mae,
                        "sizing": rep},

@@ -108,6 +108,7 @@ SIGNATURES = [
     ("sj_mlp_forward", I32, [P, P, P, I64, P]),
     ("sj_mlp_grad", I32, [P, P, P, P, I64, P, P]),
     ("sj_mlp_train_step", I32, [P, P, P, P, I64, ctypes.c_float, P]),
+    ("sj_set_schedule", I32, [P, I32]),
     ("sj_tile_axes", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), P]),
     ("sj_block_features", I32, [P, P, I64, P, I64, ctypes.POINTER(sj_grid), P, P, P, I64, ctypes.POINTER(I64)]),
     ("sj_set_model", I32, [P, P]),
@@ -659,6 +660,12 @@ def sj_extent_stats(ctx: Context, R, S):
     out = np.zeros(4, np.float64)
     _check(ctx.handle, load().sj_extent_stats(ctx.handle, pr, nr, ps, ns, out.ctypes.data))
     return out
+
+
+def sj_set_schedule(ctx: Context, heaviest_first: bool) -> None:
+    """One-pass join: blocks heaviest predicted cost first (default) or in
+    block order."""
+    _check(ctx.handle, load().sj_set_schedule(ctx.handle, int(bool(heaviest_first))))
 
 
 def sj_set_tuning(ctx: Context, block_target: int) -> None:

@@ -64,6 +64,29 @@ def test_block_features_and_labels(sj, ctx):
         assert int(round(np.expm1(float(Yc[row])))) == want_l[int(b)]
 
 
+def test_block_labels_when_tiles_exceed_shared_memory(sj, ctx):
+    """Skew-shaped input whose hottest tiles hold more entries than shared
+    memory: the features still come from the two-level partition, the labels
+    from the single-level path's per-tile counts; both equal the oracle's."""
+    R, S = inputs.zipf_pair(200_000, 200_000, seed=35, lattice=256, r_max_extent=2e-3, s_max_extent=4e-3, rho=0.0)
+    K = 400
+    assert oracle.tile_counts(R, K).max() > 3072
+    X, Y, B = sj.sj_block_features(ctx, dev(R), dev(S), sj.make_grid(K), with_blocks=True)
+    G = sj.sj_last_stats(ctx)["block_side"]
+    want_f = L.block_features(R, S, K, K, G)
+    want_l = L.block_labels(R, S, K, K, G)
+    got_b = B.cpu().numpy()
+    assert sorted(got_b.tolist()) == sorted(want_f.keys())
+    Xc, Yc = X.cpu().numpy(), Y.cpu().numpy()
+    total = 0
+    for row, b in enumerate(got_b):
+        np.testing.assert_allclose(Xc[row], want_f[int(b)], rtol=1e-5, atol=1e-6)
+        got = int(round(float(np.expm1(np.float64(Yc[row])))))
+        assert abs(got - want_l[int(b)]) <= max(1, 1e-6 * want_l[int(b)])   # float32 log1p of large counts
+        total += want_l[int(b)]
+    assert total == len(oracle.pbsm(R, S, K))
+
+
 def test_mlp_forward_and_gradient(sj, ctx):
     g = np.random.default_rng(5)
     p = g.normal(0, 0.2, L.PARAMS).astype(np.float32)
