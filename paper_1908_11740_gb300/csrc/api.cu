@@ -231,7 +231,7 @@ extern "C" int sj_create(sj_ctx **out, int device, void *cuda_stream) {
         return SJ_ECUDA;
     }
     c->sweep_bps = sweep_blocks_per_sm();
-    if (blocked_setup() != cudaSuccess) {
+    if (blocked_setup() != cudaSuccess || stripe_setup() != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return SJ_ECUDA;
@@ -815,6 +815,11 @@ int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const
 int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
                   int64_t nS, const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs) {
     const int mode = o ? o->mode : SJ_TWO_PASS;
+    {   // 1D grids (stripes): the stripe kernel, exact two-pass, in any mode
+        const int st = join_stripes(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, o, os, npairs);
+        if (st != STRIPES_UNSUITED) return st;
+        os.got = nullptr;
+    }
     const bool one_pass = (mode == SJ_ONE_PASS || mode == SJ_ONE_PASS_HEUR ||
                            (mode == SJ_AUTO && ctx->mlp_loaded));
     if (one_pass) {

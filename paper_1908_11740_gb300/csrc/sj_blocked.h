@@ -124,5 +124,10 @@ int bscan_chunks(int nb);
 cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, cudaStream_t s);
+// 1D grids: one CTA per stripe, R and S sorted along the stripe in shared
+// memory, forward scan along the stripe (stripes.cu)
+cudaError_t stripe_setup();
+size_t stripe_smem_bytes();
+cudaError_t launch_stripe_join(int mode, const BArgs &a, int vert, const BJoinOut &o, int grid, cudaStream_t s);
 
 }  // namespace sj

@@ -104,6 +104,11 @@ constexpr int ONE_PASS_UNSUITED = -1;
 // returned by join_core for point inputs when the two-level path does not
 // suit the data (the caller then materialises the squares)
 constexpr int PTS_UNSUITED = -2;
+// returned by join_stripes when the grid is not 1D or a stripe exceeds shared
+// memory (the caller then runs the general path)
+constexpr int STRIPES_UNSUITED = -3;
+int join_stripes(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S, long long nS,
+                 const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs);
 int join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S, long long nS,
                        const GridDev &gd, const sj_opts *o, int heuristic, OutSpec &os, int64_t *npairs,
                        sj_pair **lib_out);
@@ -170,6 +175,7 @@ struct sj_ctx {
     int sweep_bps = 1;
     int bjoin_bps = 1;
     int use_blocked = 1;      // the two-level path when the grid allows it
+    int use_stripes = 1;      // the stripe kernel for 1D grids
     int shared_cursors = 1;   // L1 write through shared per-block cursors
     int block_target = 1536;  // L1 entries a block should hold (two-level plan)
     int lpt = 1;              // one-pass join: blocks heaviest predicted cost first (else item order)
