@@ -54,12 +54,13 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
                     help="CPU sample: rectangles whose centre has y < frac")
-    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance", "aniso", "bands", "gbda"],
+    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance", "aniso", "bands", "gbda", "stripes"],
                     help="gis: the 10M x 20M GIS-shaped join (default); batch: 256 joins of uneven size; "
                          "skew: the 20M x 20M Zipf extent / skew stress; aniso: 10M x 20M elongated "
                          "rectangles, sweep along x against the adaptive axis of Sec. 3.3; bands: the gis join "
                          "split into one band of tile rows per rank (the default for gis with N > 1); gbda: "
-                         "the gis join with Eq. 1 against GBDA duplicate avoidance")
+                         "the gis join with Eq. 1 against GBDA duplicate avoidance; stripes: the gis join on "
+                         "1D grids (stripe kernel) against the 2D grid")
     ap.add_argument("--aniso-grids", default="1750,600",
                     help="aniso: grids to time (1750: the tile-extent rule; 600: coarse tiles)")
     ap.add_argument("--rho", type=float, default=2.1e-4,
@@ -71,6 +72,8 @@ def parse():
                          "entries (strong scaling, each rank stages its band's rectangles); instances = an "
                          "independent join per rank (weak scaling)")
     ap.add_argument("--joins", type=int, default=256)
+    ap.add_argument("--batch-grids", default="rule", choices=["rule", "tuned"],
+                    help="batch: grids by the rule of Sec. 4.3 or by the measured tuner (tune.tuned_batch)")
     ap.add_argument("--eps", type=float, default=5e-5, help="distance of the eps-distance join")
     ap.add_argument("--dist-grid", type=int, default=2000, help="grid of the eps-distance join")
     return ap.parse_args()
@@ -424,10 +427,13 @@ def ours(args):
 
 def batch_arm(args):
     """256 independent joins (sizes log-uniform in [1e3, 2e6] per side), grids
-    by the rule of thumb per join.  With N ranks the joins are split into N
-    disjoint shards of about equal input size (no data-path collective); each
-    rank joins its shard in one batched call.  Total work is fixed as N grows
-    (strong scaling); value = all pairs / the slowest rank's time."""
+    by the rule of thumb per join (or the measured tuner, --batch-grids
+    tuned).  With N ranks the joins are split into N disjoint shards of about
+    equal input size (no data-path collective); each rank joins its shard in
+    one batched call.  Total work is fixed as N grows (strong scaling);
+    value = all pairs / the slowest rank's time.  Beside it: the phases of the
+    same batch launched without graphs (a second context), the algorithmic
+    bytes over the HBM peak, and the oracle on a bounded sample of the joins."""
     import torch
 
     from paper_1908_11740_gb300 import build, sj
@@ -441,10 +447,17 @@ def batch_arm(args):
     Ss = [torch.from_numpy(joins[j][1]).cuda() for j in mine]
     n_in = sum(len(r) + len(s) for r, s in joins)
     ctx = sj.sj_create(env.local_rank)
-    pairs, offs = sj.sj_join_batch(ctx, Rs, Ss, None)
+    grids = None
+    if args.batch_grids == "tuned":
+        from paper_1908_11740_gb300 import tune
+
+        grids = tune.tuned_batch(ctx, Rs, Ss, cache=tune.Cache(os.path.join(tempfile.gettempdir(), "sj_tune.json")))
+    pairs, offs = sj.sj_join_batch(ctx, Rs, Ss, grids)
+    st = sj.sj_last_stats(ctx)
+    E1 = st["l1_entries_r"] + st["l1_entries_s"]
     out = torch.empty((int(offs[-1]) + 1, 2), dtype=torch.int32, device="cuda")
     for _ in range(max(3, args.warmup)):
-        sj.sj_join_batch(ctx, Rs, Ss, None, out=out)
+        sj.sj_join_batch(ctx, Rs, Ss, grids, out=out)
     torch.cuda.synchronize()
     clocks = ClockSampler(env.local_rank)
     clocks.start()
@@ -456,27 +469,71 @@ def batch_arm(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        sj.sj_join_batch(ctx, Rs, Ss, None, out=out)
+        sj.sj_join_batch(ctx, Rs, Ss, grids, out=out)
     ev1.record(stream)
     torch.cuda.synchronize()
     sjdist.barrier(env)
     tm = sj.sj_timing_read(ctx)
     clk = clocks.stop()
     ms, P = sjdist.reduce_result(ev0.elapsed_time(ev1) / args.steps, int(offs[-1]), env)
+    # the same batch without graphs: direct launches, phases timed
+    os.environ["SJ_BATCH_GRAPHS"] = "0"
+    ctx_direct = sj.sj_create(env.local_rank)
+    del os.environ["SJ_BATCH_GRAPHS"]
+    for _ in range(2):
+        sj.sj_join_batch(ctx_direct, Rs, Ss, grids, out=out)
+    torch.cuda.synchronize()
+    sj.sj_timing_enable(ctx_direct, True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sj.sj_join_batch(ctx_direct, Rs, Ss, grids, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    tmd = sj.sj_timing_read(ctx_direct)
+    ms_direct = ev0.elapsed_time(ev1) / args.steps
+    sj.sj_destroy(ctx_direct)
+    cpu = None
+    if env.rank == 0 and not args.no_cpu:
+        import oracle
+
+        t, npairs, nrect, k = 0.0, 0, 0, 0
+        for R, S in joins:   # bounded sample: the first joins, about 4M rectangles
+            K = int(grids[k].nx) if grids is not None and k < len(grids) else None
+            from paper_1908_11740_gb300 import learn
+
+            K = K or learn.grid_rule(R, S)
+            t0 = time.perf_counter()
+            npairs += len(oracle.pbsm(R, S, K))
+            t += time.perf_counter() - t0
+            nrect += len(R) + len(S)
+            k += 1
+            if nrect >= 4_000_000 or t > 20:
+                break
+        cpu = {"value": npairs / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"single-threaded oracle PBSM on the first {k} joins of the batch ({nrect:,} rectangles, "
+                         f"{npairs:,} pairs, rule-of-thumb grids), {t:.2f} s"}
     if env.rank == 0:
+        peak, _ = load_peaks()
+        b_alg = 16 * n_in + 40 * E1 + 8 * P
         line = {"metric": METRIC + " (batched joins)", "value": P / (ms / 1e3), "unit": UNIT,
                 "n_gpus": env.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": f"{args.joins} independent joins, per-side sizes log-uniform in [1e3, 2e6], "
                                        f"uniform / mixture centres, log-normal extents median 1e-4",
-                           "rectangles": n_in, "pairs": P, "grids": "rule of thumb per join",
+                           "rectangles": n_in, "pairs": P, "l1_entries": E1,
+                           "grids": "measured tuner per join" if grids is not None else "rule of thumb per join",
                            "mode": "batched two-pass, CUDA graphs replayed",
                            "sharding": "joins split over ranks by input size, no data-path collective"},
+                "join_roofline": {"alg_bytes": b_alg, "alg_bytes_formula": "16 (n_R + n_S) + 40 E1 + 8 P (E1 = L1 "
+                                  "entries, a lower bound of the per-tile entries)",
+                                  "achieved_gbs": b_alg / (ms / 1e3) / 1e9, "frac": b_alg / (ms / 1e3) / 1e9 / peak},
                 "gpu_launches": tm["launches"], "clocks": clk,
                 "input_gbs": 16 * n_in / (ms / 1e3) / 1e9,
-                "phases_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in tm.items()
-                                       if k != "launches" and v[0]}}
+                "direct_launches": {"ms_per_step": ms_direct,
+                                    "phases_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in tmd.items()
+                                                           if k != "launches" and v[0]}},
+                "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     sj.sj_destroy(ctx)
     sjdist.teardown(env)
@@ -807,6 +864,81 @@ def aniso_arm(args):
     sjdist.teardown(env)
 
 
+def stripes_arm(args):
+    """1D partitioning (Sec. 3.1): the GIS-shaped 10M x 20M join on vertical
+    stripes (K x 1, swept along y) and horizontal stripes (1 x K, swept
+    along x) through the stripe kernel, against the 2D grid (3000 x 3000) and
+    against the same stripes on the general path (a second context created
+    with SJ_STRIPES=0); exact two-pass, inputs resident."""
+    import torch
+
+    from paper_1908_11740_gb300 import build, sj
+
+    env = sjdist.setup("nccl")
+    torch.cuda.set_device(env.local_rank)
+    build.build()
+    R, S = inputs.gis_pair(args.n_r, args.n_s, seed=sjdist.instance_seed(args.seed, env))
+    dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
+    ctx = sj.sj_create(env.local_rank)
+    os.environ["SJ_STRIPES"] = "0"
+    ctx_general = sj.sj_create(env.local_rank)
+    del os.environ["SJ_STRIPES"]
+    stream = torch.cuda.current_stream()
+    steps = max(3, min(args.steps, 20))
+
+    def timed(c, g):
+        o = sj.make_opts("two_pass")
+        for _ in range(max(3, args.warmup)):
+            sj.sj_join(c, dR, dS, g, o)
+        torch.cuda.synchronize()
+        sjdist.barrier(env)
+        sj.sj_timing_enable(c, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            out = sj.sj_join(c, dR, dS, g, o)
+            P = out.shape[0]
+            del out
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sjdist.barrier(env)
+        tm = sj.sj_timing_read(c)
+        sj.sj_timing_enable(c, False)
+        st = sj.sj_last_stats(c)
+        return {"ms_per_step": round(ev0.elapsed_time(ev1) / steps, 4), "pairs": P, "launches": tm["launches"],
+                "path": {0: "single-level", 1: "two-level", 2: "stripes"}[st["path"]],
+                "stored_entries": st["l1_entries_r"] + st["l1_entries_s"] if st["path"] else
+                st["entries_r"] + st["entries_s"],
+                "phases_ms": {k: round(v[1] / steps, 4) for k, v in tm.items() if k != "launches" and v[0]}}
+
+    clocks = ClockSampler(env.local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    res = {}
+    for name, c, (nx, ny) in (("vertical 3000 x 1, stripe kernel", ctx, (3000, 1)),
+                              ("vertical 7000 x 1, stripe kernel", ctx, (7000, 1)),
+                              ("horizontal 1 x 3000, stripe kernel", ctx, (1, 3000)),
+                              ("2D 3000 x 3000", ctx, (3000, 3000)),
+                              ("vertical 3000 x 1, general path", ctx_general, (3000, 1)),
+                              ("horizontal 1 x 3000, general path", ctx_general, (1, 3000))):
+        res[name] = timed(c, sj.make_grid(nx, ny))
+    clk = clocks.stop()
+    head = res["vertical 7000 x 1, stripe kernel"]
+    ms, P_all = sjdist.reduce_result(head["ms_per_step"], head["pairs"], env)
+    if env.rank == 0:
+        line = {"metric": METRIC + " (1D stripes)", "value": P_all / (ms / 1e3), "unit": UNIT,
+                "n_gpus": env.world, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"GIS-shaped plain join |R|={args.n_r:,} |S|={args.n_s:,}, 7000 vertical "
+                                       f"stripes swept along y, two-pass", "pairs": head["pairs"]},
+                "compare": res, "gpu_launches": head["launches"], "clocks": clk}
+        print(json.dumps(line), flush=True)
+    sj.sj_destroy(ctx_general)
+    sj.sj_destroy(ctx)
+    sjdist.teardown(env)
+
+
 def gbda_arm(args):
     """Duplicate avoidance: the GIS-shaped 10M x 20M join with the
     reference-point test of Eq. 1 against GBDA (class mini-joins, no test per
@@ -861,6 +993,8 @@ def main():
         aniso_arm(args)
     elif args.workload == "gbda":
         gbda_arm(args)
+    elif args.workload == "stripes":
+        stripes_arm(args)
     elif args.workload == "bands" or (int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.split == "bands"):
         bands_arm(args)
     else:

@@ -353,7 +353,8 @@ int  sj_set_model(sj_ctx *ctx, const sj_mlp *m);
 /* ---- statistics of the last join ------------------------------------------ */
 /* Counters of the last join / count on this context (host copy; valid after
  * the call returned SJ_OK).  path: 1 = two-level (blocked) partitioning,
- * 0 = single-level.  For the two-level path, l1_entries_* are the entries
+ * 0 = single-level, 2 = stripes (a 1D grid joined stripe by stripe in
+ * shared memory, swept along the stripe; blocks = stripes).  For the two-level path, l1_entries_* are the entries
  * written to the coarse blocks (a rectangle is copied into every block it
  * overlaps) and blocks / block_side describe the coarse grid; the per-tile
  * segments of the method then exist only in shared memory.  For the

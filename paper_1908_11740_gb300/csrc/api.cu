@@ -242,6 +242,10 @@ extern "C" int sj_create(sj_ctx **out, int device, void *cuda_stream) {
         if (e && strcmp(e, "private") == 0) c->shared_cursors = 0;
         const char *t = getenv("SJ_BLOCK_TARGET");   // entries per block of the two-level plan
         if (t && atoi(t) >= 64) c->block_target = atoi(t);
+        const char *st = getenv("SJ_STRIPES");   // "0": 1D grids take the general path (comparison)
+        if (st && strcmp(st, "0") == 0) c->use_stripes = 0;
+        const char *bg = getenv("SJ_BATCH_GRAPHS");   // "0": batches launch directly (phase timing)
+        if (bg && strcmp(bg, "0") == 0) c->batch_graphs = 0;
     }
     if (cudaMallocHost(&c->h_stats, sizeof(Stats)) != cudaSuccess ||
         cudaMallocHost(&c->h_aux, 64) != cudaSuccess ||

@@ -74,6 +74,9 @@ void sj::batch_release(sj_ctx *ctx) {
 // Run `body` on the internal stream as a graph cached under `key`.
 template <typename F>
 static int run_graph(sj_ctx *ctx, sj_batch_state *b, GraphCache &gc, unsigned long long key, F body) {
+    // without graphs: the same kernels launched directly on the caller's
+    // stream (their phases can then be timed)
+    if (!ctx->batch_graphs) return body();
     cudaError_t e;
     if (!(gc.exec && gc.key == key)) {
         if (gc.exec) {

@@ -176,6 +176,7 @@ struct sj_ctx {
     int bjoin_bps = 1;
     int use_blocked = 1;      // the two-level path when the grid allows it
     int use_stripes = 1;      // the stripe kernel for 1D grids
+    int batch_graphs = 1;     // batched joins replay captured CUDA graphs (else direct launches)
     int shared_cursors = 1;   // L1 write through shared per-block cursors
     int block_target = 1536;  // L1 entries a block should hold (two-level plan)
     int lpt = 1;              // one-pass join: blocks heaviest predicted cost first (else item order)

@@ -9,6 +9,7 @@ without measuring.
 
     from paper_1908_11740_gb300 import tune
     grid, block = tune.tuned(ctx, R, S)            # cached or measured
+    grids = tune.tuned_batch(ctx, Rs, Ss)          # one grid per join of a batch
 """
 from __future__ import annotations
 
@@ -121,3 +122,28 @@ def tuned(ctx, R, S, cache: Cache | None = None, device_name: str | None = None,
     f = hit["factor"] if hit else 1.0
     b = hit["block_target"] if hit else 1536
     return sj.make_grid(max(1, int(round(rule_k(m) * f)))), b
+
+
+def tuned_batch(ctx, Rs, Ss, cache: Cache | None = None, device_name: str | None = None,
+                measure_if_missing=True, factors=FACTORS, reps=2):
+    """The grid of every join of a batch: the rule of Sec. 4.3 scaled by the
+    factor cached for the join's (size, extent) bucket.  A bucket without an
+    entry is measured once, on its largest join, over the grid factors (the
+    block target of a batch is one for all joins and is not tuned here)."""
+    import torch
+
+    from . import sj
+
+    cache = cache if cache is not None else Cache()
+    dev = device_name or torch.cuda.get_device_name(ctx.device)
+    means = [mean_extent(ctx, R, S) for R, S in zip(Rs, Ss)]
+    keys = [bucket(R.shape[0] + S.shape[0], m) for R, S, m in zip(Rs, Ss, means)]
+    factor = {}
+    for key in sorted(set(keys)):
+        hit = cache.get(dev, key)
+        if hit is None and measure_if_missing:
+            j = max((i for i, k in enumerate(keys) if k == key), key=lambda i: Rs[i].shape[0] + Ss[i].shape[0])
+            hit, _ = measure(ctx, Rs[j], Ss[j], factors=factors, blocks=(1536,), reps=reps)
+            cache.put(dev, key, hit)
+        factor[key] = hit["factor"] if hit else 1.0
+    return [sj.make_grid(max(1, int(round(rule_k(m) * factor[k])))) for m, k in zip(means, keys)]
