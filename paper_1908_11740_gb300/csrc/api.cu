@@ -688,6 +688,7 @@ BArgs sj::blocked_args(Workspace &w, const BPlan &p, const float4 *R, long long 
     a.pts = w.in_pts;
     a.h = w.in_h;
     a.nbt = p.nb;
+    a.fine_cap = kFineCap;
     a.st = (Stats *)w.stats.p;
     return a;
 }

@@ -256,6 +256,7 @@ extern "C" int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, con
         a.lpool = (unsigned *)w.bList.p;
         a.lpool_cap = list_pool_cap(w);
         a.scan_part = (unsigned long long *)w.bScanPart.p;
+        a.fine_cap = kFineCap;
         a.st = (Stats *)w.stats.p;
         // the arguments that shape the captured work
         unsigned long long key = 1469598103934665603ull;

@@ -321,11 +321,12 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan_fill(BArgs a, const unsi
             a.jfirst[0] = idx;
         }
         // more entries than every tile of the block could hold in shared
-        // memory: some tile exceeds it (each entry covers a tile of its
+        // memory (fine_cap per tile: the block join's, or the stripe
+        // kernel's): some tile exceeds it (each entry covers a tile of its
         // block), and the join needs the single-level path
         {
             const unsigned long long G = (unsigned long long)(a.nj > 1 ? a.jd[lo].G : (a.G > 0 ? a.G : a.jd[0].G));
-            if ((unsigned long long)vr[k] + vs[k] > (unsigned long long)kFineCap * G * G)
+            if ((unsigned long long)vr[k] + vs[k] > (unsigned long long)a.fine_cap * G * G)
                 atomicOr(&a.st->need_direct, 1);
         }
         if (vr[k] > 0 && vs[k] > 0) {

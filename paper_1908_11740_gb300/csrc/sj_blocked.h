@@ -78,6 +78,7 @@ struct BArgs {
     float h;
     int adaptive;               // single join: sweep axis per tile from Eq. 2 histograms (Sec. 3.3)
     int gbda;                   // single join: grouping-based duplicate avoidance instead of Eq. 1
+    int fine_cap;               // entries one tile may hold for the consumer of the partition
     Stats *st;
 };
 

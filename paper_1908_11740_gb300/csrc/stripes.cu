@@ -294,6 +294,7 @@ int sj::join_stripes(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, c
         if ((st = size_blocked(ctx, w, p))) return st;
         BArgs a = blocked_args(w, p, R, nR, S, nS, gd);
         if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
+        a.fine_cap = kStCap;   // a stripe beyond the stripe kernel's capacity needs the general path
         if ((st = enqueue_blocked_partition(ctx, w, p, a))) return st;
         cudaError_t e;
         {

@@ -84,6 +84,20 @@ def test_stripe_path_taken_and_modes(sj, ctx):
     assert (buf[len(want):] == -1).all()
 
 
+@pytest.mark.parametrize("K", [150, 300])
+def test_stripes_of_several_thousand_entries(sj, ctx, K):
+    """Stripes of 5,000-15,000 entries (beyond one tile of the block join,
+    within the stripe kernel's shared memory) take the stripe path."""
+    R, S = inputs.uniform_pair(1_000_000, 1_500_000, max_extent=2e-4, seed=127)
+    for nx, ny in ((K, 1), (1, K)):
+        want = oracle.pbsm(R, S, nx, ny)
+        got = sj.sj_join(ctx, dev(R), dev(S), sj.make_grid(nx, ny))
+        st = sj.sj_last_stats(ctx)
+        assert st["path"] == 2, st
+        assert 3072 < (st["l1_entries_r"] + st["l1_entries_s"]) / K < 16384
+        np.testing.assert_array_equal(sorted_pairs(got), want)
+
+
 def test_stripe_beyond_shared_memory_falls_back(sj, ctx):
     """40,000 rectangles in one stripe (more than 16,384 entries): the general
     path joins it, exactly."""
