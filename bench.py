@@ -476,6 +476,35 @@ def batch_arm(args):
     tm = sj.sj_timing_read(ctx)
     clk = clocks.stop()
     ms, P = sjdist.reduce_result(ev0.elapsed_time(ev1) / args.steps, int(offs[-1]), env)
+    # one-pass sizing of the whole batch: the learned model and the Eq. 2 estimate
+    from paper_1908_11740_gb300 import learn
+
+    model, _ = learn.load(ctx, args.model or learn.DEFAULT_MODEL)
+    sj.sj_set_model(ctx, model)
+    one = {}
+    for name in ("one_pass", "one_pass_heur"):
+        o = sj.make_opts(name)
+        for _ in range(max(3, args.warmup)):
+            sj.sj_join_batch(ctx, Rs, Ss, grids, out=out, opts=o)
+        torch.cuda.synchronize()
+        sjdist.barrier(env)
+        sj.sj_timing_enable(ctx, True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sj.sj_join_batch(ctx, Rs, Ss, grids, out=out, opts=o)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sjdist.barrier(env)
+        tmo = sj.sj_timing_read(ctx)
+        sj.sj_timing_enable(ctx, False)
+        lo = sj.sj_last_stats(ctx)
+        one[name] = {"ms_per_step": ev0.elapsed_time(ev1) / args.steps, "capacity": lo["capacity"],
+                     "refit_blocks": lo["refit_items"], "launches": tmo["launches"],
+                     "phases_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in tmo.items()
+                                            if k != "launches" and v[0]}}
+    sj.sj_set_model(ctx, None)
+    model.free()
+    ms_one, _ = sjdist.reduce_result(one["one_pass"]["ms_per_step"], 0, env)
     # the same batch without graphs: direct launches, phases timed
     os.environ["SJ_BATCH_GRAPHS"] = "0"
     ctx_direct = sj.sj_create(env.local_rank)
@@ -515,21 +544,29 @@ def batch_arm(args):
     if env.rank == 0:
         peak, _ = load_peaks()
         b_alg = 16 * n_in + 40 * E1 + 8 * P
-        line = {"metric": METRIC + " (batched joins)", "value": P / (ms / 1e3), "unit": UNIT,
-                "n_gpus": env.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        line = {"metric": METRIC + " (batched joins)", "value": P / (ms_one / 1e3), "unit": UNIT,
+                "n_gpus": env.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_one,
                 "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": f"{args.joins} independent joins, per-side sizes log-uniform in [1e3, 2e6], "
                                        f"uniform / mixture centres, log-normal extents median 1e-4",
                            "rectangles": n_in, "pairs": P, "l1_entries": E1,
                            "grids": "measured tuner per join" if grids is not None else "rule of thumb per join",
-                           "mode": "batched two-pass, CUDA graphs replayed",
+                           "mode": "batched learned one-pass (packaged model), direct launches",
+                           "one_pass_capacity": one["one_pass"]["capacity"],
+                           "one_pass_refit_blocks": one["one_pass"]["refit_blocks"],
                            "sharding": "joins split over ranks by input size, no data-path collective"},
                 "join_roofline": {"alg_bytes": b_alg, "alg_bytes_formula": "16 (n_R + n_S) + 40 E1 + 8 P (E1 = L1 "
                                   "entries, a lower bound of the per-tile entries)",
-                                  "achieved_gbs": b_alg / (ms / 1e3) / 1e9, "frac": b_alg / (ms / 1e3) / 1e9 / peak},
-                "gpu_launches": tm["launches"], "clocks": clk,
-                "input_gbs": 16 * n_in / (ms / 1e3) / 1e9,
+                                  "achieved_gbs": b_alg / (ms_one / 1e3) / 1e9,
+                                  "frac": b_alg / (ms_one / 1e3) / 1e9 / peak},
+                "gpu_launches": one["one_pass"]["launches"], "clocks": clk,
+                "input_gbs": 16 * n_in / (ms_one / 1e3) / 1e9,
+                "compare": {"two_pass": {"ms_per_step": ms, "value": P / (ms / 1e3),
+                                         "mode": "batched two-pass, CUDA graphs replayed",
+                                         "launches": tm["launches"]},
+                            "one_pass_heur": one["one_pass_heur"],
+                            "one_pass_phases_ms_per_step": one["one_pass"]["phases_ms_per_step"]},
                 "direct_launches": {"ms_per_step": ms_direct,
                                     "phases_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in tmd.items()
                                                            if k != "launches" and v[0]}},

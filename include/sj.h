@@ -292,9 +292,19 @@ int sj_set_schedule(sj_ctx *ctx, int heaviest_first);
  *       are d_out[h_offsets[j] .. h_offsets[j+1]) (ids local to the join)
  *   h_offsets : host, nj + 1 values (also filled on SJ_EOVERFLOW, which is
  *       returned when cap < h_offsets[nj]; nothing is written then)
- * Exact two-pass join (o->mode and o->sort_output are ignored: each join's
- * range is unsorted); synchronises once after counting.
- * Joins whose tiles exceed shared memory fall back to sj_join_into each. */
+ * Modes (o->mode): SJ_TWO_PASS (default) is the exact two-pass join in
+ * graphs and synchronises once after counting.  SJ_ONE_PASS (with a model
+ * set by sj_set_model), SJ_ONE_PASS_HEUR and SJ_AUTO size the whole batch in
+ * one pass: the Eq. 2 sample of every join's blocks, the predicted pairs per
+ * block, one capacity for all blocks (heaviest first, see sj_set_schedule),
+ * one reserve-and-write block-join launch into the context's workspace, an
+ * exact re-run of the blocks that did not fit, and a regroup of every block's
+ * pairs into its join's range; direct launches, two synchronisations (the
+ * capacity, the offsets).  The pairs are the same in every mode.
+ * o->sort_output is ignored (each join's range is unsorted); o->flags
+ * (adaptive axis, GBDA) apply to single joins only.
+ * Joins whose tiles exceed shared memory fall back to sj_join_into each
+ * (exact two-pass). */
 int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const int64_t *nR,
                   const sj_rect *const *d_S, const int64_t *nS, const sj_grid *g, const sj_opts *o,
                   sj_pair *d_out, int64_t cap, int64_t *h_offsets);

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "sj_internal.h"
+#include "sj_learned.h"
 
 using namespace sj;
 
@@ -154,6 +155,188 @@ static int rule_grids(sj_ctx *ctx, Workspace &w, std::vector<JoinDesc> &jd, std:
     return SJ_OK;
 }
 
+// The batch in one pass: the join-aware Eq. 2 sample of every block, the
+// predicted pairs (model or Eq. 2), the capacity plan and heaviest-first
+// order over all joins' blocks, one reserve-and-write block-join launch into
+// a workspace buffer, an exact re-run of the blocks that did not fit, and a
+// regroup of every block's pairs into its join's range of d_out (blocks of a
+// join are consecutive work items, so the scan of the per-item counts in item
+// order gives every block's place).  Direct launches, no graphs: the
+// capacity is read back between the phases.  Returns BATCH_TWO_PASS when a
+// tile exceeds shared memory (the caller then runs the exact two-pass batch).
+constexpr int BATCH_TWO_PASS = -4;
+
+static int batch_one_pass(sj_ctx *ctx, std::vector<JoinDesc> &jd, int nbt, long long tot_r, long long tot_s,
+                          const sj_opts *o, int heuristic, sj_pair *d_out, int64_t cap, int64_t *h_offsets) {
+    Workspace &w = ctx->ws;
+    const int nj = (int)jd.size();
+    long long nsamp = 0;
+    for (int j = 0; j < nj; j++) {
+        jd[j].samp_off = nsamp;
+        nsamp += (jd[j].nR + kPhi - 1) / kPhi + (jd[j].nS + kPhi - 1) / kPhi;
+    }
+    const float margin = (o ? 1.0f + o->margin : 1.25f) * ctx->onepass_scale - 1.0f;
+    w.bcap_r = std::max<unsigned long long>(w.bcap_r, (unsigned long long)tot_r + tot_r / 8 + 1024);
+    w.bcap_s = std::max<unsigned long long>(w.bcap_s, (unsigned long long)tot_s + tot_s / 8 + 1024);
+    cudaStream_t s = ctx->stream;
+    for (int attempt = 0; attempt < 3; attempt++) {
+        BPlan p;
+        p.nb = nbt;
+        p.nc = 1;
+        p.G = 1;
+        p.bx = nbt;
+        p.by = 1;
+        int st;
+        if ((st = size_blocked(ctx, w, p)) || (st = size_learned(ctx, w, p)) ||
+            (st = upload_joins(ctx, w, jd.data(), nj)) || (st = ensure(ctx, w.bIjoin, 4ull * (nbt + 1))) ||
+            (st = ensure(ctx, w.bJfirst, 4ull * (nj + 1))) || (st = ensure(ctx, w.bJoff, 32ull * (nj + 1))) ||
+            (st = ensure(ctx, w.dstats, 2 * sizeof(Stats))))
+            return st;
+        BArgs a;
+        memset(&a, 0, sizeof a);
+        a.nb = nbt;
+        a.nbt = nbt;
+        a.nj = nj;
+        a.jd = (const JoinDesc *)w.bJd.p;
+        a.btot = (unsigned *)w.bTot.p;
+        a.bo_r = (unsigned *)w.bBoR.p;
+        a.bo_s = (unsigned *)w.bBoS.p;
+        a.items = (unsigned *)w.bItems.p;
+        a.imeta = (uint4 *)w.bImeta.p;
+        a.ins = (unsigned *)w.bIns.p;
+        a.ijoin = (unsigned *)w.bIjoin.p;
+        a.jfirst = (unsigned *)w.bJfirst.p;
+        a.bent_r = (BEnt *)w.bEntR.p;
+        a.bent_s = (BEnt *)w.bEntS.p;
+        a.cap_r = w.bcap_r;
+        a.cap_s = w.bcap_s;
+        a.cur = (unsigned *)w.bCur.p;
+        a.lpool = (unsigned *)w.bList.p;
+        a.lpool_cap = list_pool_cap(w);
+        a.scan_part = (unsigned long long *)w.bScanPart.p;
+        a.feat_raw = (unsigned *)w.bFeatRaw.p;
+        a.fine_cap = kFineCap;
+        a.st = (Stats *)w.stats.p;
+        cudaError_t e;
+        {
+            PhaseScope ph(ctx, PH_RESET, 0);
+            if ((e = zero_async(ctx, w.stats.p, sizeof(Stats))) || (e = zero_async(ctx, w.bTot.p, 8ull * nbt)) ||
+                (e = zero_async(ctx, w.bPc.p, 4ull * (nbt + 1))) ||
+                (e = zero_async(ctx, w.bFeatRaw.p, 4ull * kRawPerBlock * nbt)))
+                return cuda_fail(ctx, e, "memset");
+        }
+        {
+            PhaseScope ph(ctx, PH_COUNT, 1);
+            if ((e = launch_bcount_global(a, ctx->num_sms * 8, s))) return cuda_fail(ctx, e, "batch count");
+        }
+        {
+            PhaseScope ph(ctx, PH_SCAN, 1);
+            if ((e = launch_bscan_blocks_only(a, s))) return cuda_fail(ctx, e, "batch scan");
+        }
+        {
+            PhaseScope ph(ctx, PH_MODEL, 1);
+            if ((e = launch_bfeat_sample_batch(a, nsamp, ctx->num_sms * 4, s))) return cuda_fail(ctx, e, "sampling");
+        }
+        {
+            PhaseScope ph(ctx, PH_MODEL, 4);
+            if ((st = enqueue_prediction(ctx, w, nbt, a, heuristic, margin, 2))) return st;
+            if ((e = copy_async(ctx, ctx->h_aux, w.bCapTot.p, 8)) || (e = cudaEventRecord(ctx->ev_aux, s)))
+                return cuda_fail(ctx, e, "capacity copy");
+        }
+        {
+            PhaseScope ph(ctx, PH_SCATTER, 1);
+            if ((e = launch_bscatter(a, ctx->num_sms, s))) return cuda_fail(ctx, e, "batch write");
+        }
+        if ((e = cudaEventSynchronize(ctx->ev_aux))) return cuda_fail(ctx, e, "event sync");
+        const unsigned long long planned = *(volatile unsigned long long *)ctx->h_aux;
+        const unsigned long long C = std::max<unsigned long long>(planned, 1024ull);
+        if ((st = ensure(ctx, w.out, 8ull * C))) return st;
+        BJoinOut bo = bjoin_out(w, 2);
+        bo.list = ctx->lpt ? (const unsigned *)w.bOrder.p : nullptr;
+        bo.list_n = &a.st->nchunks;
+        bo.out = (int2 *)w.out.p;
+        bo.cap = C;
+        {
+            PhaseScope ph(ctx, PH_SWEEP_WRITE, 1);
+            if ((e = launch_bjoin(MODE_RESERVE, a, bo, ctx->num_sms * ctx->bjoin_bps, s)))
+                return cuda_fail(ctx, e, "batch join");
+        }
+        Stats stats;
+        if ((st = read_stats(ctx, w, &stats))) return st;
+        if (stats.err & kErrBadRect) return fail(ctx, SJ_EINVAL, "invalid rectangle in the batch");
+        if (stats.err & kErrEntCap) {
+            w.bcap_r = std::max<unsigned long long>(w.bcap_r, stats.e_r + stats.e_r / 8 + 1024);
+            w.bcap_s = std::max<unsigned long long>(w.bcap_s, stats.e_s + stats.e_s / 8 + 1024);
+            continue;
+        }
+        if (stats.err) return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", stats.err);
+        if (stats.need_direct) return BATCH_TWO_PASS;
+        const unsigned long long P = stats.npairs;
+        calibrate_capacity(ctx, P, planned);
+        const int2 *src = (const int2 *)w.out.p;
+        Buf big;
+        if (stats.nfail) {
+            // the blocks that did not fit, exactly, at their reserved offsets
+            if ((st = ensure(ctx, big, 8ull * P))) return st;
+            if ((e = cudaMemcpyAsync(big.p, w.out.p, 8ull * std::min(C, P), cudaMemcpyDeviceToDevice, s)))
+                return cuda_fail(ctx, e, "copy");
+            BJoinOut fo = bjoin_out(w, 3);
+            fo.list = (const unsigned *)w.bFail.p;
+            fo.list_n = &a.st->nfail;
+            fo.off_in = (const unsigned long long *)w.bResv.p;
+            fo.out = (int2 *)big.p;
+            fo.cap = P;
+            PhaseScope ph(ctx, PH_SWEEP_WRITE, 1);
+            if ((e = launch_bjoin(MODE_WRITE, a, fo, ctx->num_sms * ctx->bjoin_bps, s))) {
+                dev_free(ctx, big.p);
+                return cuda_fail(ctx, e, "batch join");
+            }
+            src = (const int2 *)big.p;
+        }
+        // every block's place in item order, every join's offset
+        unsigned long long *d_joff = (unsigned long long *)w.bJoff.p;
+        {
+            PhaseScope ph(ctx, PH_PAIRSCAN, 2);
+            if ((e = launch_scan_pairs((const unsigned *)w.bPc.p, (unsigned)nbt, (unsigned long long *)w.bPoff.p,
+                                       (Stats *)w.dstats.p, s)) ||
+                (e = launch_join_offsets(a, (const unsigned long long *)w.bPoff.p, d_joff, s)))
+                return cuda_fail(ctx, e, "pair scan");
+        }
+        if ((e = cudaMemcpyAsync(ctx->h_joff, d_joff, 8ull * (nj + 1), cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaStreamSynchronize(s))) {
+            if (big.p) dev_free(ctx, big.p);
+            return cuda_fail(ctx, e, "copy");
+        }
+        const unsigned long long *joff = (const unsigned long long *)ctx->h_joff;
+        for (int j = 0; j <= nj; j++) h_offsets[j] = (int64_t)joff[j];
+        memset(&ctx->last, 0, sizeof ctx->last);
+        ctx->last.path = 1;
+        ctx->last.blocks = nbt;
+        ctx->last.work_items = stats.nchunks;
+        ctx->last.l1_entries_r = (int64_t)stats.e_r;
+        ctx->last.l1_entries_s = (int64_t)stats.e_s;
+        ctx->last.npairs = (int64_t)P;
+        ctx->last.one_pass = 1;
+        ctx->last.capacity = (int64_t)C;
+        ctx->last.refit_items = stats.nfail;
+        int rc = SJ_OK;
+        if ((unsigned long long)cap < P) {
+            rc = fail(ctx, SJ_EOVERFLOW, "need %llu pairs, cap %lld", P, (long long)cap);
+        } else if (P && !d_out) {
+            rc = fail(ctx, SJ_EINVAL, "null output buffer");
+        } else if (P) {
+            PhaseScope ph(ctx, PH_OTHER, 1);
+            if ((e = launch_regroup((const unsigned *)w.bPc.p, (const unsigned long long *)w.bResv.p,
+                                    (const unsigned long long *)w.bPoff.p, &a.st->nchunks, src, (int2 *)d_out,
+                                    ctx->num_sms * 8, s)))
+                rc = cuda_fail(ctx, e, "regroup");
+        }
+        if (big.p) dev_free(ctx, big.p);
+        return rc;
+    }
+    return fail(ctx, SJ_EINTERNAL, "batch workspace did not converge");
+}
+
 extern "C" int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const int64_t *nR,
                              const sj_rect *const *d_S, const int64_t *nS, const sj_grid *g_in,
                              const sj_opts *o, sj_pair *d_out, int64_t cap, int64_t *h_offsets) {
@@ -220,6 +403,16 @@ extern "C" int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, con
         nbt += jd[j].bx * jd[j].by;
     }
 
+    {   // learned (or Eq. 2) one-pass sizing of the whole batch
+        const int mode = o ? o->mode : SJ_TWO_PASS;
+        const bool one_pass = mode == SJ_ONE_PASS || mode == SJ_ONE_PASS_HEUR || (mode == SJ_AUTO && ctx->mlp_loaded);
+        if (mode == SJ_ONE_PASS && !ctx->model) return fail(ctx, SJ_EINVAL, "SJ_ONE_PASS needs a model (sj_set_model)");
+        if (one_pass) {
+            st = batch_one_pass(ctx, jd, nbt, tot_r, tot_s, o, mode == SJ_ONE_PASS_HEUR ? 1 : 0, d_out, cap,
+                                h_offsets);
+            if (st != BATCH_TWO_PASS) return st;
+        }
+    }
     w.bcap_r = std::max<unsigned long long>(w.bcap_r, (unsigned long long)tot_r + tot_r / 8 + 1024);
     w.bcap_s = std::max<unsigned long long>(w.bcap_s, (unsigned long long)tot_s + tot_s / 8 + 1024);
     cudaError_t e;

@@ -221,7 +221,7 @@ extern "C" int sj_set_model(sj_ctx *ctx, const sj_mlp *m) {
 // ---------------------------------------------------------------------------
 // features + labels
 // ---------------------------------------------------------------------------
-static int size_learned(sj_ctx *ctx, Workspace &w, const BPlan &p) {
+int sj::size_learned(sj_ctx *ctx, Workspace &w, const BPlan &p) {
     int st;
     if ((st = ensure(ctx, w.bFeatRaw, 4ull * kRawPerBlock * p.nb))) return st;
     if ((st = ensure(ctx, w.bFeat, 4ull * kFeat * (p.nb + 1)))) return st;
@@ -329,6 +329,31 @@ extern "C" int sj_block_features(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, co
     return fail(ctx, SJ_EINTERNAL, "workspace did not converge");
 }
 
+// Features of every work item from the sampled histograms, the predicted
+// pairs (the model, or the Eq. 2 estimate), the capacity plan and the
+// heaviest-first order, for nb blocks (one join or a whole batch); the
+// capacity total lands in w.bCapTot.
+int sj::enqueue_prediction(sj_ctx *ctx, Workspace &w, int nb, const BArgs &a, int heuristic, float margin,
+                           unsigned slack) {
+    cudaStream_t s = ctx->stream;
+    cudaError_t e;
+    if ((e = launch_features((const unsigned *)w.bFeatRaw.p, a.items, a.btot, nb, a.st, (float *)w.bFeat.p,
+                             ctx->num_sms * 8, s)))
+        return cuda_fail(ctx, e, "features");
+    if (heuristic)
+        e = launch_heur_pred((const float *)w.bFeat.p, a.items, a.btot, nb, a.st, (float *)w.bPred.p,
+                             ctx->num_sms * 2, s);
+    else
+        e = launch_mlp_forward(weights_of(ctx->model), (const float *)w.bFeat.p, 0, &a.st->nchunks,
+                               (float *)w.bPred.p, mlp_infer_grid(ctx, nb), s);
+    if (e) return cuda_fail(ctx, e, "prediction");
+    if ((e = zero_async(ctx, w.bCapTot.p, kPlanScratch)) ||
+        (e = launch_plan((const float *)w.bPred.p, a.imeta, a.ins, a.st, margin, slack,
+                         (unsigned long long *)w.bCapTot.p, (unsigned *)w.bOrder.p, ctx->num_sms, s)))
+        return cuda_fail(ctx, e, "plan");
+    return SJ_OK;
+}
+
 // ---------------------------------------------------------------------------
 // the one-pass join
 // ---------------------------------------------------------------------------
@@ -343,7 +368,7 @@ extern "C" int sj_block_features(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, co
 // back towards 1.  Bounded to [1, 8], so that one odd join (or a model that
 // predicts nothing) cannot inflate later buffers without limit.  Exactness
 // never depends on it.
-static void calibrate_capacity(sj_ctx *ctx, unsigned long long P, unsigned long long planned) {
+void sj::calibrate_capacity(sj_ctx *ctx, unsigned long long P, unsigned long long planned) {
     const double c = (double)std::max<unsigned long long>(planned, 1);
     double f = ctx->onepass_scale;
     if ((double)P > c) f *= 1.1 * (double)P / c;

@@ -1452,6 +1452,7 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                         } else {
                             const unsigned long long bs = atomicAdd(&a.st->npairs, (unsigned long long)tot);
                             o.resv[it] = bs;
+                            if (o.cnt_out) o.cnt_out[it] = tot;
                             const bool ok = tot == 0 || bs + tot <= o.cap;
                             s_ok = ok;
                             s_base = bs;
@@ -1508,6 +1509,46 @@ __global__ void __launch_bounds__(256) k_bfeat_sample(BArgs a) {
     }
 }
 
+// Feature sampling of a batch: sample k of the batch is rectangle
+// kPhi * (k - samp_off of its join) of the join's R, then of its S (the same
+// systematic sample per side as a single join); its buckets go to the join's
+// blocks in the global block index space.
+__global__ void __launch_bounds__(256) k_bfeat_sample_batch(BArgs a, long long nsamp) {
+    extern __shared__ long long s_soff[];   // nj + 1
+    for (int j = threadIdx.x; j < a.nj; j += 256) s_soff[j] = a.jd[j].samp_off;
+    if (threadIdx.x == 0) s_soff[a.nj] = nsamp;
+    __syncthreads();
+    for (long long k = blockIdx.x * 256ll + threadIdx.x; k < nsamp; k += 256ll * gridDim.x) {
+        const int j = a.nj == 1 ? 0 : join_of(s_soff, a.nj, k);
+        const JoinDesc &d = a.jd[j];
+        const long long loc = k - s_soff[j], mr = (d.nR + kPhi - 1) / kPhi;
+        const int side = loc >= mr;
+        const long long i = (side ? loc - mr : loc) * kPhi;
+        const float4 v = ld_stream(side ? d.S + i : d.R + i);
+        if (!rect_ok(v)) continue;
+        const int cx0 = cell_of(v.x, d.g.x0, d.g.gx, d.g.nx), cx1 = cell_of(v.z, d.g.x0, d.g.gx, d.g.nx);
+        const int cy0 = cell_of(v.y, d.g.y0, d.g.gy, d.g.ny), cy1 = cell_of(v.w, d.g.y0, d.g.gy, d.g.ny);
+        feat_add(a.feat_raw + (size_t)d.boff * kRawPerBlock, d.G, d.bx, side, cx0, cx1, cy0, cy1,
+                 div_gj(cx0, d), div_gj(cx1, d), div_gj(cy0, d), div_gj(cy1, d));
+    }
+}
+
+// One warp per work item: its cnt pairs from src[resv ...] to dst[poff ...].
+__global__ void __launch_bounds__(256) k_regroup(const unsigned *__restrict__ cnt,
+                                                 const unsigned long long *__restrict__ resv,
+                                                 const unsigned long long *__restrict__ poff,
+                                                 const unsigned *__restrict__ n_dev, const int2 *__restrict__ src,
+                                                 int2 *__restrict__ dst) {
+    const unsigned n = *n_dev;
+    const unsigned lane = threadIdx.x & 31;
+    for (unsigned it = (blockIdx.x * 256u + threadIdx.x) >> 5; it < n; it += gridDim.x * 8u) {
+        const unsigned c = cnt[it];
+        const int2 *s = src + resv[it];
+        int2 *d = dst + poff[it];
+        for (unsigned i = lane; i < c; i += 32) d[i] = s[i];
+    }
+}
+
 // Sums of widths and heights of every join's rectangles (for the grid rule),
 // out[4 j + 0..3] = sum w_R, sum h_R, sum w_S, sum h_S (float64).  Every
 // lane walks a contiguous run of rectangles, accumulates in registers and
@@ -1553,6 +1594,17 @@ __global__ void __launch_bounds__(256) k_extent_stats(BArgs a, double *__restric
 cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s) {
     if (a.pts) k_bfeat_sample<1><<<grid, 256, 0, s>>>(a);
     else k_bfeat_sample<0><<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bfeat_sample_batch(const BArgs &a, long long nsamp, int grid, cudaStream_t s) {
+    k_bfeat_sample_batch<<<grid, 256, 8ull * (a.nj + 1), s>>>(a, nsamp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_regroup(const unsigned *cnt, const unsigned long long *resv, const unsigned long long *poff,
+                           const unsigned *n_dev, const int2 *src, int2 *dst, int grid, cudaStream_t s) {
+    k_regroup<<<grid, 256, 0, s>>>(cnt, resv, poff, n_dev, src, dst);
     return cudaGetLastError();
 }
 

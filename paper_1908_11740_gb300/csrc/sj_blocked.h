@@ -46,6 +46,7 @@ struct JoinDesc {
     int boff;               // first global block id
     int pad;
     float h;                // point inputs (BArgs::pts): half-width of their squares
+    long long samp_off;     // batched one-pass: first feature sample of this join
 };
 
 struct BArgs {
@@ -124,6 +125,12 @@ cudaError_t launch_bscan_blocks_only(const BArgs &a, cudaStream_t s);
 int bscan_chunks(int nb);
 cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_bfeat_sample(const BArgs &a, int grid, cudaStream_t s);
+// batches: rectangles 0, kPhi, 2 kPhi, ... of every side of every join
+cudaError_t launch_bfeat_sample_batch(const BArgs &a, long long nsamp, int grid, cudaStream_t s);
+// pairs of every work item moved from its reserved range to its place in
+// item order (batched one-pass join)
+cudaError_t launch_regroup(const unsigned *cnt, const unsigned long long *resv, const unsigned long long *poff,
+                           const unsigned *n_dev, const int2 *src, int2 *dst, int grid, cudaStream_t s);
 cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, cudaStream_t s);
 // 1D grids: one CTA per stripe, R and S sorted along the stripe in shared
 // memory, forward scan along the stripe (stripes.cu)

@@ -142,6 +142,13 @@ int blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const flo
                             const float4 *S, long long nS, const GridDev &g, Stats *stats, bool *use_direct,
                             int flags, unsigned char *tile_axis = nullptr);
 int check_opts(sj_ctx *ctx, const sj_opts *o);
+// Learned sizing buffers of nb blocks, and the prediction + capacity plan of
+// their work items (features, model or Eq. 2, plan, heaviest-first order).
+int size_learned(sj_ctx *ctx, Workspace &w, const BPlan &p);
+int enqueue_prediction(sj_ctx *ctx, Workspace &w, int nb, const BArgs &a, int heuristic, float margin,
+                       unsigned slack);
+// One-pass factor of the capacity calibration of a context (see api_learned.cu).
+void calibrate_capacity(sj_ctx *ctx, unsigned long long P, unsigned long long planned);
 // The join of sj_join / sj_join_into / sj_join_host on checked inputs.
 int join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS,
               const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs);

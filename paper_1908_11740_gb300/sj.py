@@ -620,11 +620,13 @@ def sj_block_features(ctx: Context, R, S, grid: sj_grid, with_blocks: bool = Fal
     return (X[:k], Y[:k], B[:k]) if with_blocks else (X[:k], Y[:k])
 
 
-def sj_join_batch(ctx: Context, Rs, Ss, grids=None, out: torch.Tensor | None = None):
+def sj_join_batch(ctx: Context, Rs, Ss, grids=None, out: torch.Tensor | None = None,
+                  opts: sj_opts | None = None):
     """Join every (Rs[j], Ss[j]) in one batched pass.  Returns (pairs
     int32[P, 2] device tensor, offsets int64[nj + 1]); the pairs of join j
     are pairs[offsets[j]:offsets[j+1]] (ids local to the join).  grids:
-    list of sj_grid, or None for the rule-of-thumb grid of every join."""
+    list of sj_grid, or None for the rule-of-thumb grid of every join;
+    opts.mode: two-pass (default) or one-pass sizing of the whole batch."""
     import numpy as np
     lib = load()
     nj = len(Rs)
@@ -642,11 +644,12 @@ def sj_join_batch(ctx: Context, Rs, Ss, grids=None, out: torch.Tensor | None = N
         g = (sj_grid * nj)(*grids)
     offs = np.zeros(nj + 1, np.int64)
     buf = out if out is not None else torch.empty((0, 2), dtype=torch.int32, device=ctx.device)
-    st = lib.sj_join_batch(ctx.handle, nj, pr, nr, ps, ns, g, None, buf.data_ptr() if buf.numel() else None,
+    po = ctypes.byref(opts) if opts is not None else None
+    st = lib.sj_join_batch(ctx.handle, nj, pr, nr, ps, ns, g, po, buf.data_ptr() if buf.numel() else None,
                            buf.shape[0], offs.ctypes.data)
     if st == SJ_EOVERFLOW and out is None:
         buf = torch.empty((int(offs[-1]), 2), dtype=torch.int32, device=ctx.device)
-        st = lib.sj_join_batch(ctx.handle, nj, pr, nr, ps, ns, g, None, buf.data_ptr(), buf.shape[0],
+        st = lib.sj_join_batch(ctx.handle, nj, pr, nr, ps, ns, g, po, buf.data_ptr(), buf.shape[0],
                                offs.ctypes.data)
     _check(ctx.handle, st)
     return buf[: int(offs[-1])], offs

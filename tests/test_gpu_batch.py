@@ -68,3 +68,47 @@ def test_batch_overflow_reports_offsets(sj, ctx):
     assert e.value.status == sj.SJ_EOVERFLOW
     pairs, offs = sj.sj_join_batch(ctx, Rs, Ss, None)
     assert offs[-1] == sum(len(oracle.sweep(r, s)) for r, s in joins)
+
+
+@pytest.mark.parametrize("kind", ["learned", "eq2", "undersized"])
+def test_batch_one_pass_matches_oracle(sj, ctx, kind):
+    """One-pass sizing of the whole batch: every join's range equals the
+    oracle, with the packaged model, the Eq. 2 estimate, and a model that
+    predicts no pairs (every block re-run exactly)."""
+    import oracle.learned as L
+
+    from paper_1908_11740_gb300 import learn
+
+    joins = _batch()
+    Rs = [dev(r) for r, _ in joins]
+    Ss = [dev(s) for _, s in joins]
+    model = None
+    try:
+        if kind == "learned":
+            model, _ = learn.load(ctx)
+            sj.sj_set_model(ctx, model)
+            opts = sj.make_opts("one_pass")
+        elif kind == "eq2":
+            opts = sj.make_opts("one_pass_heur")
+        else:
+            model = sj.Model(ctx, np.zeros(L.PARAMS, np.float32))
+            sj.sj_set_model(ctx, model)
+            opts = sj.make_opts("one_pass", margin=0.0)
+        for rep in range(2):
+            pairs, offs = sj.sj_join_batch(ctx, Rs, Ss, None, opts=opts)
+            st = sj.sj_last_stats(ctx)
+            assert st["one_pass"] == 1
+            if kind == "undersized":
+                assert st["refit_items"] > 0
+            got = pairs.cpu().numpy()
+            for j, (r, s) in enumerate(joins):
+                want = oracle.brute(r, s) if len(r) * len(s) < 2e7 else oracle.sweep(r, s)
+                np.testing.assert_array_equal(srt(got[offs[j]:offs[j + 1]]), want)
+        small = torch.empty((1, 2), dtype=torch.int32, device="cuda")
+        with pytest.raises(sj.SJError) as e:
+            sj.sj_join_batch(ctx, Rs, Ss, None, out=small, opts=opts)
+        assert e.value.status == sj.SJ_EOVERFLOW
+    finally:
+        sj.sj_set_model(ctx, None)
+        if model is not None:
+            model.free()

@@ -84,7 +84,7 @@ def test_stripe_path_taken_and_modes(sj, ctx):
     assert (buf[len(want):] == -1).all()
 
 
-@pytest.mark.parametrize("K", [150, 300])
+@pytest.mark.parametrize("K", [200, 400])
 def test_stripes_of_several_thousand_entries(sj, ctx, K):
     """Stripes of 5,000-15,000 entries (beyond one tile of the block join,
     within the stripe kernel's shared memory) take the stripe path."""
