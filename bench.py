@@ -334,6 +334,13 @@ def ours(args):
             compare[name] = {"ms_per_step": cms, "value": cP / (cms / 1e3), "pairs": cP,
                              "capacity": cl["capacity"] if cl["one_pass"] else None,
                              "refit_blocks": cl["refit_items"] if cl["one_pass"] else None}
+        if args.mode == "one_pass":
+            # the plan's heaviest-first block order against plain block order
+            sj.sj_set_schedule(ctx, False)
+            cms, ctm, cP = timed(opts, max(3, args.steps // 2))
+            sj.sj_set_schedule(ctx, True)
+            compare["one_pass_block_order"] = {"ms_per_step": cms, "value": cP / (cms / 1e3), "pairs": cP,
+                                               "block_join_ms": round(ctm["sweep_write"][1] / max(3, args.steps // 2), 4)}
     ms, p_all = sjdist.reduce_result(ms, P, env)
     value = p_all / (ms / 1e3)
 

@@ -159,7 +159,9 @@ __global__ void __launch_bounds__(kStThreads, 1) k_stripe_join(StArgs a, BJoinOu
     StSmem &sm = *reinterpret_cast<StSmem *>(smem_raw);
     __shared__ unsigned s_w[32];
     __shared__ unsigned s_item, s_cnt;
-    if (block_skip(a.st)) return;
+    // a stripe beyond shared memory (flagged by the block scan) sends the
+    // join to the general path, whose L1 write then did not run: stop here
+    if (block_skip_blocked(a.st)) return;
     const unsigned nitems = a.st->nchunks;
     for (;;) {
         if (threadIdx.x == 0) {

@@ -19,6 +19,10 @@ def main(argv=None):
     ap.add_argument("--workload", default="gis", choices=["gis", "uniform", "zipf"])
     ap.add_argument("--scale", type=float, default=1.0, help="fraction of the default sizes")
     ap.add_argument("--grid", type=int, default=3000)
+    ap.add_argument("--stripes", default=None, choices=["vertical", "horizontal"],
+                    help="1D grid of --grid stripes instead of a --grid x --grid grid")
+    ap.add_argument("--axis", default="x", choices=["x", "adaptive"])
+    ap.add_argument("--dedup", default="refpoint", choices=["refpoint", "gbda"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--mode", default="two_pass")
     ap.add_argument("--rho", type=float, default=0.0)
@@ -45,8 +49,13 @@ def main(argv=None):
             from . import learn
             model, _ = learn.load(ctx, a.model or learn.DEFAULT_MODEL)
             sj.sj_set_model(ctx, model)
-        g = sj.make_grid(a.grid)
-        opts = sj.make_opts(a.mode)
+        if a.stripes == "vertical":
+            g = sj.make_grid(a.grid, 1)
+        elif a.stripes == "horizontal":
+            g = sj.make_grid(1, a.grid)
+        else:
+            g = sj.make_grid(a.grid)
+        opts = sj.make_opts(a.mode, axis=a.axis, dedup=a.dedup)
         n = 0
         for i in range(a.reps):
             if i == a.reps - 1:
