@@ -817,6 +817,112 @@ int sj::blocked_partition_count(sj_ctx *ctx, Workspace &w, const BPlan &p, const
     return fail(ctx, SJ_EINTERNAL, "blocked workspace did not converge");
 }
 
+// One pass on the single-level path (one-pass modes when a tile exceeds
+// shared memory): the small tiles are counted (they are cheap to sweep
+// twice) and the large tiles' candidate chunks planned; the output holds the
+// small tiles' exact pairs plus, as an upper bound for the large tiles, one
+// pair per candidate of their chunks.  Then the small tiles are written at
+// their exact offsets and every candidate chunk of the large tiles appends
+// its pairs after them with one atomic: each large-tile candidate is
+// examined once.  The first P pairs of the output are the result.
+// ONE_PASS_UNSUITED when a caller buffer is smaller than the bound (the exact
+// two-pass join then runs).
+static int single_level_one_pass(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S,
+                                 long long nS, const GridDev &g, const sj_opts *o, OutSpec &os, int64_t *npairs) {
+    const long long T = (long long)g.nx * g.ny;
+    w.cap_r = std::max<unsigned long long>(w.cap_r, (unsigned long long)nR + nR / 4 + 1024);
+    w.cap_s = std::max<unsigned long long>(w.cap_s, (unsigned long long)nS + nS / 4 + 1024);
+    cudaStream_t s = ctx->stream;
+    for (int attempt = 0; attempt < 3; attempt++) {
+        int st;
+        if ((st = size_workspace(ctx, w, T))) return st;
+        if (!w.lcoff.p) return ONE_PASS_UNSUITED;
+        if ((st = enqueue_partition(ctx, w, R, nR, S, nS, g))) return st;
+        cudaError_t e;
+        const unsigned nslots = w.nch_cap + w.vb_cap;
+        if ((e = zero_async(ctx, w.pc.p, 4ull * nslots))) return cuda_fail(ctx, e, "memset");
+        SweepArgs a = sweep_args(w);
+        a.work_slot = 0;
+        {
+            PhaseScope ph(ctx, PH_SWEEP_COUNT, 1);
+            if ((e = launch_sweep_chunks(MODE_COUNT, a, ctx->num_sms * ctx->sweep_bps, s)))
+                return cuda_fail(ctx, e, "sweep kernel");
+        }
+        {
+            PhaseScope ph(ctx, PH_LSWEEP_COUNT, 2);
+            if ((e = launch_large_plan(large_args(w), ctx->num_sms * 4, s)))
+                return cuda_fail(ctx, e, "large-tile plan");
+        }
+        {
+            PhaseScope ph(ctx, PH_PAIRSCAN, 1);
+            if ((e = launch_scan_pairs((const unsigned *)w.pc.p, nslots, (unsigned long long *)w.poff.p,
+                                       (Stats *)w.stats.p, s)))
+                return cuda_fail(ctx, e, "pair-count scan");
+        }
+        Stats stats;
+        if ((st = read_stats(ctx, w, &stats))) return st;
+        if (stats.err & kErrBadRect)
+            return fail(ctx, SJ_EINVAL, "invalid rectangle: NaN/Inf coordinate or xl > xu / yl > yu");
+        if (stats.err & kErrTooMany) return fail(ctx, SJ_EINVAL, "more than 2^31 replicated entries on one side");
+        if (stats.err & (kErrEntCap | kErrChunkCap | kErrLargeCap)) {
+            w.cap_r = std::max<unsigned long long>(w.cap_r, stats.e_r + stats.e_r / 8 + 1024);
+            w.cap_s = std::max<unsigned long long>(w.cap_s, stats.e_s + stats.e_s / 8 + 1024);
+            continue;
+        }
+        if (stats.err) return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", stats.err);
+        const unsigned long long P_small = stats.npairs;
+        const unsigned long long bound = P_small + (unsigned long long)stats.nlch * kLargeCandChunk;
+        if (os.kind == OutSpec::INTO && (unsigned long long)os.cap < bound) return ONE_PASS_UNSUITED;
+        if ((st = out_acquire(ctx, w, os, bound))) return st;
+        if (bound) {
+            SweepArgs wa = sweep_args(w);
+            wa.out = os.got;
+            wa.cap = bound;
+            wa.work_slot = 2;
+            PhaseScope ph(ctx, PH_SWEEP_WRITE, 1);
+            if ((e = launch_sweep_chunks(MODE_WRITE, wa, ctx->num_sms * ctx->sweep_bps, s))) {
+                out_abandon(ctx, os);
+                return cuda_fail(ctx, e, "sweep kernel");
+            }
+        }
+        if (stats.nlch) {
+            SweepArgs la = sweep_args(w);
+            la.out = os.got;
+            la.cap = bound;
+            la.work_slot = 3;
+            la.base = P_small;
+            la.append = &((Stats *)w.stats.p)->apairs;
+            PhaseScope ph(ctx, PH_LSWEEP_WRITE, 1);
+            if ((e = launch_large_append(large_args(w), la, ctx->num_sms * 4, s))) {
+                out_abandon(ctx, os);
+                return cuda_fail(ctx, e, "large-tile sweep kernel");
+            }
+        }
+        if ((st = read_stats(ctx, w, &stats))) {
+            out_abandon(ctx, os);
+            return st;
+        }
+        if (stats.err) {
+            out_abandon(ctx, os);
+            return fail(ctx, SJ_EINTERNAL, "device error bits 0x%x", stats.err);
+        }
+        const unsigned long long P = P_small + stats.apairs;
+        *npairs = (int64_t)P;
+        memset(&ctx->last, 0, sizeof ctx->last);
+        ctx->last.entries_r = (int64_t)stats.e_r;
+        ctx->last.entries_s = (int64_t)stats.e_s;
+        ctx->last.npairs = (int64_t)P;
+        ctx->last.one_pass = 1;
+        ctx->last.capacity = (int64_t)bound;
+        if (o && o->sort_output && P && (st = sort_pairs(ctx, w, os.got, P))) {
+            out_abandon(ctx, os);
+            return st;
+        }
+        return SJ_OK;
+    }
+    return fail(ctx, SJ_EINTERNAL, "workspace did not converge");
+}
+
 int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
                   int64_t nS, const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs) {
     const int mode = o ? o->mode : SJ_TWO_PASS;
@@ -827,17 +933,19 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
     }
     const bool one_pass = (mode == SJ_ONE_PASS || mode == SJ_ONE_PASS_HEUR ||
                            (mode == SJ_AUTO && ctx->mlp_loaded));
+    bool direct_known = false;   // a tile exceeds shared memory: the single-level path
     if (one_pass) {
         int st = join_one_pass_spec(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, o,
                                     mode == SJ_ONE_PASS_HEUR ? 1 : 0, os, npairs, nullptr);
-        if (st != ONE_PASS_UNSUITED) return st;
-        os.got = nullptr;   // the grid or the data need the exact two-pass join
+        if (st != ONE_PASS_UNSUITED && st != ONE_PASS_DIRECT) return st;
+        direct_known = st == ONE_PASS_DIRECT;
+        os.got = nullptr;   // the grid or the data need another path
     }
     Stats stats;
     int st;
     BPlan bp;
     const int flags = o ? o->flags : 0;
-    if (plan_blocked(ctx, gd, nR, nS, bp)) {
+    if (!direct_known && plan_blocked(ctx, gd, nR, nS, bp)) {
         bool direct = false;
         if ((st = blocked_partition_count(ctx, w, bp, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd,
                                           &stats, &direct, flags)))
@@ -870,6 +978,11 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
         }
     }
     if (w.in_pts) return PTS_UNSUITED;   // the single-level path reads rectangles only
+    if (one_pass) {
+        st = single_level_one_pass(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, o, os, npairs);
+        if (st != ONE_PASS_UNSUITED) return st;
+        os.got = nullptr;
+    }
     st = partition_and_count(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &stats, true);
     if (st) return st;
     return write_pass(ctx, w, stats, o, os, npairs);

@@ -496,7 +496,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         }
         if (stats.need_direct) {
             out_abandon(ctx, os);
-            return ONE_PASS_UNSUITED;
+            return ONE_PASS_DIRECT;
         }
         const unsigned long long P = stats.npairs;
         *npairs = (int64_t)P;

@@ -70,6 +70,7 @@ struct Stats {
     int pad;
     unsigned int nlch;                  // candidate chunks of the large-tile sweep
     unsigned int naxis_y;               // blocked path: work items swept along y (adaptive axis)
+    unsigned long long apairs;          // large tiles appended in one pass (single-level one-pass)
 };
 
 // ---- the cell function (tile index of a coordinate) ------------------------

@@ -101,6 +101,9 @@ struct OutSpec;
 // returned by join_one_pass_spec when the grid or the data do not suit the
 // two-level path; the caller then runs the exact two-pass join
 constexpr int ONE_PASS_UNSUITED = -1;
+// ... and when a tile exceeds shared memory (the caller then goes straight to
+// the single-level path)
+constexpr int ONE_PASS_DIRECT = -5;
 // returned by join_core for point inputs when the two-level path does not
 // suit the data (the caller then materialises the squares)
 constexpr int PTS_UNSUITED = -2;

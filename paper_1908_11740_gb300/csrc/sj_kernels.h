@@ -20,7 +20,7 @@ namespace sj {
 cudaError_t zero_words_async(void *p, size_t bytes, cudaStream_t s);
 cudaError_t copy_words_async(void *dst, const void *src, size_t bytes, cudaStream_t s);
 
-enum { MODE_COUNT = 0, MODE_WRITE = 1, MODE_RESERVE = 2, MODE_TILES = 3 };
+enum { MODE_COUNT = 0, MODE_WRITE = 1, MODE_RESERVE = 2, MODE_TILES = 3, MODE_APPEND = 4 };
 
 // Arguments of the sweep kernels (small-tile chunks and large tiles).
 struct SweepArgs {
@@ -41,8 +41,10 @@ struct SweepArgs {
     unsigned *nfail;                  // ... their number (device)
     unsigned cnt_base;                // large path: first slot in cnt_out/off_in/resv
     int2 *out;                        // pair buffer
-    unsigned long long cap;           // MODE_RESERVE: capacity of out
+    unsigned long long cap;           // MODE_RESERVE / MODE_APPEND: capacity of out
     unsigned *tile_pairs;             // MODE_TILES: pairs per tile
+    unsigned long long base;          // MODE_APPEND: first slot of the appended pairs
+    unsigned long long *append;       // MODE_APPEND: pairs appended so far (device counter)
 };
 
 // Arguments of the large-tile path (segmented radix sort + sweep).
@@ -92,6 +94,11 @@ cudaError_t launch_sweep_chunks(int mode, const SweepArgs &a, int grid, cudaStre
 cudaError_t launch_large_sort(LargeArgs a, int grid, cudaStream_t s);
 cudaError_t launch_sweep_large(int mode, const LargeArgs &a, const SweepArgs &o, int grid,
                                cudaStream_t s);
+// one-pass large tiles: candidate ranges and chunks (sets st->nlch), then the
+// candidate sweep appending every chunk's pairs at o.base + *o.append
+constexpr int kLargeCandChunk = 4096;   // candidates per chunk of the large-tile sweep
+cudaError_t launch_large_plan(const LargeArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_large_append(const LargeArgs &a, const SweepArgs &o, int grid, cudaStream_t s);
 cudaError_t launch_scan_pairs(const unsigned *cnt, unsigned n, unsigned long long *off, Stats *st,
                               cudaStream_t s);
 

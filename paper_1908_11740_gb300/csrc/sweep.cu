@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(256) k_sweep_large(LargeArgs a, SweepArgs o) {
 //  4. k_large_finish (count pass): the per-block counts as 32-bit work-item
 //     counts of the pair scan.
 // ---------------------------------------------------------------------------
-constexpr int kCandChunk = 4096;
+constexpr int kCandChunk = kLargeCandChunk;
 constexpr int kCandThreads = 256;
 
 // Exclusive scan over the NT threads of a block; *total = sum.  Every warp
@@ -878,7 +878,7 @@ __global__ void __launch_bounds__(kCandThreads) k_large_cand(LargeArgs a, SweepA
 #pragma unroll
                 for (int u = 0; u < kU; u++) {   // y-test, reference-point test, emission
                     const bool hit = ok[u] && ob[u].y <= pv[u].w && pv[u].y <= ob[u].w && reported_here(pid[u], oid[u]);
-                    if (MODE == MODE_WRITE) {
+                    if (MODE == MODE_WRITE || MODE == MODE_APPEND) {
                         const unsigned hm = __ballot_sync(kFull, hit);
                         if (hm) {
                             unsigned pos = 0;
@@ -893,12 +893,18 @@ __global__ void __launch_bounds__(kCandThreads) k_large_cand(LargeArgs a, SweepA
                     }
                 }
             }
-            if (MODE == MODE_WRITE) {
+            if (MODE == MODE_WRITE || MODE == MODE_APPEND) {
                 __syncthreads();
-                if (threadIdx.x == 0 && s_n)
-                    s_base = o.off_in[o.cnt_base + vb] + atomicAdd(&a.vbcur[vb], (unsigned long long)s_n);
+                if (threadIdx.x == 0 && s_n) {
+                    if (MODE == MODE_APPEND) {   // one pass: the chunk's range from one atomic
+                        s_base = o.base + atomicAdd(o.append, (unsigned long long)s_n);
+                        if (s_base + s_n > o.cap) atomicOr(&o.st->err, kErrOutCap);
+                    } else {
+                        s_base = o.off_in[o.cnt_base + vb] + atomicAdd(&a.vbcur[vb], (unsigned long long)s_n);
+                    }
+                }
                 __syncthreads();
-                const unsigned n = s_n;
+                const unsigned n = (MODE == MODE_APPEND && s_base + s_n > o.cap) ? 0u : s_n;
                 for (unsigned i = threadIdx.x; i < n; i += kCandThreads) o.out[s_base + i] = s_pairs[i];
             } else {
 #pragma unroll
@@ -1032,6 +1038,19 @@ cudaError_t launch_sweep_large(int mode, const LargeArgs &a, const SweepArgs &o,
         case MODE_RESERVE: k_sweep_large<MODE_RESERVE><<<grid, 256, 0, s>>>(a, o); break;
         default: k_sweep_large<MODE_TILES><<<grid, 256, 0, s>>>(a, o); break;
     }
+    return cudaGetLastError();
+}
+
+// One-pass large tiles: the candidate ranges and chunks (before the count is
+// known), then the candidate sweep appending each chunk's pairs.
+cudaError_t launch_large_plan(const LargeArgs &a, int grid, cudaStream_t s) {
+    k_large_ranges<<<grid, kCandThreads, 0, s>>>(a);
+    k_large_plan<<<1, 1024, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_large_append(const LargeArgs &a, const SweepArgs &o, int grid, cudaStream_t s) {
+    k_large_cand<MODE_APPEND><<<grid, kCandThreads, 0, s>>>(a, o);
     return cudaGetLastError();
 }
 
