@@ -65,6 +65,8 @@ def parse():
                     help="aniso: grids to time (1750: the tile-extent rule; 600: coarse tiles)")
     ap.add_argument("--rho", type=float, default=2.1e-4,
                     help="skew: probability that S shares R's hot spots (2.1e-4: about 1e9 pairs)")
+    ap.add_argument("--skew-mode", default="one_pass_heur", choices=["one_pass_heur", "two_pass"],
+                    help="skew: one pass (small tiles counted, large tiles appended) or the exact two-pass join")
     ap.add_argument("--skew-grid", type=int, default=500,
                     help="skew: tiles per axis (500: fastest of 500-3000 on this workload)")
     ap.add_argument("--split", default="bands", choices=["bands", "instances"],
@@ -588,8 +590,12 @@ def skew_arm(args):
     lattice, R extents U[0, 1e-4], S extents U[0, 1e-3], S sharing R's hot
     spots with probability rho; grid --skew-grid (500 x 500).  Hot lattice cells hold
     millions of entries, so the join runs on the single-level path (global
-    segmented radix sort of the large tiles).  Exact two-pass join: the
-    output is 8 bytes per pair (7.7 GB at rho = 2.1e-4)."""
+    segmented radix sort of the large tiles).  By default the one-pass join
+    (the small tiles counted, the large tiles' pairs appended after them in
+    one examination of their candidates, into an output sized by the small
+    tiles' pairs plus one slot per large-tile candidate); the exact two-pass
+    join is timed alongside.  The output is 8 bytes per pair (7.7 GB at
+    rho = 2.1e-4)."""
     import torch
 
     from paper_1908_11740_gb300 import build, sj
@@ -601,7 +607,9 @@ def skew_arm(args):
     dR, dS = torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda()
     ctx = sj.sj_create(env.local_rank)
     g = sj.make_grid(args.skew_grid)
-    o = sj.make_opts("two_pass")
+    # one pass (small tiles counted, large tiles appended) is the default; the
+    # exact two-pass join is timed alongside
+    o = sj.make_opts(args.skew_mode)
     for _ in range(max(3, args.warmup)):
         sj.sj_join(ctx, dR, dS, g, o)
     torch.cuda.synchronize()
@@ -622,9 +630,23 @@ def skew_arm(args):
     torch.cuda.synchronize()
     sjdist.barrier(env)
     tm = sj.sj_timing_read(ctx)
+    sj.sj_timing_enable(ctx, False)
     clk = clocks.stop()
     st = sj.sj_last_stats(ctx)
     ms, P_all = sjdist.reduce_result(ev0.elapsed_time(ev1) / steps, P, env)
+    other = "two_pass" if args.skew_mode != "two_pass" else "one_pass_heur"
+    o2 = sj.make_opts(other)
+    sj.sj_join(ctx, dR, dS, g, o2)
+    torch.cuda.synchronize()
+    sj.sj_timing_enable(ctx, True)
+    ev0.record(stream)
+    for _ in range(steps):
+        out = sj.sj_join(ctx, dR, dS, g, o2)
+        del out
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    tm2 = sj.sj_timing_read(ctx)
+    ms2 = ev0.elapsed_time(ev1) / steps
     if env.rank == 0:
         n_in = 40_000_000
         E = st["entries_r"] + st["entries_s"]
@@ -633,8 +655,12 @@ def skew_arm(args):
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": f"Zipf(1.2) skew |R|=|S|=20M, rho={args.rho}, grid {args.skew_grid}x{args.skew_grid}",
-                           "pairs": P, "entries": E, "mode": "two_pass",
+                           "pairs": P, "entries": E, "mode": args.skew_mode,
+                           "one_pass_capacity": st["capacity"] if st["one_pass"] else None,
                            "path": "single-level" if st["path"] == 0 else "two-level"},
+                "compare": {other: {"ms_per_step": ms2, "value": P / (ms2 / 1e3),
+                                    "phases_ms_per_step": {k: round(v[1] / steps, 4) for k, v in tm2.items()
+                                                           if k != "launches" and v[0]}}},
                 "join_roofline": {"alg_bytes": 16 * n_in + 40 * E + 8 * P,
                                   "achieved_gbs": (16 * n_in + 40 * E + 8 * P) / (ms / 1e3) / 1e9},
                 "gpu_launches": tm["launches"], "clocks": clk,

@@ -10,7 +10,9 @@ and xor of a 64-bit mix of every pair, ``oracle.pbsm_digest``), and the GPU
 pairs are folded into the same digest on the host, chunk by chunk
 (``tests/pair_digest.py``, written independently with numpy).  Beside it: no
 pair occurs twice, the count equals sj_count, and the device-sorted output is
-exactly the same set in (r, s) order."""
+exactly the same set in (r, s) order.  The one-pass join of the same input
+(small tiles counted, large tiles appended in one examination of their
+candidates) gives the same digest."""
 import numpy as np
 import pytest
 
@@ -62,3 +64,7 @@ def test_skew_full_size(sj, ctx, rho):
     srt = sj.sj_join(ctx, dR, dS, g, sj.make_opts("two_pass", sort_output=True))
     skey = srt[:, 0].to(torch.int64) * (1 << 32) + srt[:, 1].to(torch.int64)
     assert torch.equal(skey, key)
+    del srt, skey, key
+    one = sj.sj_join(ctx, dR, dS, g, sj.make_opts("one_pass_heur"))
+    assert sj.sj_last_stats(ctx)["one_pass"] == 1
+    assert digest_device(one) == want
