@@ -54,13 +54,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--cpu-frac", type=float, default=0.125,
                     help="CPU sample: rectangles whose centre has y < frac")
-    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance", "aniso", "bands", "gbda", "stripes"],
+    ap.add_argument("--workload", default="gis", choices=["gis", "batch", "skew", "distance", "aniso", "bands", "gbda", "stripes", "link"],
                     help="gis: the 10M x 20M GIS-shaped join (default); batch: 256 joins of uneven size; "
                          "skew: the 20M x 20M Zipf extent / skew stress; aniso: 10M x 20M elongated "
                          "rectangles, sweep along x against the adaptive axis of Sec. 3.3; bands: the gis join "
                          "split into one band of tile rows per rank (the default for gis with N > 1); gbda: "
                          "the gis join with Eq. 1 against GBDA duplicate avoidance; stripes: the gis join on "
-                         "1D grids (stripe kernel) against the 2D grid")
+                         "1D grids (stripe kernel) against the 2D grid; link: the host link's copy bandwidth "
+                         "and a copy running beside a join")
     ap.add_argument("--aniso-grids", default="1750,600",
                     help="aniso: grids to time (1750: the tile-extent rule; 600: coarse tiles)")
     ap.add_argument("--rho", type=float, default=2.1e-4,
@@ -1009,6 +1010,98 @@ def stripes_arm(args):
     sjdist.teardown(env)
 
 
+def link_arm(args):
+    """The host link behind the end-to-end numbers: the copy of the GIS-shaped
+    join's inputs (480 MB) host -> device from page-locked memory, the copy of
+    its pairs back, each alone; then the input copy on a second stream while
+    the learned one-pass join runs on the first, against each alone.  CUDA
+    events; the copies are single cudaMemcpyAsync calls (torch copy_)."""
+    import torch
+
+    from paper_1908_11740_gb300 import build, learn, sj
+
+    env = sjdist.setup("nccl")
+    torch.cuda.set_device(env.local_rank)
+    build.build()
+    R, S = inputs.gis_pair(args.n_r, args.n_s, seed=args.seed)
+    hin = torch.from_numpy(np.concatenate([R, S])).pin_memory()
+    din = hin.cuda()
+    dR, dS = din[:len(R)], din[len(R):]
+    ctx = sj.sj_create(env.local_rank)
+    model, _ = learn.load(ctx, args.model or learn.DEFAULT_MODEL)
+    sj.sj_set_model(ctx, model)
+    g = sj.make_grid(args.grid)
+    o = sj.make_opts("one_pass")
+    pairs = sj.sj_join(ctx, dR, dS, g, o)
+    hout = torch.empty(pairs.shape, dtype=pairs.dtype).pin_memory()
+    dcopy = torch.empty_like(din)
+    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    steps = max(3, min(args.steps, 20))
+
+    def timed(fn, stream):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def h2d():
+        with torch.cuda.stream(side):
+            dcopy.copy_(hin, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(side):
+            hout.copy_(pairs, non_blocking=True)
+
+    def join():
+        out = sj.sj_join(ctx, dR, dS, g, o)
+        del out
+
+    h2d_ms, d2h_ms, join_ms = timed(h2d, side), timed(d2h, side), timed(join, main)
+    # both at once: the copy on the side stream, the join on the main stream
+    for _ in range(2):
+        h2d(); join()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev = []
+    for _ in range(steps):
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        j0, j1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(side)
+        h2d()
+        c1.record(side)
+        j0.record(main)
+        join()
+        j1.record(main)
+        torch.cuda.synchronize()
+        ev.append((c0.elapsed_time(c1), j0.elapsed_time(j1)))
+    both_ms = (time.perf_counter() - t0) * 1e3 / steps
+    if env.rank == 0:
+        nb = hin.numel() * 4
+        line = {"metric": "host link: copy bandwidth and copy / join overlap", "value": nb / (h2d_ms / 1e3) / 1e9,
+                "unit": "GB/s (host -> device, page-locked)", "n_gpus": env.world, "steps": steps,
+                "warmup": 2, "ms_per_step": h2d_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"{nb / 1e6:.0f} MB of inputs of the GIS-shaped join, "
+                                       f"{pairs.shape[0]:,} pairs back"},
+                "h2d": {"ms": h2d_ms, "gbs": nb / (h2d_ms / 1e3) / 1e9},
+                "d2h": {"ms": d2h_ms, "gbs": hout.numel() * 4 / (d2h_ms / 1e3) / 1e9},
+                "join_alone_ms": join_ms,
+                "together": {"copy_ms": float(np.median([c for c, _ in ev])),
+                             "join_ms": float(np.median([j for _, j in ev])),
+                             "wall_ms_per_step": both_ms}}
+        print(json.dumps(line), flush=True)
+    sj.sj_set_model(ctx, None)
+    model.free()
+    sj.sj_destroy(ctx)
+    sjdist.teardown(env)
+
+
 def gbda_arm(args):
     """Duplicate avoidance: the GIS-shaped 10M x 20M join with the
     reference-point test of Eq. 1 against GBDA (class mini-joins, no test per
@@ -1065,6 +1158,8 @@ def main():
         gbda_arm(args)
     elif args.workload == "stripes":
         stripes_arm(args)
+    elif args.workload == "link":
+        link_arm(args)
     elif args.workload == "bands" or (int(os.environ.get("WORLD_SIZE", "1")) > 1 and args.split == "bands"):
         bands_arm(args)
     else:
