@@ -246,6 +246,8 @@ extern "C" int sj_create(sj_ctx **out, int device, void *cuda_stream) {
         if (st && strcmp(st, "0") == 0) c->use_stripes = 0;
         const char *bg = getenv("SJ_BATCH_GRAPHS");   // "0": batches launch directly (phase timing)
         if (bg && strcmp(bg, "0") == 0) c->batch_graphs = 0;
+        const char *bc = getenv("SJ_BATCH_COUNT");   // "global": per-rectangle global atomics (comparison)
+        if (bc && strcmp(bc, "global") == 0) c->batch_count_local = 0;
     }
     if (cudaMallocHost(&c->h_stats, sizeof(Stats)) != cudaSuccess ||
         cudaMallocHost(&c->h_aux, 64) != cudaSuccess ||
@@ -504,13 +506,39 @@ int sj::enqueue_sweep(sj_ctx *ctx, Workspace &w, int mode, int2 *out, unsigned l
     return SJ_OK;
 }
 
+// Debug build: SJ_EINTERNAL naming the site of the first failed bounds check.
+int sj::check_failed(sj_ctx *ctx, unsigned site) {
+    static const char *const files[] = {"?",          "blocked.cu",   "sweep.cu",   "partition.cu",
+                                        "stripes.cu", "distance.cu",  "bands.cu",   "sortpairs.cu",
+                                        "learned.cu", "noalloc.cu"};
+    const unsigned f = site >> 16;
+    return fail(ctx, SJ_EINTERNAL, "bounds check failed at %s:%u",
+                f < sizeof files / sizeof files[0] ? files[f] : "?", site & 0xffffu);
+}
+
 int sj::read_stats(sj_ctx *ctx, Workspace &w, Stats *out) {
     cudaError_t e;
     if ((e = copy_async(ctx, ctx->h_stats, w.stats.p, sizeof(Stats))))
         return cuda_fail(ctx, e, "stats copy");
     if ((e = cudaStreamSynchronize(ctx->stream))) return cuda_fail(ctx, e, "stream sync");
     memcpy(out, ctx->h_stats, sizeof(Stats));
+#if SJ_CHECK
+    if (out->err & kErrCheck) return check_failed(ctx, out->check);
+#endif
     return SJ_OK;
+}
+
+// Debug build: after a call's last kernel, read the counters once more so
+// that a check failed after the last read is reported (no-op otherwise).
+int sj::check_tail(sj_ctx *ctx, Workspace &w) {
+#if SJ_CHECK
+    Stats s;
+    return read_stats(ctx, w, &s);
+#else
+    (void)ctx;
+    (void)w;
+    return SJ_OK;
+#endif
 }
 
 // Partition + count pass with capacity retry.  On return the workspace
@@ -923,8 +951,8 @@ static int single_level_one_pass(sj_ctx *ctx, Workspace &w, const float4 *R, lon
     return fail(ctx, SJ_EINTERNAL, "workspace did not converge");
 }
 
-int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
-                  int64_t nS, const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs) {
+static int join_core_body(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
+                          int64_t nS, const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs) {
     const int mode = o ? o->mode : SJ_TWO_PASS;
     {   // 1D grids (stripes): the stripe kernel, exact two-pass, in any mode
         const int st = join_stripes(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, o, os, npairs);
@@ -962,6 +990,12 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
             BJoinOut bo = bjoin_out(w, 1);
             bo.out = os.got;
             bo.cap = P;
+#if SJ_CHECK
+            // debug build, self-test of the checks: one slot fewer than the
+            // pairs, so the bound of the last pair's write fails (the write
+            // is skipped, nothing is written out of bounds)
+            if (getenv("SJ_CHECK_SELFTEST")) bo.cap = P - 1;
+#endif
             cudaError_t e;
             {
                 PhaseScope ph(ctx, PH_SWEEP_WRITE, 1);
@@ -986,6 +1020,13 @@ int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, con
     st = partition_and_count(ctx, w, (const float4 *)d_R, nR, (const float4 *)d_S, nS, gd, &stats, true);
     if (st) return st;
     return write_pass(ctx, w, stats, o, os, npairs);
+}
+
+int sj::join_core(sj_ctx *ctx, Workspace &w, const sj_rect *d_R, int64_t nR, const sj_rect *d_S,
+                  int64_t nS, const GridDev &gd, const sj_opts *o, OutSpec &os, int64_t *npairs) {
+    int st = join_core_body(ctx, w, d_R, nR, d_S, nS, gd, o, os, npairs);
+    if (st == SJ_OK && (st = check_tail(ctx, w))) out_abandon(ctx, os);
+    return st;
 }
 
 int sj::check_opts(sj_ctx *ctx, const sj_opts *o) {
@@ -1227,6 +1268,10 @@ extern "C" int sj_part_join(sj_ctx *ctx, sj_part *p, const sj_opts *o, sj_pair *
     OutSpec os{OutSpec::LIB};
     *d_pairs = nullptr;
     if ((st = write_pass(ctx, w, stats, o, os, npairs))) return st;
+    if ((st = check_tail(ctx, w))) {
+        out_abandon(ctx, os);
+        return st;
+    }
     *d_pairs = (sj_pair *)os.got;
     return SJ_OK;
 }

@@ -227,7 +227,9 @@ static int batch_one_pass(sj_ctx *ctx, std::vector<JoinDesc> &jd, int nbt, long 
         }
         {
             PhaseScope ph(ctx, PH_COUNT, 1);
-            if ((e = launch_bcount_global(a, ctx->num_sms * 8, s))) return cuda_fail(ctx, e, "batch count");
+            e = ctx->batch_count_local ? launch_bcount_local(a, ctx->num_sms * 2, s)
+                                       : launch_bcount_global(a, ctx->num_sms * 8, s);
+            if (e) return cuda_fail(ctx, e, "batch count");
         }
         {
             PhaseScope ph(ctx, PH_SCAN, 1);
@@ -337,9 +339,24 @@ static int batch_one_pass(sj_ctx *ctx, std::vector<JoinDesc> &jd, int nbt, long 
     return fail(ctx, SJ_EINTERNAL, "batch workspace did not converge");
 }
 
+static int join_batch_body(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const int64_t *nR,
+                           const sj_rect *const *d_S, const int64_t *nS, const sj_grid *g_in, const sj_opts *o,
+                           sj_pair *d_out, int64_t cap, int64_t *h_offsets);
+
 extern "C" int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const int64_t *nR,
                              const sj_rect *const *d_S, const int64_t *nS, const sj_grid *g_in,
                              const sj_opts *o, sj_pair *d_out, int64_t cap, int64_t *h_offsets) {
+    int st = join_batch_body(ctx, nj, d_R, nR, d_S, nS, g_in, o, d_out, cap, h_offsets);
+    if (st == SJ_OK) {
+        DeviceGuard dg(ctx->device);
+        st = check_tail(ctx, ctx->ws);
+    }
+    return st;
+}
+
+static int join_batch_body(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const int64_t *nR,
+                           const sj_rect *const *d_S, const int64_t *nS, const sj_grid *g_in, const sj_opts *o,
+                           sj_pair *d_out, int64_t cap, int64_t *h_offsets) {
     if (!ctx) return SJ_EINVAL;
     if (nj < 1 || nj > kMaxJoins) return fail(ctx, SJ_EINVAL, "1 <= joins <= %d", kMaxJoins);
     if (!d_R || !nR || !d_S || !nS || !h_offsets || cap < 0) return fail(ctx, SJ_EINVAL, "null argument");
@@ -468,7 +485,9 @@ extern "C" int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, con
                 return cuda_fail(ctx, e2, "memset");
             {
                 PhaseScope ph(ctx, PH_COUNT, 1);
-                if ((e2 = launch_bcount_global(a, grid_l1, s))) return cuda_fail(ctx, e2, "batch count");
+                e2 = ctx->batch_count_local ? launch_bcount_local(a, ctx->num_sms * 2, s)
+                                            : launch_bcount_global(a, grid_l1, s);
+                if (e2) return cuda_fail(ctx, e2, "batch count");
             }
             {
                 PhaseScope ph(ctx, PH_SCAN, 1);

@@ -400,6 +400,7 @@ int sj::join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long
         if ((st = size_blocked(ctx, w, p)) || (st = size_learned(ctx, w, p))) return st;
         BArgs a = blocked_args(w, p, R, nR, S, nS, gd);
         a.feat_raw = (unsigned *)w.bFeatRaw.p;
+        a.stop_direct = 1;
         if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
         a.adaptive = o && (o->flags & SJ_SWEEP_ADAPTIVE);
         a.gbda = o && (o->flags & SJ_DEDUP_GBDA);

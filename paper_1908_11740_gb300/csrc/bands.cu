@@ -21,6 +21,7 @@
 //     its reference tile, max(cy0_r, cy0_s) = cell(max(r.y_l, s.y_l)) (the
 //     cell function is monotone), lies in the band; kept pairs are written in
 //     candidate order with the input indices of both rectangles.
+#define SJ_FILE_CODE 6
 #include "sj_internal.h"
 
 namespace sj {
@@ -155,7 +156,8 @@ __global__ void __launch_bounds__(kBandThreads) k_band_write_pairs(const int2 *_
                                                                    const unsigned long long *__restrict__ off,
                                                                    const int *__restrict__ ir,
                                                                    const int *__restrict__ is,
-                                                                   int2 *__restrict__ out) {
+                                                                   int2 *__restrict__ out, Stats *st,
+                                                                   unsigned long long cap) {
     __shared__ unsigned s_pre[kBandWords];
     const unsigned *m = mask + (size_t)blockIdx.x * kBandWords;
     chunk_prefix(m, s_pre);
@@ -169,7 +171,8 @@ __global__ void __launch_bounds__(kBandThreads) k_band_write_pairs(const int2 *_
         const long long k = base + u * kBandThreads;
         if (((b >> lane) & 1u) && k < C) {
             const int2 p = cand[k];
-            out[o + s_pre[w] + __popc(b & lt)] = make_int2(__ldg(ir + p.x), __ldg(is + p.y));
+            const unsigned long long d = o + s_pre[w] + __popc(b & lt);
+            if (SJ_IN(st, d, cap)) out[d] = make_int2(__ldg(ir + p.x), __ldg(is + p.y));
         }
     }
 }
@@ -274,7 +277,7 @@ int rows_core(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, i
         PhaseScope ph(ctx, PH_OTHER, 1);
         k_band_write_pairs<<<(unsigned)nch, kBandThreads, 0, ctx->stream>>>(
             cs.got, C, (const unsigned *)w.dmask.p, (const unsigned long long *)w.doff.p, (const int *)w.band_ir.p,
-            (const int *)w.band_is.p, os.got);
+            (const int *)w.band_is.p, os.got, (Stats *)w.stats.p, P);
         if ((e = cudaGetLastError())) {
             out_abandon(ctx, os);
             return cuda_fail(ctx, e, "band pair write");
@@ -284,7 +287,8 @@ int rows_core(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, i
         out_abandon(ctx, os);
         return st;
     }
-    return SJ_OK;
+    if ((st = check_tail(ctx, w))) out_abandon(ctx, os);
+    return st;
 }
 
 int rows_check(sj_ctx *ctx, const sj_rect *d_R, int64_t nR, const sj_rect *d_S, int64_t nS, const sj_grid *g,

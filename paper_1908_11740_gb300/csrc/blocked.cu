@@ -17,6 +17,7 @@
 // The pairs reported are exactly those of single-level PBSM on the same
 // nx x ny grid: a pair is reported by the tile that holds its reference
 // point, and that tile belongs to exactly one block.
+#define SJ_FILE_CODE 1
 #include <cstddef>
 
 #include "sj_blocked.h"
@@ -77,7 +78,8 @@ __global__ void __launch_bounds__(kL1Threads) k_bcount(BArgs a) {
             const int bx0 = div_g(cx0, a), bx1 = div_g(cx1, a), by0 = div_g(cy0, a), by1 = div_g(cy1, a);
             unsigned *h = hist + side * a.nb;
             for (int by = by0; by <= by1; by++)
-                for (int bx = bx0; bx <= bx1; bx++) atomicAdd(h + by * a.bx + bx, 1u);
+                for (int bx = bx0; bx <= bx1; bx++)
+                    if (SJ_IN(a.st, by * a.bx + bx, a.nb)) atomicAdd(h + by * a.bx + bx, 1u);
 
         }
     }
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(kScanThreads) k_bscan_fill(BArgs a, const unsi
             if ((unsigned long long)vr[k] + vs[k] > (unsigned long long)a.fine_cap * G * G)
                 atomicOr(&a.st->need_direct, 1);
         }
-        if (vr[k] > 0 && vs[k] > 0) {
+        if (vr[k] > 0 && vs[k] > 0 && SJ_IN(a.st, idx, nb)) {
             a.items[idx] = (unsigned)b;
             a.imeta[idx] = make_uint4((unsigned)b, orr[k], vr[k], oss[k]);
             a.ins[idx] = vs[k];
@@ -347,6 +349,22 @@ __global__ void k_join_offsets(BArgs a, const unsigned long long *__restrict__ p
         const unsigned f = a.jfirst[j];
         joff[j] = f < n ? poff[f] : a.st->npairs;
     }
+}
+
+// Debug build: slot pos of block key kb (side * nbt + block) lies in that
+// block's run of the L1 array, [block start, block start + block total).
+__device__ __forceinline__ bool l1_slot_ok(const BArgs &a, unsigned kb, unsigned pos) {
+#if SJ_CHECK
+    if (!SJ_IN(a.st, kb, 2ull * (unsigned)a.nbt)) return false;
+    const unsigned side = kb >= (unsigned)a.nbt, b = kb - side * (unsigned)a.nbt;
+    const long long start = side ? a.bo_s[b] : a.bo_r[b];
+    return SJ_IN(a.st, (long long)pos - start, a.btot[kb]);
+#else
+    (void)a;
+    (void)kb;
+    (void)pos;
+    return true;
+#endif
 }
 
 // L1 write: the same slice per CTA as k_bcount; shared cursors start at
@@ -396,7 +414,7 @@ __global__ void __launch_bounds__(kL1Threads) k_bscatter(BArgs a) {
             for (int by = by0; by <= by1; by++)
                 for (int bx = bx0; bx <= bx1; bx++) {
                     const unsigned pos = atomicAdd(c + by * a.bx + bx, 1u);
-                    if (pos < cap)
+                    if (pos < cap && l1_slot_ok(a, (unsigned)(side * a.nbt + by * a.bx + bx), pos))
                         store_bent(dst + pos,
                                    make_uint4(__float_as_uint(v.x), __float_as_uint(v.y), __float_as_uint(v.z),
                                               __float_as_uint(v.w)),
@@ -484,7 +502,8 @@ __global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
             key[u] = ok[u] ? cb + (unsigned)(div_gj(cy0, d) * d.bx + div_gj(cx0, d)) : 0xffffffffu;
             peers[u] = __match_any_sync(0xffffffffu, key[u]);
             pos0[u] = 0;
-            if (ok[u] && (int)lane == __ffs(peers[u]) - 1) pos0[u] = atomicAdd(a.cur + key[u], (unsigned)__popc(peers[u]));
+            if (ok[u] && (int)lane == __ffs(peers[u]) - 1 && SJ_IN(a.st, key[u], 2ull * (unsigned)a.nbt))
+                pos0[u] = atomicAdd(a.cur + key[u], (unsigned)__popc(peers[u]));
         }
 #pragma unroll
         for (int u = 0; u < kScatterU; u++) {   // slots, stores (further blocks: one atomic each)
@@ -502,10 +521,10 @@ __global__ void __launch_bounds__(256) k_bscatter_shared(BArgs a) {
             const int bx0 = div_gj(cx0, d), bx1 = div_gj(cx1, d), by0 = div_gj(cy0, d), by1 = div_gj(cy1, d);
             for (int by = by0; by <= by1; by++)
                 for (int bx = bx0; bx <= bx1; bx++) {
-                    const unsigned pos =
-                        (by == by0 && bx == bx0) ? pos0[u] : atomicAdd(a.cur + cb + by * d.bx + bx, 1u);
-                    if (pos < cap) store_bent(dst + pos, head, tail);
-                    else atomicOr(&a.st->err, kErrEntCap);
+                    const unsigned kb = cb + by * d.bx + bx;
+                    const unsigned pos = (by == by0 && bx == bx0) ? pos0[u] : atomicAdd(a.cur + kb, 1u);
+                    if (pos >= cap) atomicOr(&a.st->err, kErrEntCap);
+                    else if (l1_slot_ok(a, kb, pos)) store_bent(dst + pos, head, tail);
                 }
         }
     }
@@ -548,6 +567,84 @@ __global__ void __launch_bounds__(256) k_bcount_global(BArgs a) {
         for (int by = by0; by <= by1; by++)
             for (int bx = bx0; bx <= bx1; bx++)
                 if (by != by0 || bx != bx0) atomicAdd(a.btot + cb + by * d.bx + bx, 1u);
+    }
+    if (bad) atomicOr(&a.st->err, kErrBadRect);
+}
+
+// L1 count of a batch with per-join shared histograms: every CTA takes a
+// contiguous slice of the batch's input, so it meets only the joins whose
+// input ranges overlap the slice; it counts each join's part of the slice in
+// a shared histogram of that join's blocks and then adds the non-zero counts
+// to the global totals (one atomic per touched block and CTA instead of one
+// per rectangle).  A join with more blocks than the histogram holds counts
+// with global atomics.
+constexpr int kLocalHist = 16384;   // counters: 2 per block (R, S)
+constexpr int kLocalThreads = 512;
+constexpr int kLocalU = 4;          // loads in flight per thread
+__global__ void __launch_bounds__(kLocalThreads) k_bcount_local(BArgs a) {
+    extern __shared__ long long s_dyn[];
+    long long *s_jin = s_dyn;                                         // nj + 1
+    unsigned *hist = reinterpret_cast<unsigned *>(s_dyn + a.nj + 1);   // kLocalHist
+    for (int j = threadIdx.x; j < a.nj; j += kLocalThreads) s_jin[j] = a.jd[j].in_off;
+    if (threadIdx.x == 0) s_jin[a.nj] = a.jd[a.nj - 1].in_off + a.jd[a.nj - 1].nR + a.jd[a.nj - 1].nS;
+    __syncthreads();
+    const long long n = s_jin[a.nj];
+    const long long q = (n + gridDim.x - 1) / gridDim.x;
+    const long long i0 = (long long)blockIdx.x * q, i1 = min(n, i0 + q);
+    int bad = 0;
+    const int j0 = i0 < i1 ? join_of(s_jin, a.nj, i0) : 0;
+    const int j1 = i0 < i1 ? join_of(s_jin, a.nj, i1 - 1) : -1;
+    for (int j = j0; j <= j1; j++) {   // block-uniform
+        const long long lo = max(i0, s_jin[j]), hi = min(i1, s_jin[j + 1]);
+        if (lo >= hi) continue;
+        const JoinDesc &d = a.jd[j];
+        const long long jin = s_jin[j], nRj = d.nR;
+        const float4 *Rj = d.R, *Sj = d.S;
+        const GridDev g = d.g;
+        const int jbx = d.bx, nbj = d.bx * d.by;
+        const bool local = 2 * nbj <= kLocalHist;
+        if (local) {
+            for (int k = threadIdx.x; k < 2 * nbj; k += kLocalThreads) hist[k] = 0;
+            __syncthreads();
+        }
+        for (long long base = lo + threadIdx.x; base < hi; base += (long long)kLocalU * kLocalThreads) {
+            float4 m[kLocalU];
+#pragma unroll
+            for (int u = 0; u < kLocalU; u++) {
+                const long long i = base + (long long)u * kLocalThreads;
+                if (i < hi) m[u] = ld_stream(i - jin < nRj ? Rj + (i - jin) : Sj + (i - jin - nRj));
+            }
+#pragma unroll
+            for (int u = 0; u < kLocalU; u++) {
+                const long long i = base + (long long)u * kLocalThreads;
+                if (i >= hi) break;
+                if (!rect_ok(m[u])) {
+                    bad = 1;
+                    continue;
+                }
+                const int side = i - jin >= nRj;
+                const int bx0 = div_gj(cell_of(m[u].x, g.x0, g.gx, g.nx), d);
+                const int bx1 = div_gj(cell_of(m[u].z, g.x0, g.gx, g.nx), d);
+                const int by0 = div_gj(cell_of(m[u].y, g.y0, g.gy, g.ny), d);
+                const int by1 = div_gj(cell_of(m[u].w, g.y0, g.gy, g.ny), d);
+                for (int by = by0; by <= by1; by++)
+                    for (int bx = bx0; bx <= bx1; bx++) {
+                        const int b = by * jbx + bx;
+                        if (!SJ_IN(a.st, b, nbj)) continue;
+                        if (local) atomicAdd(hist + side * nbj + b, 1u);
+                        else atomicAdd(a.btot + (unsigned)side * (unsigned)a.nbt + (unsigned)d.boff + (unsigned)b, 1u);
+                    }
+            }
+        }
+        if (local) {
+            __syncthreads();
+            for (int k = threadIdx.x; k < 2 * nbj; k += kLocalThreads) {
+                const unsigned c = hist[k];
+                const int side = k >= nbj;
+                if (c) atomicAdd(a.btot + (unsigned)side * (unsigned)a.nbt + (unsigned)d.boff + (unsigned)(k - side * nbj), c);
+            }
+            __syncthreads();   // the next join clears the histogram
+        }
     }
     if (bad) atomicOr(&a.st->err, kErrBadRect);
 }
@@ -611,6 +708,7 @@ struct BlockCtx {
     int gbda;              // grouping-based duplicate avoidance instead of the test of Eq. 1
     unsigned r0, nr1, s0, ns1;
     const BEnt *er, *es;   // the block's R and S entries (shared-memory copy or global)
+    Stats *st;             // error word of the bounds checks (debug build)
 };
 
 // Grouping-based duplicate avoidance (GBDA, the alternative to Eq. 1 that
@@ -637,7 +735,8 @@ constexpr unsigned kTileMask = 0x3FFFu;
 // the test then run along y unchanged, and the intersection test is
 // symmetric in the two axes, so the pairs are the same.
 __device__ __forceinline__ void place_entry(BJSmem &sm, const BlockCtx &bc, int side, const uint4 &hd,
-                                            const uint4 &t, int ta, int tb, int row_a, int row_b, int row) {
+                                            const uint4 &t, int ta, int tb, int row_a, int row_b, int row,
+                                            int nRb, int nb) {
     const int cx0 = t.y & 0xffff, cx1 = t.y >> 16, cy0 = t.z & 0xffff, cy1 = t.z >> 16;
     const int ly0 = max(cy0 - bc.cyb, row_a), ly1 = min(cy1 - bc.cyb, row_b);
     if (ly0 > ly1 || (row >= 0 && ly0 != row)) return;
@@ -651,6 +750,8 @@ __device__ __forceinline__ void place_entry(BJSmem &sm, const BlockCtx &bc, int 
             if (lt < ta || lt >= tb) continue;
             const int j = lt - ta;
             const unsigned pos = atomicAdd(&sm.off[side][j], 1u);
+            // the band's R entries are [0, nRb), its S entries [nRb, nb)
+            if (!SJ_IN(bc.st, (int)pos - (side ? nRb : 0), side ? nb - nRb : nRb)) continue;
             const unsigned flags = (lx + bc.cxb == cx0 ? kFlagCol : 0u) | (ly + bc.cyb == cy0 ? kFlagRow : 0u);
             const bool swap = bc.axis && ((bc.axis[lt >> 5] >> (lt & 31)) & 1u);
             const float4 mb = swap ? my : mx;
@@ -744,6 +845,7 @@ __device__ __forceinline__ void band_fill(BJSmem &sm, const BlockCtx &bc, int ta
                     }
                     row[u] = lo;
                     e[u] = (int)rl->pool[rl->off[lo] + (i - rl->pre[lo])];
+                    if (!SJ_IN(bc.st, e[u], bc.nr1 + bc.ns1)) e[u] = -1;
                 }
             }
 #pragma unroll
@@ -755,7 +857,9 @@ __device__ __forceinline__ void band_fill(BJSmem &sm, const BlockCtx &bc, int ta
                 }
 #pragma unroll
             for (int u = 0; u < kStageU; u++)
-                if (e[u] >= 0) place_entry(sm, bc, e[u] >= (int)bc.nr1, hd[u], t[u], ta, tb, row_a, row_b, row[u]);
+                if (e[u] >= 0)
+                    place_entry(sm, bc, e[u] >= (int)bc.nr1, hd[u], t[u], ta, tb, row_a, row_b, row[u], nRb,
+                                nRb + nSb);
         }
     } else {
         const int n1 = (int)(bc.nr1 + bc.ns1);
@@ -771,7 +875,8 @@ __device__ __forceinline__ void band_fill(BJSmem &sm, const BlockCtx &bc, int ta
 #pragma unroll
             for (int u = 0; u < kStageU; u++)
                 if (eb + u * NT < n1)
-                    place_entry(sm, bc, eb + u * NT >= (int)bc.nr1, hd[u], t[u], ta, tb, row_a, row_b, -1);
+                    place_entry(sm, bc, eb + u * NT >= (int)bc.nr1, hd[u], t[u], ta, tb, row_a, row_b, -1, nRb,
+                                nRb + nSb);
         }
     }
     __syncthreads();
@@ -792,6 +897,7 @@ __device__ __forceinline__ void band_fill(BJSmem &sm, const BlockCtx &bc, int ta
             const int j = (int)(tw & kTileMask);
             const int s0 = j ? (int)sm.off[side][j - 1] : (side ? nRb : 0);
             const int s1 = (int)sm.off[side][j];
+            if (!SJ_IN(bc.st, s1 - 1, nb) || !SJ_IN(bc.st, pidx - s0, s1 - s0)) continue;
             const unsigned k0 = sm.key[pidx];
             int r = 0;
             if (bc.gbda) {   // order by (class rank, x_l)
@@ -833,7 +939,7 @@ __device__ __forceinline__ void stage_band(BJSmem &sm, const BlockCtx &bc, int t
 // Candidate range of pivot p (any position) in the other side of its tile:
 // ranks k..kend-1 of that segment's x_l order (entry sm.key[k]).
 __device__ __forceinline__ void band_pivot(const BJSmem &sm, int nRb, int p, float4 &pv, unsigned &pid, int &k,
-                                           int &kend, bool &isR) {
+                                           int &kend, bool &isR, Stats *st, int nb) {
     isR = p < nRb;
     const int j = (int)(sm.tile[p] & kTileMask);
     pv = sm.mbr[p];
@@ -841,6 +947,7 @@ __device__ __forceinline__ void band_pivot(const BJSmem &sm, int nRb, int p, flo
     const int o = isR ? 1 : 0;
     int lo = j ? (int)sm.off[o][j - 1] : (o ? nRb : 0);
     int hi = (int)sm.off[o][j];
+    if (!SJ_IN(st, hi - lo, (o ? nb : nRb) - lo + 1) || !SJ_IN(st, lo, nb + 1)) hi = lo;   // empty on failure
     kend = hi;
     // first x_l > pivot.x_l (R pivot) or >= pivot.x_l (S pivot), in x_l order
     while (lo < hi) {
@@ -864,10 +971,10 @@ __device__ __forceinline__ unsigned band_count(const BJSmem &sm, const BlockCtx 
         unsigned pid;
         int k, kend;
         bool isR;
-        band_pivot(sm, nRb, p, pv, pid, k, kend, isR);
+        band_pivot(sm, nRb, p, pv, pid, k, kend, isR, bc.st, nb);
         unsigned c = 0;
         for (; k < kend; k++) {
-            const unsigned q = sm.key[k];
+            const unsigned q = SJ_AT(bc.st, sm.key[k], nb);
             const float4 o = sm.mbr[q];
             if (o.x > pv.z) break;
             if (o.y <= pv.w && pv.y <= o.w && reported_here(pid, sm.id[q])) c++;
@@ -884,7 +991,7 @@ __device__ __forceinline__ unsigned band_count(const BJSmem &sm, const BlockCtx 
 
 // Write the pairs of the staged band at out[base + cursor ...].
 __device__ __forceinline__ void band_write(const BJSmem &sm, int nRb, int nSb, int2 *out, unsigned long long base,
-                                           unsigned *s_cursor) {
+                                           unsigned *s_cursor, Stats *st, unsigned long long cap) {
     const int nb = nRb + nSb;
     if (nRb == 0 || nSb == 0) return;
     const unsigned lane = threadIdx.x & 31;
@@ -895,14 +1002,14 @@ __device__ __forceinline__ void band_write(const BJSmem &sm, int nRb, int nSb, i
         unsigned pid = 0;
         int k = 0, kend = 0;
         bool isR = true;
-        if (active) band_pivot(sm, nRb, p, pv, pid, k, kend, isR);
+        if (active) band_pivot(sm, nRb, p, pv, pid, k, kend, isR, st, nb);
         bool go = active;
         for (;;) {
             float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
             unsigned q = 0;
             bool cand = false;
             if (go && k < kend) {
-                q = sm.key[k];
+                q = SJ_AT(st, sm.key[k], nb);
                 o = sm.mbr[q];
                 cand = o.x <= pv.z;
             }
@@ -927,7 +1034,8 @@ __device__ __forceinline__ void band_write(const BJSmem &sm, int nRb, int nSb, i
                 unsigned pos = 0;
                 if ((int)lane == leader) pos = atomicAdd(s_cursor, (unsigned)__popc(hm));
                 pos = __shfl_sync(kFullMask, pos, leader);
-                if (hit) out[base + pos + __popc(hm & lanemask_lt_b())] = pr;
+                const unsigned long long at = base + pos + __popc(hm & lanemask_lt_b());
+                if (hit && SJ_IN(st, at, cap)) out[at] = pr;
             }
         }
     }
@@ -937,7 +1045,7 @@ __device__ __forceinline__ void band_write(const BJSmem &sm, int nRb, int nSb, i
 // every hit takes the next slot of *s_pc (warp-aggregated); slots beyond the
 // buffer go to the CTA's spill area (if any), slots beyond both are only
 // counted.
-__device__ __forceinline__ void band_collect(BJSmem &sm, int nRb, int nSb, unsigned *s_pc, int2 *spill) {
+__device__ __forceinline__ void band_collect(BJSmem &sm, int nRb, int nSb, unsigned *s_pc, int2 *spill, Stats *st) {
     const int nb = nRb + nSb;
     if (nRb == 0 || nSb == 0) return;
     for (int p = threadIdx.x; p < nb; p += kBJThreads) {
@@ -945,9 +1053,9 @@ __device__ __forceinline__ void band_collect(BJSmem &sm, int nRb, int nSb, unsig
         unsigned pid;
         int k, kend;
         bool isR;
-        band_pivot(sm, nRb, p, pv, pid, k, kend, isR);
+        band_pivot(sm, nRb, p, pv, pid, k, kend, isR, st, nb);
         for (; k < kend; k++) {
-            const unsigned q = sm.key[k];
+            const unsigned q = SJ_AT(st, sm.key[k], nb);
             const float4 o = sm.mbr[q];
             if (o.x > pv.z) break;
             if (o.y <= pv.w && pv.y <= o.w) {
@@ -978,7 +1086,7 @@ __device__ __forceinline__ void band_collect(BJSmem &sm, int nRb, int nSb, unsig
 template <int OUT>
 __device__ __forceinline__ unsigned gbda_sweep(BJSmem &sm, const BlockCtx &bc, int ta, int nRb, int nSb,
                                                unsigned *ctr, int2 *spill, int2 *out, unsigned long long base,
-                                               unsigned *tile_pairs, int nx) {
+                                               unsigned *tile_pairs, int nx, unsigned long long cap = ~0ull) {
     unsigned my = 0;
     const int nb = nRb + nSb;
     if (nRb == 0 || nSb == 0) return 0;
@@ -992,6 +1100,7 @@ __device__ __forceinline__ unsigned gbda_sweep(BJSmem &sm, const BlockCtx &bc, i
         const int o = isR ? 1 : 0;
         const int s0 = j ? (int)sm.off[o][j - 1] : (o ? nRb : 0);
         const int s1 = (int)sm.off[o][j];
+        if (!SJ_IN(bc.st, s1 - s0, (o ? nb : nRb) - s0 + 1)) continue;
         unsigned c = 0;
         for (unsigned cl = gbda_lo(f); cl <= gbda_hi(f); cl++) {
             // first sorted position of class > cl, or of class cl with x_l
@@ -1007,7 +1116,7 @@ __device__ __forceinline__ unsigned gbda_sweep(BJSmem &sm, const BlockCtx &bc, i
                 else lo = mid + 1;
             }
             for (int k = lo; k < s1; k++) {
-                const unsigned q = sm.key[k];
+                const unsigned q = SJ_AT(bc.st, sm.key[k], nb);
                 if (((unsigned)sm.tile[q] >> 14) != cl) break;
                 const float4 ov = sm.mbr[q];
                 if (ov.x > pv.z) break;
@@ -1026,7 +1135,7 @@ __device__ __forceinline__ unsigned gbda_sweep(BJSmem &sm, const BlockCtx &bc, i
                         if (OUT == 1) {
                             if (pos < (unsigned)kPairBuf) sm.pbuf[pos] = pr;
                             else if (spill && pos < (unsigned)(kPairBuf + kPairSpill)) spill[pos - kPairBuf] = pr;
-                        } else {
+                        } else if (SJ_IN(bc.st, base + pos, cap)) {
                             out[base + pos] = pr;
                         }
                     }
@@ -1084,7 +1193,10 @@ __device__ void build_row_lists(BJSmem &sm, const BlockCtx &bc, RowLists &rl, un
         const int ly0 = max((int)(t.z & 0xffff) - bc.cyb, 0), ly1 = min((int)(t.z >> 16) - bc.cyb, bc.gh - 1);
         const int lx0 = max((int)(t.y & 0xffff) - bc.cxb, 0), lx1 = min((int)(t.y >> 16) - bc.cxb, bc.gw - 1);
         if (lx0 > lx1) continue;   // counted in no tile of the block (never for a written entry)
-        for (int y = ly0; y <= ly1; y++) rl.pool[rl.off[y] + atomicAdd(&rl.cur[y], 1u)] = (unsigned)e;
+        for (int y = ly0; y <= ly1; y++) {
+            const unsigned k = atomicAdd(&rl.cur[y], 1u);   // within the row's room
+            if (SJ_IN(bc.st, k, rl.off[y + 1] - rl.off[y])) rl.pool[rl.off[y] + k] = (unsigned)e;
+        }
     }
     __syncthreads();
     if (warp == 0) {
@@ -1282,6 +1394,7 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
         bc.ns1 = m[5];
         bc.er = a.bent_r + bc.r0;
         bc.es = a.bent_s + bc.s0;
+        bc.st = a.st;
 
         // step 1: entries per tile of the block (and, for the adaptive sweep
         // axis, the Eq. 2 histograms of every tile: k = 8 buckets per axis)
@@ -1323,6 +1436,7 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                 for (int ly = ly0; ly <= ly1; ly++)
                     for (int lx = lx0; lx <= lx1; lx++) {
                         const int lt = ly * bc.gw + lx;
+                        if (!SJ_IN(a.st, lt, bc.ntl)) continue;
                         atomicAdd(&sm.cnt[side][lt], 1u);
                         if (ADAPT) {
                             // buckets of the projections inside this tile
@@ -1415,8 +1529,8 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
             };
             // pairs of the staged band at out[base + s_cursor ...]
             auto write = [&](int nRb, int nSb, unsigned long long base) {
-                if (GBDA) gbda_sweep<2>(sm, bc, 0, nRb, nSb, &s_cursor, nullptr, o.out, base, nullptr, 0);
-                else band_write(sm, nRb, nSb, o.out, base, &s_cursor);
+                if (GBDA) gbda_sweep<2>(sm, bc, 0, nRb, nSb, &s_cursor, nullptr, o.out, base, nullptr, 0, o.cap);
+                else band_write(sm, nRb, nSb, o.out, base, &s_cursor, a.st, o.cap);
             };
             if (MODE == MODE_WRITE) {
                 const unsigned long long base = o.off_in[it];
@@ -1434,7 +1548,7 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                     if (MODE == MODE_RESERVE) {
                         int2 *sp = o.spill ? o.spill + (size_t)blockIdx.x * kPairSpill : nullptr;
                         if (GBDA) gbda_sweep<1>(sm, bc, 0, nRb, nSb, &s_pc, sp, nullptr, 0, nullptr, 0);
-                        else band_collect(sm, nRb, nSb, &s_pc, sp);
+                        else band_collect(sm, nRb, nSb, &s_pc, sp, a.st);
                         __syncthreads();
                     } else {
                         unsigned *tp = MODE == MODE_TILES ? o.tile_pairs : nullptr;
@@ -1494,6 +1608,9 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
 // each side add their bucket ranges to every block they overlap.
 template <int PTS>
 __global__ void __launch_bounds__(256) k_bfeat_sample(BArgs a) {
+    // the one-pass join leaves for the single-level path when the block scan
+    // found a tile beyond shared memory: its sample would go unused
+    if (a.stop_direct && block_skip_blocked(a.st)) return;
     const long long mr = (a.nR + kPhi - 1) / kPhi, ms = (a.nS + kPhi - 1) / kPhi;
     for (long long k = blockIdx.x * 256ll + threadIdx.x; k < mr + ms; k += 256ll * gridDim.x) {
         const int side = k >= mr;
@@ -1628,6 +1745,9 @@ cudaError_t blocked_setup() {
     if ((e = cudaFuncSetAttribute(k_bjoin<MODE_COUNT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
     if ((e = cudaFuncSetAttribute(k_bjoin<MODE_WRITE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
     if ((e = cudaFuncSetAttribute(k_bjoin<MODE_RESERVE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))) return e;
+    if ((e = cudaFuncSetAttribute(k_bcount_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(8 * (kMaxJoins + 1) + 4 * kLocalHist))))
+        return e;
     const int l1 = 8 * kMaxBlocks;
     if ((e = cudaFuncSetAttribute(k_bcount<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
     if ((e = cudaFuncSetAttribute(k_bcount<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, l1))) return e;
@@ -1671,6 +1791,11 @@ cudaError_t launch_bscan(const BArgs &a, int nc, cudaStream_t s) {
 
 cudaError_t launch_bcount_global(const BArgs &a, int grid, cudaStream_t s) {
     k_bcount_global<<<grid, 256, 8ull * (a.nj + 1), s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bcount_local(const BArgs &a, int grid, cudaStream_t s) {
+    k_bcount_local<<<grid, kLocalThreads, 8ull * (a.nj + 1) + 4ull * kLocalHist, s>>>(a);
     return cudaGetLastError();
 }
 

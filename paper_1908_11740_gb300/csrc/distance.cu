@@ -25,6 +25,7 @@
 //  5. k_dist_write: every chunk writes its accepted pairs at its offset, in
 //     candidate order (prefix of the ballot words), into an output of the
 //     exact size.
+#define SJ_FILE_CODE 5
 #include "sj_internal.h"
 
 namespace sj {
@@ -106,7 +107,8 @@ __global__ void __launch_bounds__(kDistThreads) k_dist_mark(const int2 *__restri
 __global__ void __launch_bounds__(kDistThreads) k_dist_write(const int2 *__restrict__ cand, long long C,
                                                              const unsigned *__restrict__ mask,
                                                              const unsigned long long *__restrict__ off,
-                                                             int2 *__restrict__ out) {
+                                                             int2 *__restrict__ out, Stats *st,
+                                                             unsigned long long cap) {
     __shared__ unsigned s_pre[kDistWords];
     const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned *m = mask + (size_t)blockIdx.x * kDistWords;
@@ -131,7 +133,8 @@ __global__ void __launch_bounds__(kDistThreads) k_dist_write(const int2 *__restr
         const int w = u * (kDistThreads / 32) + warp;
         const unsigned b = m[w];
         const long long k = base + u * kDistThreads;
-        if (((b >> lane) & 1u) && k < C) out[o + s_pre[w] + __popc(b & lt)] = cand[k];
+        const unsigned long long d = o + s_pre[w] + __popc(b & lt);
+        if (((b >> lane) & 1u) && k < C && SJ_IN(st, d, cap)) out[d] = cand[k];
     }
 }
 
@@ -258,7 +261,8 @@ static int dist_core(sj_ctx *ctx, const sj_point *d_P, int64_t nP, const sj_poin
     {
         PhaseScope ph(ctx, PH_REFINE, 1);
         k_dist_write<<<(unsigned)nch, kDistThreads, 0, ctx->stream>>>(
-            cand, C, (const unsigned *)w.dmask.p, (const unsigned long long *)w.doff.p, os.got);
+            cand, C, (const unsigned *)w.dmask.p, (const unsigned long long *)w.doff.p, os.got, (Stats *)w.stats.p,
+            P);
         if ((e = cudaGetLastError())) {
             out_abandon(ctx, os);
             return cuda_fail(ctx, e, "refinement write kernel");
@@ -268,7 +272,8 @@ static int dist_core(sj_ctx *ctx, const sj_point *d_P, int64_t nP, const sj_poin
         out_abandon(ctx, os);
         return st;
     }
-    return SJ_OK;
+    if ((st = check_tail(ctx, w))) out_abandon(ctx, os);
+    return st;
 }
 
 extern "C" int sj_distance_join(sj_ctx *ctx, const sj_point *d_P, int64_t nP, const sj_point *d_Q, int64_t nQ,

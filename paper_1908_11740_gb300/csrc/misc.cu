@@ -60,6 +60,7 @@ __global__ void k_reset_counters(Stats *st) {
         st->nfail = 0;
         st->nfail_large = 0;
         st->err = 0;
+        st->check = 0;
     }
     if (threadIdx.x < 8) st->work[threadIdx.x] = 0;
 }

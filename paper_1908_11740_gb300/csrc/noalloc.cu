@@ -13,6 +13,7 @@
 // kNaMaxN rectangles per side, kNaMaxTiles tiles, and kNaMaxEnt replicated
 // entries per side (detected on the device; then nothing is written and
 // SJ_EINVAL is returned).
+#define SJ_FILE_CODE 9
 #include <mutex>
 
 #include "sj_internal.h"
@@ -170,5 +171,13 @@ extern "C" int sj_join_noalloc(const sj_rect *d_R, int64_t nR, const sj_rect *d_
     *npairs = (int64_t)stats.npairs;
     if ((unsigned long long)cap < stats.npairs) return SJ_EOVERFLOW;
     if (stats.npairs == 0) return SJ_OK;
+#if SJ_CHECK
+    // debug build: bounds checks that failed in the write pass
+    if ((st = sj::enqueue_sweep(&c, w, sj::MODE_WRITE, (int2 *)d_out, stats.npairs, nullptr, nullptr, 2))) return st;
+    if ((e = cudaMemcpyAsync(&stats, w.stats.p, sizeof stats, cudaMemcpyDeviceToHost, c.stream))) return SJ_ECUDA;
+    if ((e = cudaStreamSynchronize(c.stream))) return SJ_ECUDA;
+    return (stats.err & sj::kErrCheck) ? SJ_EINTERNAL : SJ_OK;
+#else
     return sj::enqueue_sweep(&c, w, sj::MODE_WRITE, (int2 *)d_out, stats.npairs, nullptr, nullptr, 2);
+#endif
 }

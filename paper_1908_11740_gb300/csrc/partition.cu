@@ -3,6 +3,7 @@
 // segments, then write every rectangle into every tile it overlaps
 // (multi-assignment, Sec. 2.2).  The scan also cuts the tile sequence into
 // sweep chunks and lists the tiles too heavy for one chunk.
+#define SJ_FILE_CODE 3
 #include "sj_common.cuh"
 #include "sj_kernels.h"
 
@@ -279,6 +280,8 @@ __global__ void __launch_bounds__(256) k_scatter(const float4 *__restrict__ R, l
                     const unsigned k = (cy == cy0 && cx == cx0) ? k0 : atomicSub(cnt + 2 * t + side, 1u) - 1u;
                     const unsigned o = side ? off[t].y : off[t].x;
                     const unsigned long long pos = (unsigned long long)o + k;
+                    // slot k counts down from the tile's count: within its segment
+                    if (!SJ_IN(st, k, (side ? off[t + 1].y : off[t + 1].x) - o)) continue;
                     if (pos < cap) {
                         ent[pos] = v;
                         idw[pos] = id | (cx == cx0 ? kFlagCol : 0u) | (cy == cy0 ? kFlagRow : 0u);

@@ -80,6 +80,7 @@ struct BArgs {
     int adaptive;               // single join: sweep axis per tile from Eq. 2 histograms (Sec. 3.3)
     int gbda;                   // single join: grouping-based duplicate avoidance instead of Eq. 1
     int fine_cap;               // entries one tile may hold for the consumer of the partition
+    int stop_direct;            // one-pass sizing: skip the feature sample once a tile exceeds shared memory
     Stats *st;
 };
 
@@ -117,6 +118,7 @@ int l1_blocks_per_sm(int nb);
 size_t bjoin_smem_bytes();
 cudaError_t launch_bcount(const BArgs &a, int nc, cudaStream_t s);
 cudaError_t launch_bcount_global(const BArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_bcount_local(const BArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_extent_stats(const BArgs &a, double *out, int grid, cudaStream_t s);
 cudaError_t launch_join_offsets(const BArgs &a, const unsigned long long *poff, unsigned long long *joff,
                                 cudaStream_t s);

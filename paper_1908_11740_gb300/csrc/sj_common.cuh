@@ -41,10 +41,11 @@ constexpr int kErrChunkCap = 8;      // chunk table overflow (internal)
 constexpr int kErrLargeCap = 16;     // large-tile table overflow (internal)
 constexpr int kErrOutCap = 32;       // one-pass output capacity exceeded
 constexpr int kErrTimeout = 64;      // a bounded device-side wait gave up
+constexpr int kErrCheck = 128;       // debug build: an index failed its bounds check
 
 // Errors after which the partition is incomplete: every kernel that reads the
 // partition returns at once (the host grows the workspace and starts over).
-constexpr int kErrFatal = kErrEntCap | kErrTooMany | kErrChunkCap | kErrLargeCap | kErrTimeout;
+constexpr int kErrFatal = kErrEntCap | kErrTooMany | kErrChunkCap | kErrLargeCap | kErrTimeout | kErrCheck;
 
 struct GridDev {
     int nx, ny;
@@ -67,11 +68,43 @@ struct Stats {
     unsigned long long lpool[4];        // blocked path: row-list pool cursor per work slot
     int err;
     int need_direct;                    // blocked path: a tile exceeds shared memory
-    int pad;
+    unsigned int check;                 // debug build: first failed bounds check (file << 16 | line)
     unsigned int nlch;                  // candidate chunks of the large-tile sweep
     unsigned int naxis_y;               // blocked path: work items swept along y (adaptive axis)
     unsigned long long apairs;          // large tiles appended in one pass (single-level one-pass)
 };
+
+// ---- debug build (-DSJ_CHECK=1) --------------------------------------------
+// Bounds checks of the data-dependent indexes: offsets taken from atomics,
+// scans, counts and searches.  A failed check records its site (the file
+// code SJ_FILE_CODE of the translation unit << 16 | the source line) in
+// Stats::check, the first one winning, sets kErrCheck (fatal: the remaining
+// kernels of the call return at once) and skips the access; a checked read
+// takes element 0 instead.  The call then fails with SJ_EINTERNAL and names
+// the site.  In the normal build the checks compile to nothing.
+#ifndef SJ_CHECK
+#define SJ_CHECK 0
+#endif
+#ifndef SJ_FILE_CODE
+#define SJ_FILE_CODE 0
+#endif
+__device__ __forceinline__ bool check_index(Stats *st, unsigned long long i, unsigned long long n, unsigned site) {
+    if (i < n) return true;
+    atomicCAS(&st->check, 0u, site);
+    atomicOr(&st->err, kErrCheck);
+    return false;
+}
+#if SJ_CHECK
+// true when 0 <= i < n (i of any integer type; a negative i fails)
+#define SJ_IN(st, i, n) \
+    ::sj::check_index((st), (unsigned long long)(long long)(i), (unsigned long long)(n), \
+                      ((unsigned)SJ_FILE_CODE << 16) | (unsigned)__LINE__)
+// i when 0 <= i < n, else 0 (for reads)
+#define SJ_AT(st, i, n) (SJ_IN(st, i, n) ? (i) : 0)
+#else
+#define SJ_IN(st, i, n) true
+#define SJ_AT(st, i, n) (i)
+#endif
 
 // ---- the cell function (tile index of a coordinate) ------------------------
 // clamp(floor((v - g0) * ginv), 0, n - 1) with both operations rounded to

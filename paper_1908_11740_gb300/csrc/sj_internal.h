@@ -95,6 +95,8 @@ int enqueue_partition(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, 
 int enqueue_sweep(sj_ctx *ctx, Workspace &w, int mode, int2 *out, unsigned long long cap,
                   const unsigned long long *off_in, unsigned *tile_pairs, int slot_base);
 int read_stats(sj_ctx *ctx, Workspace &w, Stats *out);
+int check_failed(sj_ctx *ctx, unsigned site);
+int check_tail(sj_ctx *ctx, Workspace &w);
 int partition_and_count(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, const float4 *S,
                         long long nS, const GridDev &g, Stats *stats, bool count_pass);
 struct OutSpec;
@@ -187,6 +189,7 @@ struct sj_ctx {
     int use_blocked = 1;      // the two-level path when the grid allows it
     int use_stripes = 1;      // the stripe kernel for 1D grids
     int batch_graphs = 1;     // batched joins replay captured CUDA graphs (else direct launches)
+    int batch_count_local = 1;   // batch L1 count with per-join shared histograms (else global atomics)
     int shared_cursors = 1;   // L1 write through shared per-block cursors
     int block_target = 1536;  // L1 entries a block should hold (two-level plan)
     int lpt = 1;              // one-pass join: blocks heaviest predicted cost first (else item order)

@@ -15,6 +15,7 @@
 //      and the warp walks its pairs 32 at a time in order, placing each pair
 //      at its digit's next slot (rank among equal digits by lane), so the
 //      pass is stable.
+#define SJ_FILE_CODE 7
 #include "sj_internal.h"
 
 namespace sj {
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kPsThreads) k_ps_scan_fill(unsigned *__restric
 
 __global__ void __launch_bounds__(kPsThreads) k_ps_scatter(const int2 *__restrict__ in, int2 *__restrict__ out,
                                                            unsigned n, int pass, const unsigned *__restrict__ off,
-                                                           unsigned nT) {
+                                                           unsigned nT, Stats *st) {
     __shared__ unsigned wc[kPsWarps][256];
     for (int k = threadIdx.x; k < kPsWarps * 256; k += kPsThreads) (&wc[0][0])[k] = 0;
     __syncthreads();
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(kPsThreads) k_ps_scatter(const int2 *__restric
         if (ok) pos = c[d] + __popc(peers & lt);
         __syncwarp();
         if (ok) {
-            out[pos] = p;
+            if (SJ_IN(st, pos, n)) out[pos] = p;
             if ((int)lane == __ffs(peers) - 1) c[d] += __popc(peers);
         }
         __syncwarp();
@@ -196,7 +197,7 @@ int sort_pairs(sj_ctx *ctx, Workspace &w, int2 *pairs, unsigned long long n) {
         k_ps_scan_part<<<nc, kPsThreads, 0, s>>>(hist, m, part);
         k_ps_scan_top<<<1, 1024, 0, s>>>(part, nc);
         k_ps_scan_fill<<<nc, kPsThreads, 0, s>>>(hist, m, part);
-        k_ps_scatter<<<nT, kPsThreads, 0, s>>>(a, b, (unsigned)n, pass, hist, nT);
+        k_ps_scatter<<<nT, kPsThreads, 0, s>>>(a, b, (unsigned)n, pass, hist, nT, (Stats *)w.stats.p);
         int2 *t = a;
         a = b;
         b = t;

@@ -11,22 +11,24 @@
 //     S entries are then contiguous runs of 32-byte L1 entries.
 //  2. k_stripe_join: persistent, one CTA of 1024 threads per stripe (taken
 //     from a counter).  The stripe's keys -- the order-preserving image of
-//     the lower coordinate along the stripe -- are sorted in shared memory,
-//     R and S separately, by an LSD radix sort (4 passes of 8-bit digits,
-//     per-warp digit counts, a digit-major exclusive scan, and a stable
-//     scatter in which every warp walks its items 32 at a time in order,
-//     ranking equal digits by lane).  Then every entry of the stripe is a
-//     pivot of Algorithm 1's forward scan along the stripe: an R pivot
-//     scans the S entries whose lower coordinate lies in (lo, hi] of its
-//     own, an S pivot the R entries in [lo, hi] (the tie rule of Algorithm
-//     1), starting at a binary search in the sorted keys.  Such a candidate
-//     intersects along the stripe by construction, so only the other axis
-//     is tested, and the pair is reported when the stripe is the one that
-//     holds its reference point.  Candidates are read from their L1 entries.
+//     the lower coordinate along the stripe -- of its S entries, then its R
+//     entries, are sorted together in shared memory by a stable LSD radix
+//     sort (4 passes of 8-bit digits, per-warp digit counts, a digit-major
+//     exclusive scan, and a stable scatter in which every warp walks its
+//     items 32 at a time in order, ranking equal digits by lane).  S before
+//     R on equal keys is Algorithm 1's tie rule, so the candidates of every
+//     entry follow it in the merged order: each entry is a pivot of the
+//     forward scan along the stripe, from its own sorted position, over the
+//     other side's entries whose lower coordinate is at most its upper one.
+//     Such a candidate intersects along the stripe by construction, so only
+//     the other axis is tested, and the pair is reported when the stripe is
+//     the one that holds its reference point.  Candidates are read from their
+//     L1 entries.
 //  3. Two passes: count (pairs per stripe), scan, exact allocation, write.
 //     The write pass sorts again (cheaper than storing the order).
 // A stripe with more entries than shared memory holds sends the join to the
 // general path.
+#define SJ_FILE_CODE 4
 #include <string.h>
 
 #include <algorithm>
@@ -41,10 +43,10 @@ constexpr int kStWarps = kStThreads / 32;
 constexpr int kStCap = 16384;   // R + S entries of one stripe joined in shared memory
 
 struct StSmem {
-    unsigned key[kStCap];            // sorted keys: R in [0, nr), S in [nr, n)
-    unsigned short val[kStCap];      // index of each key's entry within its side
+    unsigned key[kStCap];            // sorted keys of the stripe's S and R entries (merged)
+    unsigned short val[kStCap];      // merged index of each key's entry: S in [0, ns), R in [ns, n)
     unsigned tkey[kStCap];           // radix ping-pong
-    unsigned short tval[kStCap];
+    unsigned short tval[kStCap];     // radix ping-pong; then the sorted position of every entry
     unsigned hist[kStWarps * 256];   // per-warp digit counts, then running offsets
 };
 
@@ -183,55 +185,58 @@ __global__ void __launch_bounds__(kStThreads, 1) k_stripe_join(StArgs a, BJoinOu
             __syncthreads();
             continue;
         }
-        // keys of the lower coordinate along the stripe, R then S
+        // keys of the lower coordinate along the stripe, S first, then R: the
+        // stable sort then puts S before R on equal keys, which is Algorithm
+        // 1's tie rule (on r.x_l == s.x_l, s is the pivot), so every pivot's
+        // candidates follow it in the merged order
         for (int e = threadIdx.x; e < n; e += kStThreads) {
-            const bool isR = e < nr;
-            const float4 m = (isR ? er[e] : es[e - nr]).mbr;
+            const bool isS = e < ns;
+            const float4 m = (isS ? es[e] : er[e - ns]).mbr;
             sm.key[e] = xkey(a.vert ? m.y : m.x);
-            sm.val[e] = (unsigned short)(isR ? e : e - nr);
+            sm.val[e] = (unsigned short)e;
         }
         __syncthreads();
-        st_sort(sm.key, sm.val, sm.tkey, sm.tval, nr, sm.hist, s_w);
-        st_sort(sm.key + nr, sm.val + nr, sm.tkey, sm.tval, ns, sm.hist, s_w);
-        // every entry is a pivot of the forward scan along the stripe
+        st_sort(sm.key, sm.val, sm.tkey, sm.tval, n, sm.hist, s_w);
+        // position of every entry in the merged order (tval is free now)
+        for (int k = threadIdx.x; k < n; k += kStThreads)
+            if (SJ_IN(a.st, sm.val[k], n)) sm.tval[sm.val[k]] = (unsigned short)k;
+        __syncthreads();
+        // every entry is a pivot of the forward scan along the stripe: the
+        // other side's entries after it, while their lower coordinate is at
+        // most its upper one (for an R pivot those have a key above its own;
+        // for an S pivot, at least its own)
         unsigned my = 0;
         for (int e = threadIdx.x; e < n; e += kStThreads) {
-            const bool isR = e < nr;
-            const BEnt &me = isR ? er[e] : es[e - nr];
+            const bool isS = e < ns;
+            const BEnt &me = isS ? es[e] : er[e - ns];
             const float4 m = me.mbr;
             const unsigned pid = me.id;
             const int cx0 = (int)(me.cx & 0xffffu), cy0 = (int)(me.cy & 0xffffu);
-            const float lo = a.vert ? m.y : m.x, hi = a.vert ? m.w : m.z;
+            const float hi = a.vert ? m.w : m.z;
             const float olo = a.vert ? m.x : m.y, ohi = a.vert ? m.z : m.w;
-            const unsigned klo = xkey(lo), khi = xkey(hi);
-            int b0 = isR ? nr : 0, b1 = isR ? n : nr;
-            const int end = b1;
-            // first key > klo (R pivot) or >= klo (S pivot)
-            while (b0 < b1) {
-                const int mid = (b0 + b1) >> 1;
-                const unsigned km = sm.key[mid];
-                if (isR ? km > klo : km >= klo) b1 = mid;
-                else b0 = mid + 1;
-            }
-            for (int k = b0; k < end && sm.key[k] <= khi; k++) {
-                const BEnt &c = isR ? es[sm.val[k]] : er[sm.val[k]];
-                const float4 cm = c.mbr;
+            const unsigned khi = xkey(hi);
+            for (int k = (int)sm.tval[e] + 1; k < n && sm.key[k] <= khi; k++) {
+                const unsigned c = SJ_AT(a.st, sm.val[k], n);
+                const bool cS = c < (unsigned)ns;
+                if (cS == isS) continue;   // same side
+                const BEnt &ce = cS ? es[c] : er[c - ns];
+                const float4 cm = ce.mbr;
                 const float clo = a.vert ? cm.x : cm.y, chi = a.vert ? cm.z : cm.w;
                 if (!(clo <= ohi && olo <= chi)) continue;
                 // Eq. 1 in 1D: the pair's reference point lies in this stripe
-                const int ccx0 = (int)(c.cx & 0xffffu), ccy0 = (int)(c.cy & 0xffffu);
+                const int ccx0 = (int)(ce.cx & 0xffffu), ccy0 = (int)(ce.cy & 0xffffu);
                 if (max(cx0, ccx0) != col || max(cy0, ccy0) != row) continue;
                 if (MODE == MODE_COUNT) {
                     my++;
                 } else {
-                    const unsigned oid = c.id;
-                    const int2 pr = isR ? make_int2((int)pid, (int)oid) : make_int2((int)oid, (int)pid);
+                    const unsigned oid = ce.id;
+                    const int2 pr = isS ? make_int2((int)oid, (int)pid) : make_int2((int)pid, (int)oid);
                     const unsigned msk = __activemask();
                     const int leader = __ffs(msk) - 1;
                     unsigned pos = 0;
                     if ((int)(threadIdx.x & 31) == leader) pos = atomicAdd(&s_cnt, (unsigned)__popc(msk));
                     pos = __shfl_sync(msk, pos, leader) + (unsigned)__popc(msk & st_lanemask_lt());
-                    o.out[o.off_in[it] + pos] = pr;
+                    if (SJ_IN(a.st, o.off_in[it] + pos, o.cap)) o.out[o.off_in[it] + pos] = pr;
                 }
             }
         }
@@ -335,6 +340,7 @@ int sj::join_stripes(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, c
         if (P == 0) return SJ_OK;
         BJoinOut wo = bjoin_out(w, 1);
         wo.out = os.got;
+        wo.cap = P;
         {
             PhaseScope ph(ctx, PH_SWEEP_WRITE, 1);
             if ((e = launch_stripe_join(MODE_WRITE, a, vert, wo, ctx->num_sms, s))) {

@@ -11,6 +11,7 @@
 // therefore an independent pivot: it locates its start in the other side's
 // sorted segment by binary search and scans forward.  The set of examined
 // candidates and reported pairs is the same as Algorithm 1's.
+#define SJ_FILE_CODE 2
 #include "sj_common.cuh"
 #include "sj_kernels.h"
 
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_chunks(SweepArgs a) 
                     const unsigned kq = sm.key[q];
                     r += (kq < k0) | ((kq == k0) & (q < e));
                 }
+                if (!SJ_IN(a.st, r, s1 - s0) || !SJ_IN(a.st, s1 - 1, nc)) continue;
                 sm.mbr[s0 + r] = m[it];
                 sm.id[s0 + r] = idv[it];
             }
@@ -253,7 +255,8 @@ __global__ void __launch_bounds__(kSweepThreads, 3) k_sweep_chunks(SweepArgs a) 
                         unsigned pos = 0;
                         if ((int)lane == leader) pos = atomicAdd(&s_cursor, (unsigned)__popc(hm));
                         pos = __shfl_sync(kFull, pos, leader);
-                        if (hit) a.out[base + pos + __popc(hm & lanemask_lt())] = pr;
+                        const unsigned long long at = base + pos + __popc(hm & lanemask_lt());
+                        if (hit && SJ_IN(a.st, at, a.cap)) a.out[at] = pr;
                     }
                 }
             }
@@ -443,8 +446,10 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(LargeArgs a, in
                 unsigned before = s_run[dg];
                 for (unsigned ww = 0; ww < w; ww++) before += s_w[ww][dg];
                 const unsigned dst = s_dst[dg] + before + rank;
-                a.key_out[dst] = key;
-                a.val_out[dst] = val;
+                if (SJ_IN(a.st, dst, a.items_cap)) {
+                    a.key_out[dst] = key;
+                    a.val_out[dst] = val;
+                }
             }
             __syncthreads();
             {
@@ -613,7 +618,8 @@ __global__ void __launch_bounds__(256) k_sweep_large(LargeArgs a, SweepArgs o) {
                     unsigned pos = 0;
                     if ((int)lane == leader) pos = atomicAdd(&s_cursor, (unsigned)__popc(hm));
                     pos = __shfl_sync(kFull, pos, leader);
-                    if (hit) o.out[base + pos + __popc(hm & lanemask_lt())] = pr;
+                    const unsigned long long at = base + pos + __popc(hm & lanemask_lt());
+                if (hit && SJ_IN(o.st, at, o.cap)) o.out[at] = pr;
                 }
             }
         }
@@ -884,7 +890,7 @@ __global__ void __launch_bounds__(kCandThreads) k_large_cand(LargeArgs a, SweepA
                             unsigned pos = 0;
                             if (lane == (unsigned)(__ffs(hm) - 1)) pos = atomicAdd(&s_n, (unsigned)__popc(hm));
                             pos = __shfl_sync(kFull, pos, __ffs(hm) - 1) + __popc(hm & lanemask_lt());
-                            if (hit)
+                            if (hit && SJ_IN(o.st, pos, kCandChunk))
                                 s_pairs[pos] = isR ? make_int2((int)(pid[u] & kIdMask), (int)(oid[u] & kIdMask))
                                                    : make_int2((int)(oid[u] & kIdMask), (int)(pid[u] & kIdMask));
                         }
@@ -905,7 +911,8 @@ __global__ void __launch_bounds__(kCandThreads) k_large_cand(LargeArgs a, SweepA
                 }
                 __syncthreads();
                 const unsigned n = (MODE == MODE_APPEND && s_base + s_n > o.cap) ? 0u : s_n;
-                for (unsigned i = threadIdx.x; i < n; i += kCandThreads) o.out[s_base + i] = s_pairs[i];
+                for (unsigned i = threadIdx.x; i < n; i += kCandThreads)
+                    if (SJ_IN(o.st, s_base + i, o.cap)) o.out[s_base + i] = s_pairs[i];
             } else {
 #pragma unroll
                 for (int d = 16; d > 0; d >>= 1) my += __shfl_xor_sync(kFull, my, d);

@@ -40,6 +40,12 @@ def combine(parts) -> tuple[int, int, int]:
     return n, s, x
 
 
-def digest_device(pairs, chunk: int = 1 << 26) -> tuple[int, int, int]:
-    """Digest of a device tensor of pairs, copied to the host in chunks."""
-    return combine(digest(pairs[i:i + chunk].cpu().numpy()) for i in range(0, pairs.shape[0], chunk))
+def digest_device(pairs, chunk: int = 1 << 24, threads: int = 8) -> tuple[int, int, int]:
+    """Digest of a device tensor of pairs, copied to the host in chunks and
+    digested by a few threads (numpy releases the GIL in its loops)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    starts = range(0, pairs.shape[0], chunk)
+    with ThreadPoolExecutor(threads) as pool:
+        parts = list(pool.map(lambda i: digest(pairs[i:i + chunk].cpu().numpy()), starts))
+    return combine(parts)
