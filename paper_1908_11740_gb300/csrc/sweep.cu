@@ -358,6 +358,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(LargeArgs a, int p
     __shared__ unsigned h[256];
     const unsigned nvb = a.st->nvb, nseg = 2 * a.st->nlarge;
     const int shift = 8 * pass;
+    const unsigned lane = threadIdx.x & 31;
     for (unsigned vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
         h[threadIdx.x] = 0;
         __syncthreads();
@@ -365,10 +366,16 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(LargeArgs a, int p
         const unsigned q0 = (vb - a.seg_vb[sg]) * kRadixBlock;
         const unsigned n = a.seg_off[sg + 1] - a.seg_off[sg];
         const unsigned q1 = min(n, q0 + kRadixBlock);
-        for (unsigned q = q0 + threadIdx.x; q < q1; q += kRadixThreads) {
-            unsigned key, val;
-            radix_item(a, pass, sg, q, key, val);
-            atomicAdd(&h[(key >> shift) & 255u], 1u);
+        // lanes with equal digits add with one atomic (skewed tiles: long runs
+        // of equal high digits)
+        for (unsigned qb = q0; qb < q1; qb += kRadixThreads) {
+            const unsigned q = qb + threadIdx.x;
+            const bool ok = q < q1;
+            unsigned key = 0, val = 0;
+            if (ok) radix_item(a, pass, sg, q, key, val);
+            const unsigned dg = ok ? (key >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(kFull, dg);
+            if (ok && (int)lane == __ffs(peers) - 1) atomicAdd(&h[dg], (unsigned)__popc(peers));
         }
         __syncthreads();
         a.hist[(unsigned long long)vb * 256 + threadIdx.x] = h[threadIdx.x];
@@ -380,89 +387,117 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(LargeArgs a, int p
 // digit d of virtual block vb (digit-major order inside the segment).
 __global__ void __launch_bounds__(256) k_radix_offsets(LargeArgs a) {
     if (block_skip(a.st)) return;
-    __shared__ unsigned s_tot[256];
+    constexpr int B = 8;   // virtual blocks loaded per step (independent loads in flight)
+    __shared__ unsigned s_w[8];
     const unsigned nseg = 2 * a.st->nlarge;
+    const unsigned d = threadIdx.x, lane = d & 31, warp = d >> 5;
     for (unsigned sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
         const unsigned v0 = a.seg_vb[sg], v1 = a.seg_vb[sg + 1];
-        const unsigned d = threadIdx.x;
+        unsigned *col = a.hist + d;
+        // exclusive prefix over the segment's virtual blocks, per digit
         unsigned run = 0;
-        for (unsigned vb = v0; vb < v1; vb++) {
-            const unsigned x = a.hist[(unsigned long long)vb * 256 + d];
-            a.hist[(unsigned long long)vb * 256 + d] = run;
-            run += x;
+        for (unsigned vb = v0; vb < v1; vb += B) {
+            unsigned x[B];
+#pragma unroll
+            for (int k = 0; k < B; k++) x[k] = vb + k < v1 ? col[(unsigned long long)(vb + k) * 256] : 0u;
+#pragma unroll
+            for (int k = 0; k < B; k++)
+                if (vb + k < v1) {
+                    col[(unsigned long long)(vb + k) * 256] = run;
+                    run += x[k];
+                }
         }
-        s_tot[d] = run;
-        __syncthreads();
-        if (d == 0) {
-            unsigned acc = 0;
-            for (int q = 0; q < 256; q++) {
-                const unsigned x = s_tot[q];
-                s_tot[q] = acc;
-                acc += x;
-            }
+        // exclusive scan of the digit totals (digit-major order in the segment)
+        unsigned inc = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(kFull, inc, o);
+            if ((int)lane >= o) inc += y;
         }
+        if (lane == 31) s_w[warp] = inc;
         __syncthreads();
-        const unsigned add = s_tot[d] + a.seg_off[sg];
-        for (unsigned vb = v0; vb < v1; vb++) a.hist[(unsigned long long)vb * 256 + d] += add;
-        __syncthreads();
+        unsigned wpre = 0;
+        for (unsigned k = 0; k < warp; k++) wpre += s_w[k];
+        const unsigned add = wpre + inc - run + a.seg_off[sg];
+        for (unsigned vb = v0; vb < v1; vb += B) {
+            unsigned x[B];
+#pragma unroll
+            for (int k = 0; k < B; k++) x[k] = vb + k < v1 ? col[(unsigned long long)(vb + k) * 256] : 0u;
+#pragma unroll
+            for (int k = 0; k < B; k++)
+                if (vb + k < v1) col[(unsigned long long)(vb + k) * 256] = x[k] + add;
+        }
+        __syncthreads();   // s_w is reused by the next segment
     }
 }
 
-// Stable scatter: items are taken in rounds of 256 in order; inside a round
-// a warp ranks equal digits with match_any, warps are ordered through a
-// shared per-warp digit table.
+// Stable scatter of a virtual block: warp w owns the block's items
+// [w * 512, (w + 1) * 512) and walks them 32 at a time in order.  The warps'
+// digit counts give every (warp, digit) its first destination (after the
+// same digit's items of the warps before it); inside a warp, equal digits
+// are ranked by lane with match_any.  Two barriers per virtual block.
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(LargeArgs a, int pass) {
     if (block_skip(a.st)) return;
     constexpr int NW = kRadixThreads / 32;
-    __shared__ unsigned s_run[256];
-    __shared__ unsigned s_w[NW][256];
-    __shared__ unsigned s_dst[256];
+    constexpr int PER = kRadixBlock / kRadixThreads;   // items per lane
+    constexpr int WITEMS = kRadixBlock / NW;           // items per warp
+    __shared__ unsigned s_w[NW][256];   // per-warp digit counts, then next destinations
     const unsigned nvb = a.st->nvb, nseg = 2 * a.st->nlarge;
     const int shift = 8 * pass;
     const unsigned lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int q = threadIdx.x; q < NW * 256; q += kRadixThreads) (&s_w[0][0])[q] = 0;
+    const unsigned lt = lanemask_lt();
     for (unsigned vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
-        s_run[threadIdx.x] = 0;
-        s_dst[threadIdx.x] = a.hist[(unsigned long long)vb * 256 + threadIdx.x];
-        __syncthreads();
+        for (int d = lane; d < 256; d += 32) s_w[w][d] = 0;
+        __syncwarp();
         const unsigned sg = seg_of_vb(a.seg_vb, nseg, vb);
-        const unsigned q0 = (vb - a.seg_vb[sg]) * kRadixBlock;
+        const unsigned q0 = (vb - a.seg_vb[sg]) * kRadixBlock + w * WITEMS;
         const unsigned n = a.seg_off[sg + 1] - a.seg_off[sg];
-        const unsigned q1 = min(n, q0 + kRadixBlock);
-        for (unsigned qb = q0; qb < q1; qb += kRadixThreads) {
-            const unsigned q = qb + threadIdx.x;
-            const bool valid = q < q1;
-            unsigned key = 0, val = 0, dg = 0xffffffffu;
-            if (valid) {
-                radix_item(a, pass, sg, q, key, val);
-                dg = (key >> shift) & 255u;
-            }
-            const unsigned peers = __match_any_sync(kFull, dg);
-            const unsigned rank = __popc(peers & lanemask_lt());
-            const int leader = __ffs(peers) - 1;
-            if (valid && (int)lane == leader) s_w[w][dg] = __popc(peers);
-            __syncthreads();
-            if (valid) {
-                unsigned before = s_run[dg];
-                for (unsigned ww = 0; ww < w; ww++) before += s_w[ww][dg];
-                const unsigned dst = s_dst[dg] + before + rank;
-                if (SJ_IN(a.st, dst, a.items_cap)) {
-                    a.key_out[dst] = key;
-                    a.val_out[dst] = val;
-                }
-            }
-            __syncthreads();
-            {
-                const unsigned d = threadIdx.x;
-                unsigned add = 0;
-                for (int ww = 0; ww < NW; ww++) {
-                    add += s_w[ww][d];
-                    s_w[ww][d] = 0;
-                }
-                s_run[d] += add;
-            }
-            __syncthreads();
+        const unsigned q1 = min(n, (vb - a.seg_vb[sg]) * kRadixBlock + kRadixBlock);
+        unsigned key[PER], val[PER];
+#pragma unroll
+        for (int r = 0; r < PER; r++) {
+            const unsigned q = q0 + r * 32 + lane;
+            key[r] = 0;
+            val[r] = 0;
+            if (q < q1) radix_item(a, pass, sg, q, key[r], val[r]);
         }
+#pragma unroll
+        for (int r = 0; r < PER; r++) {   // digit counts of this warp
+            const bool ok = q0 + r * 32 + lane < q1;
+            const unsigned dg = ok ? (key[r] >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(kFull, dg);
+            if (ok && (int)lane == __ffs(peers) - 1) s_w[w][dg] += (unsigned)__popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {   // thread d: first destination of digit d for every warp
+            const unsigned d = threadIdx.x;
+            unsigned run = a.hist[(unsigned long long)vb * 256 + d];
+            for (int ww = 0; ww < NW; ww++) {
+                const unsigned c = s_w[ww][d];
+                s_w[ww][d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PER; r++) {   // stable placement
+            const bool ok = q0 + r * 32 + lane < q1;
+            const unsigned dg = ok ? (key[r] >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(kFull, dg);
+            const unsigned base = ok ? s_w[w][dg] : 0u;
+            __syncwarp();
+            if (ok) {
+                const unsigned dst = base + (unsigned)__popc(peers & lt);
+                if (SJ_IN(a.st, dst, a.items_cap)) {
+                    a.key_out[dst] = key[r];
+                    a.val_out[dst] = val[r];
+                }
+                if ((int)lane == __ffs(peers) - 1) s_w[w][dg] = base + (unsigned)__popc(peers);
+            }
+            __syncwarp();
+        }
+        __syncthreads();   // the rows are cleared for the next virtual block
     }
 }
 

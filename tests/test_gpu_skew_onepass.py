@@ -46,7 +46,8 @@ def sorted_pairs(a):
 
 @pytest.fixture(scope="module")
 def data():
-    R, S = inputs.zipf_pair(300_000, 300_000, seed=131, lattice=256, r_max_extent=2e-3, s_max_extent=6e-3,
+    # 22 tiles beyond shared memory (the largest 59,722 entries), 8.3M pairs
+    R, S = inputs.zipf_pair(300_000, 300_000, seed=131, lattice=256, r_max_extent=1e-4, s_max_extent=5e-4,
                             rho=0.3)
     return R, S, oracle.pbsm(R, S, 200)
 
