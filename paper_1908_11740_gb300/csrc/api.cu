@@ -99,7 +99,7 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
                   &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
                   &w.bResv, &w.bFail, &w.bImeta, &w.bIns, &w.bFeatRaw, &w.bFeat, &w.bPred,
                   &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bSpill, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff, &w.bScanPart,
-                  &w.lstart, &w.lcoff, &w.lvb, &w.dsq_r, &w.dsq_s, &w.dmask, &w.dcnt, &w.doff, &w.dstats,
+                  &w.lstart, &w.lcoff, &w.lvb, &w.ly, &w.dsq_r, &w.dsq_s, &w.dmask, &w.dcnt, &w.doff, &w.dstats,
                   &w.band_r, &w.band_s, &w.band_ir, &w.band_is, &w.tpairs, &w.item_of, &w.cnt64};
     for (Buf *b : all) {
         dev_free(ctx, b->p);
@@ -374,6 +374,7 @@ int sj::size_workspace(sj_ctx *ctx, Workspace &w, long long T) {
     if ((st = ensure(ctx, w.lid, 4ull * (w.items_cap + 1)))) return st;
     if ((st = ensure(ctx, w.lstart, 4ull * (w.items_cap + 1)))) return st;
     if ((st = ensure(ctx, w.lcoff, 8ull * (w.items_cap + 1)))) return st;
+    if ((st = ensure(ctx, w.ly, 8ull * (w.items_cap + 1)))) return st;
     if ((st = ensure(ctx, w.lvb, 32ull * (w.vb_cap + 2)))) return st;
     if ((st = ensure(ctx, w.pc, 4ull * nslots))) return st;
     if ((st = ensure(ctx, w.poff, 8ull * nslots))) return st;
@@ -404,8 +405,9 @@ LargeArgs sj::large_args(Workspace &w) {
     a.lid = (unsigned *)w.lid.p;
     a.items_cap = w.items_cap;
     a.vb_cap = w.vb_cap;
-    if (w.lcoff.p && w.lstart.p && w.lvb.p) {
+    if (w.lcoff.p && w.lstart.p && w.lvb.p && w.ly.p) {
         a.lstart = (unsigned *)w.lstart.p;
+        a.ly = (float2 *)w.ly.p;
         a.lcoff = (unsigned long long *)w.lcoff.p;
         unsigned long long *v = (unsigned long long *)w.lvb.p;
         const size_t n = (size_t)w.vb_cap + 2;

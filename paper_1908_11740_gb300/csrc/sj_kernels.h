@@ -69,6 +69,7 @@ struct LargeArgs {
     unsigned long long *vbpairs;      // pairs of every virtual block (count pass)
     unsigned long long *vbcur;        // write cursor of every virtual block (write pass)
     unsigned *vbch;                   // first candidate chunk of every virtual block (vb_cap + 1)
+    float2 *ly;                       // (y_l, y_u) of the sorted entries: all a candidate test reads
     unsigned long long items_cap;
     unsigned vb_cap;
     Stats *st;

@@ -515,13 +515,10 @@ __global__ void __launch_bounds__(256) k_large_gather(LargeArgs a) {
             else hi = mid;
         }
         const unsigned v = a.val_in[i];
-        if (lo & 1) {
-            a.lmbr[i] = a.ent_s[v];
-            a.lid[i] = a.id_s[v];
-        } else {
-            a.lmbr[i] = a.ent_r[v];
-            a.lid[i] = a.id_r[v];
-        }
+        const float4 m = (lo & 1) ? a.ent_s[v] : a.ent_r[v];
+        a.lmbr[i] = m;
+        a.lid[i] = (lo & 1) ? a.id_s[v] : a.id_r[v];
+        if (a.ly) a.ly[i] = make_float2(m.y, m.w);
     }
 }
 
@@ -828,7 +825,7 @@ __global__ void __launch_bounds__(kCandThreads) k_large_cand(LargeArgs a, SweepA
     __shared__ int2 s_pairs[kCandChunk];   // MODE_WRITE: the chunk's pairs
     __shared__ unsigned s_vb, s_sg, s_pa, s_pb, s_n, s_q0;
     __shared__ unsigned long long s_c0, s_c1, s_base;
-    __shared__ float4 s_pv;
+    __shared__ float2 s_pv;
     __shared__ unsigned s_pid;
     __shared__ unsigned s_red[kCandThreads / 32];
     if (block_skip(o.st)) return;
@@ -880,7 +877,7 @@ __global__ void __launch_bounds__(kCandThreads) k_large_cand(LargeArgs a, SweepA
                 s_pa = pa;
                 s_pb = pb;
                 if (pa == pb) {   // one pivot owns the whole chunk (a heavy pivot): its data once
-                    s_pv = a.lmbr[pa];
+                    s_pv = a.ly[pa];
                     s_pid = a.lid[pa];
                     s_q0 = a.lstart[pa] + (unsigned)(c0 - a.lcoff[pa]);
                 }
@@ -893,7 +890,9 @@ __global__ void __launch_bounds__(kCandThreads) k_large_cand(LargeArgs a, SweepA
             const bool single = pa == pb;
             unsigned my = 0;
             for (unsigned jb = 0; jb < nc; jb += kCandThreads * kU) {
-                float4 pv[kU], ob[kU];
+                // the candidates lie in the pivot's x range by construction: the
+                // test reads only the y extents (8 bytes) and ids of both
+                float2 pv[kU], ob[kU];
                 unsigned pid[kU], oid[kU];
                 bool ok[kU];
 #pragma unroll
@@ -910,15 +909,15 @@ __global__ void __launch_bounds__(kCandThreads) k_large_cand(LargeArgs a, SweepA
                         const unsigned long long c = c0 + j;
                         const unsigned p = cand_owner(a.lcoff, pa, pb, c);
                         q = a.lstart[p] + (unsigned)(c - a.lcoff[p]);
-                        pv[u] = a.lmbr[p];
+                        pv[u] = a.ly[p];
                         pid[u] = a.lid[p];
                     }
-                    ob[u] = a.lmbr[q];
+                    ob[u] = a.ly[q];
                     oid[u] = a.lid[q];
                 }
 #pragma unroll
                 for (int u = 0; u < kU; u++) {   // y-test, reference-point test, emission
-                    const bool hit = ok[u] && ob[u].y <= pv[u].w && pv[u].y <= ob[u].w && reported_here(pid[u], oid[u]);
+                    const bool hit = ok[u] && ob[u].x <= pv[u].y && pv[u].x <= ob[u].y && reported_here(pid[u], oid[u]);
                     if (MODE == MODE_WRITE || MODE == MODE_APPEND) {
                         const unsigned hm = __ballot_sync(kFull, hit);
                         if (hm) {
