@@ -125,7 +125,12 @@ typedef void (*sj_free_fn)(void *ptr, void *user);
 /* ---- context ---------------------------------------------------------- */
 /* Create a context on `device` issuing all work on `cuda_stream` (a
  * cudaStream_t; NULL = the legacy default stream).  *out receives the
- * handle.  Returns SJ_EINVAL for a bad device, SJ_ECUDA / SJ_ENOMEM. */
+ * handle.  Returns SJ_EINVAL for a bad device, SJ_ECUDA / SJ_ENOMEM.
+ * Environment variables read here, for measurements only (the results are
+ * the same either way): SJ_L1_WRITE=private (per-CTA L1 write ranges),
+ * SJ_BLOCK_TARGET=n (entries per block of the two-level plan),
+ * SJ_STRIPES=0 (1D grids take the general path), SJ_BATCH_GRAPHS=0 (batches
+ * launch directly), SJ_BATCH_COUNT=global (batch count by global atomics). */
 int sj_create(sj_ctx **out, int device, void *cuda_stream);
 
 /* Release the context and its workspace (synchronises its stream). */
