@@ -138,6 +138,7 @@ cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, 
 // memory, forward scan along the stripe (stripes.cu)
 cudaError_t stripe_setup();
 size_t stripe_smem_bytes();
-cudaError_t launch_stripe_join(int mode, const BArgs &a, int vert, const BJoinOut &o, int grid, cudaStream_t s);
+cudaError_t launch_stripe_join(int mode, const BArgs &a, int vert, unsigned *skey, unsigned short *sval,
+                               unsigned long long scap, const BJoinOut &o, int grid, cudaStream_t s);
 
 }  // namespace sj

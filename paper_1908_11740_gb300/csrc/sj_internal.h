@@ -35,6 +35,7 @@ struct Workspace {
     Buf bJd, bIjoin, bJfirst, bJoff;               // join table (batches: per-join offsets)
     Buf bScanPart;                                 // block scan: sums per chunk of blocks
     Buf lstart, lcoff, lvb, ly;                    // candidate-parallel sweep of the large tiles
+    Buf st_order;                                  // stripe kernel: every stripe's sorted keys and order
     Buf dsq_r, dsq_s, dmask, dcnt, doff, dstats;   // eps-distance join: squares, refinement
     Buf band_r, band_s, band_ir, band_is;          // row band of a join: its rectangles and their indices
     Buf tpairs, item_of, cnt64;                    // block labels from per-tile pair counts

@@ -25,7 +25,9 @@
 //     the one that holds its reference point.  Candidates are read from their
 //     L1 entries.
 //  3. Two passes: count (pairs per stripe), scan, exact allocation, write.
-//     The write pass sorts again (cheaper than storing the order).
+//     The count pass stores every stripe's sorted keys and order (6 bytes an
+//     entry, at the stripe's R start + S start, which are disjoint ranges);
+//     the write pass loads them instead of sorting again.
 // A stripe with more entries than shared memory holds sends the join to the
 // general path.
 #define SJ_FILE_CODE 4
@@ -152,6 +154,9 @@ struct StArgs {
     const unsigned *ins;       // per work item: S count
     int bx;                    // stripes per row of the block grid (G = 1: blocks are tiles)
     int vert;                  // 1: vertical stripes (nx x 1), swept along y; 0: along x
+    unsigned *skey;            // sorted keys of every stripe (count pass writes, write pass reads)
+    unsigned short *sval;      // ... and the merged index of each sorted position
+    unsigned long long scap;   // entries skey / sval hold
     Stats *st;
 };
 
@@ -185,18 +190,33 @@ __global__ void __launch_bounds__(kStThreads, 1) k_stripe_join(StArgs a, BJoinOu
             __syncthreads();
             continue;
         }
-        // keys of the lower coordinate along the stripe, S first, then R: the
-        // stable sort then puts S before R on equal keys, which is Algorithm
-        // 1's tie rule (on r.x_l == s.x_l, s is the pivot), so every pivot's
-        // candidates follow it in the merged order
-        for (int e = threadIdx.x; e < n; e += kStThreads) {
-            const bool isS = e < ns;
-            const float4 m = (isS ? es[e] : er[e - ns]).mbr;
-            sm.key[e] = xkey(a.vert ? m.y : m.x);
-            sm.val[e] = (unsigned short)e;
+        const unsigned long long sbase = (unsigned long long)mt.y + mt.w;   // this stripe's sorted order
+        const bool keep = a.skey && sbase + (unsigned long long)n <= a.scap;   // room for the stored order
+        if (MODE == MODE_WRITE && keep) {   // the count pass's order
+            for (int k = threadIdx.x; k < n; k += kStThreads) {
+                sm.key[k] = a.skey[sbase + k];
+                sm.val[k] = a.sval[sbase + k];
+            }
+            __syncthreads();
+        } else {
+            // keys of the lower coordinate along the stripe, S first, then R:
+            // the stable sort then puts S before R on equal keys, which is
+            // Algorithm 1's tie rule (on r.x_l == s.x_l, s is the pivot), so
+            // every pivot's candidates follow it in the merged order
+            for (int e = threadIdx.x; e < n; e += kStThreads) {
+                const bool isS = e < ns;
+                const float4 m = (isS ? es[e] : er[e - ns]).mbr;
+                sm.key[e] = xkey(a.vert ? m.y : m.x);
+                sm.val[e] = (unsigned short)e;
+            }
+            __syncthreads();
+            st_sort(sm.key, sm.val, sm.tkey, sm.tval, n, sm.hist, s_w);
+            if (MODE == MODE_COUNT && keep)
+                for (int k = threadIdx.x; k < n; k += kStThreads) {
+                    a.skey[sbase + k] = sm.key[k];
+                    a.sval[sbase + k] = sm.val[k];
+                }
         }
-        __syncthreads();
-        st_sort(sm.key, sm.val, sm.tkey, sm.tval, n, sm.hist, s_w);
         // position of every entry in the merged order (tval is free now)
         for (int k = threadIdx.x; k < n; k += kStThreads)
             if (SJ_IN(a.st, sm.val[k], n)) sm.tval[sm.val[k]] = (unsigned short)k;
@@ -261,7 +281,8 @@ cudaError_t stripe_setup() {
     return cudaFuncSetAttribute(k_stripe_join<MODE_WRITE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
-cudaError_t launch_stripe_join(int mode, const BArgs &b, int vert, const BJoinOut &o, int grid, cudaStream_t s) {
+cudaError_t launch_stripe_join(int mode, const BArgs &b, int vert, unsigned *skey, unsigned short *sval,
+                               unsigned long long scap, const BJoinOut &o, int grid, cudaStream_t s) {
     StArgs a;
     a.bent_r = b.bent_r;
     a.bent_s = b.bent_s;
@@ -269,6 +290,9 @@ cudaError_t launch_stripe_join(int mode, const BArgs &b, int vert, const BJoinOu
     a.ins = b.ins;
     a.bx = b.bx;
     a.vert = vert;
+    a.skey = skey;
+    a.sval = sval;
+    a.scap = scap;
     a.st = b.st;
     if (mode == MODE_COUNT) k_stripe_join<MODE_COUNT><<<grid, kStThreads, sizeof(StSmem), s>>>(a, o);
     else k_stripe_join<MODE_WRITE><<<grid, kStThreads, sizeof(StSmem), s>>>(a, o);
@@ -299,6 +323,11 @@ int sj::join_stripes(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, c
     for (int attempt = 0; attempt < 3; attempt++) {
         int st;
         if ((st = size_blocked(ctx, w, p))) return st;
+        // the stripes' sorted orders: keys, then merged indexes, one slot per L1 entry
+        const unsigned long long scap = w.bcap_r + w.bcap_s;
+        if ((st = ensure(ctx, w.st_order, 6ull * scap + 16))) return st;
+        unsigned *skey = (unsigned *)w.st_order.p;
+        unsigned short *sval = (unsigned short *)(skey + scap);
         BArgs a = blocked_args(w, p, R, nR, S, nS, gd);
         if (ctx->shared_cursors) a.cur = (unsigned *)w.bCur.p;
         a.fine_cap = kStCap;   // a stripe beyond the stripe kernel's capacity needs the general path
@@ -306,7 +335,7 @@ int sj::join_stripes(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, c
         cudaError_t e;
         {
             PhaseScope ph(ctx, PH_SWEEP_COUNT, 1);
-            if ((e = launch_stripe_join(MODE_COUNT, a, vert, bjoin_out(w, 0), ctx->num_sms, s)))
+            if ((e = launch_stripe_join(MODE_COUNT, a, vert, skey, sval, scap, bjoin_out(w, 0), ctx->num_sms, s)))
                 return cuda_fail(ctx, e, "stripe join kernel");
         }
         {
@@ -343,7 +372,7 @@ int sj::join_stripes(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR, c
         wo.cap = P;
         {
             PhaseScope ph(ctx, PH_SWEEP_WRITE, 1);
-            if ((e = launch_stripe_join(MODE_WRITE, a, vert, wo, ctx->num_sms, s))) {
+            if ((e = launch_stripe_join(MODE_WRITE, a, vert, skey, sval, scap, wo, ctx->num_sms, s))) {
                 out_abandon(ctx, os);
                 return cuda_fail(ctx, e, "stripe join kernel");
             }
