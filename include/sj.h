@@ -201,7 +201,7 @@ int sj_join_into(sj_ctx *ctx, const sj_rect *d_R, int64_t nR,
 
 /* Per-tile statistics of a join on grid *g (device outputs, caller-owned,
  * each nx*ny long; any may be NULL): replicated entries per side and the
- * exact number of pairs each tile reports.  Used to train and judge the
+ * exact number of pairs each tile reports.  Used to train and evaluate the
  * per-tile result-count predictor.  Synchronises once. */
 int sj_tile_stats(sj_ctx *ctx, const sj_rect *d_R, int64_t nR,
                   const sj_rect *d_S, int64_t nS, const sj_grid *g,
