@@ -42,6 +42,16 @@ def test_every_declared_symbol_is_exported(lib):
     assert not missing, missing
 
 
+def test_debug_build_exports_the_same_symbols():
+    """The debug build with bounds checks (-DSJ_CHECK=1) compiles and loads
+    with the same boundary."""
+    from paper_1908_11740_gb300 import build
+
+    dbg = ctypes.CDLL(build.build(check=True))
+    missing = [n for n in declared_functions() if not hasattr(dbg, n)]
+    assert not missing, missing
+
+
 def test_binding_covers_every_symbol():
     from paper_1908_11740_gb300 import sj
 
