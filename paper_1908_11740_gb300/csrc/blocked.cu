@@ -659,6 +659,7 @@ struct BJSmem {
     float4 mbr[kFineCap];            // the band's entries, grouped by tile segment
     unsigned id[kFineCap];
     unsigned short tile[kFineCap];   // band-local tile of each position
+    unsigned short ord[kFineCap];    // x_l order of every tile segment (positions of its entries)
     unsigned short band[kMaxFine + 2];
     int2 pbuf[kPairBuf];             // one-pass: the block's pairs before its reservation
     unsigned axis[kMaxFine / 32];    // adaptive sweep axis: bit per tile, 1 = y
@@ -676,6 +677,7 @@ static_assert(offsetof(BJSmem, id) + sizeof(BJSmem::id) - offsetof(BJSmem, key) 
                   sizeof(unsigned) * kHistWords * kMaxFine,
               "per-tile histograms must fit in key[] .. id[]");
 static_assert(kFineCap < 65536, "16-bit histogram counters");
+static_assert(sizeof(BJSmem) <= 111 * 1024, "two block-join CTAs (and their static shared memory) per SM");
 
 // Bucket index at 8x the tile resolution: floor(8 t) for the cell-function
 // value t = (v - g0) * ginv (both rounded to float32, as in cell_of; 8 t is
@@ -881,16 +883,14 @@ __device__ __forceinline__ void band_fill(BJSmem &sm, const BlockCtx &bc, int ta
     }
     __syncthreads();
     // sort every tile segment by x_l: the rank of each position among its
-    // segment (ties by position) gives key[segment start + rank] = position,
-    // i.e. after this step key[] holds the x_l order of every segment and
+    // segment (ties by position) gives ord[segment start + rank] = position,
+    // i.e. after this step ord[] holds the x_l order of every segment and
     // the entries themselves stay where the scatter put them
     const int nb = nRb + nSb;
     constexpr int KP = kFineCap / kBJThreads;
-    int dst[KP];
 #pragma unroll
     for (int q = 0; q < KP; q++) {
         const int pidx = threadIdx.x + q * NT;
-        dst[q] = -1;
         if (pidx < nb) {
             const int side = pidx >= nRb;
             const unsigned tw = sm.tile[pidx];
@@ -912,13 +912,9 @@ __device__ __forceinline__ void band_fill(BJSmem &sm, const BlockCtx &bc, int ta
                     r += (kq < k0) | ((kq == k0) & (qq < pidx));
                 }
             }
-            dst[q] = s0 + r;
+            sm.ord[s0 + r] = (unsigned short)pidx;
         }
     }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < KP; q++)
-        if (dst[q] >= 0) sm.key[dst[q]] = (unsigned)(threadIdx.x + q * NT);
     __syncthreads();
 }
 
@@ -937,7 +933,7 @@ __device__ __forceinline__ void stage_band(BJSmem &sm, const BlockCtx &bc, int t
 }
 
 // Candidate range of pivot p (any position) in the other side of its tile:
-// ranks k..kend-1 of that segment's x_l order (entry sm.key[k]).
+// ranks k..kend-1 of that segment's x_l order (entry sm.ord[k]).
 __device__ __forceinline__ void band_pivot(const BJSmem &sm, int nRb, int p, float4 &pv, unsigned &pid, int &k,
                                            int &kend, bool &isR, Stats *st, int nb) {
     isR = p < nRb;
@@ -952,7 +948,7 @@ __device__ __forceinline__ void band_pivot(const BJSmem &sm, int nRb, int p, flo
     // first x_l > pivot.x_l (R pivot) or >= pivot.x_l (S pivot), in x_l order
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        const float xm = sm.mbr[sm.key[mid]].x;
+        const float xm = sm.mbr[sm.ord[mid]].x;
         const bool right = isR ? (xm > pv.x) : (xm >= pv.x);
         if (right) hi = mid;
         else lo = mid + 1;
@@ -974,7 +970,7 @@ __device__ __forceinline__ unsigned band_count(const BJSmem &sm, const BlockCtx 
         band_pivot(sm, nRb, p, pv, pid, k, kend, isR, bc.st, nb);
         unsigned c = 0;
         for (; k < kend; k++) {
-            const unsigned q = SJ_AT(bc.st, sm.key[k], nb);
+            const unsigned q = SJ_AT(bc.st, sm.ord[k], nb);
             const float4 o = sm.mbr[q];
             if (o.x > pv.z) break;
             if (o.y <= pv.w && pv.y <= o.w && reported_here(pid, sm.id[q])) c++;
@@ -1009,7 +1005,7 @@ __device__ __forceinline__ void band_write(const BJSmem &sm, int nRb, int nSb, i
             unsigned q = 0;
             bool cand = false;
             if (go && k < kend) {
-                q = SJ_AT(st, sm.key[k], nb);
+                q = SJ_AT(st, sm.ord[k], nb);
                 o = sm.mbr[q];
                 cand = o.x <= pv.z;
             }
@@ -1055,7 +1051,7 @@ __device__ __forceinline__ void band_collect(BJSmem &sm, int nRb, int nSb, unsig
         bool isR;
         band_pivot(sm, nRb, p, pv, pid, k, kend, isR, st, nb);
         for (; k < kend; k++) {
-            const unsigned q = SJ_AT(st, sm.key[k], nb);
+            const unsigned q = SJ_AT(st, sm.ord[k], nb);
             const float4 o = sm.mbr[q];
             if (o.x > pv.z) break;
             if (o.y <= pv.w && pv.y <= o.w) {
@@ -1108,7 +1104,7 @@ __device__ __forceinline__ unsigned gbda_sweep(BJSmem &sm, const BlockCtx &bc, i
             int lo = s0, hi = s1;
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                const unsigned q = sm.key[mid];
+                const unsigned q = sm.ord[mid];
                 const unsigned cq = (unsigned)sm.tile[q] >> 14;
                 const float xm = sm.mbr[q].x;
                 const bool right = cq > cl || (cq == cl && (isR ? (xm > pv.x) : (xm >= pv.x)));
@@ -1116,7 +1112,7 @@ __device__ __forceinline__ unsigned gbda_sweep(BJSmem &sm, const BlockCtx &bc, i
                 else lo = mid + 1;
             }
             for (int k = lo; k < s1; k++) {
-                const unsigned q = SJ_AT(bc.st, sm.key[k], nb);
+                const unsigned q = SJ_AT(bc.st, sm.ord[k], nb);
                 if (((unsigned)sm.tile[q] >> 14) != cl) break;
                 const float4 ov = sm.mbr[q];
                 if (ov.x > pv.z) break;
@@ -1372,6 +1368,11 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
         raw_next = atomicAdd(&a.st->work[o.work_slot], 1u);
         load_meta(r0_, s_meta[0]);
     }
+    // per-tile counters start cleared; each block clears the ones it used
+    // when it ends (the adaptive variant clears them, with its histograms, as
+    // each block starts)
+    if (!ADAPT)
+        for (int k = threadIdx.x; k < 2 * kMaxFine; k += kBJThreads) (&sm.cnt[0][0])[k] = 0;
     __syncthreads();
     for (int step = 0;; step++) {
         const int cur = step & 1;
@@ -1399,13 +1400,14 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
         // step 1: entries per tile of the block (and, for the adaptive sweep
         // axis, the Eq. 2 histograms of every tile: k = 8 buckets per axis)
         unsigned *hist = reinterpret_cast<unsigned *>(sm.key);
-        for (int k = threadIdx.x; k < bc.ntl; k += kBJThreads) {
-            sm.cnt[0][k] = 0;
-            sm.cnt[1][k] = 0;
-        }
-        if (ADAPT)
+        if (ADAPT) {
+            for (int k = threadIdx.x; k < bc.ntl; k += kBJThreads) {
+                sm.cnt[0][k] = 0;
+                sm.cnt[1][k] = 0;
+            }
             for (int k = threadIdx.x; k < bc.ntl * kHistWords; k += kBJThreads) hist[k] = 0;
-        __syncthreads();
+            __syncthreads();
+        }
         const int n1 = (int)(bc.nr1 + bc.ns1);
         constexpr int kCountU = 2;   // entries a thread loads before counting them
         for (int eb = threadIdx.x; eb < n1; eb += kCountU * kBJThreads) {
@@ -1491,31 +1493,33 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
         // heavier than h (each band then holds fewer than 2h entries), and
         // neighbouring bands are merged while they fit.
         int nR0, nS0;
-        band_offsets(sm, 0, bc.ntl, nR0, nS0);
-        {
-            if (nR0 + nS0 <= kFineCap) {
-                if (threadIdx.x == 0) {
-                    sm.band[0] = 0;
-                    sm.band[1] = (unsigned short)bc.ntl;
-                    s_nbands = 1;
-                    s_huge = 0;
-                }
-            } else {
-                band_split(sm, bc.ntl, &s_nbands, &s_huge);
-            }
+        band_offsets(sm, 0, bc.ntl, nR0, nS0);   // ends with a barrier: every thread knows the total
+        const bool single = nR0 + nS0 <= kFineCap;
+        if (single) {
+            // the usual case decides without a barrier: the cursors are first
+            // used after the barrier of the band's scatter
             if (threadIdx.x == 0) {
                 s_cursor = 0;
                 s_pc = 0;
             }
+        } else {
+            band_split(sm, bc.ntl, &s_nbands, &s_huge);
+            if (threadIdx.x == 0) {
+                s_cursor = 0;
+                s_pc = 0;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (s_huge) {   // a single tile exceeds shared memory: the caller reruns on the direct path
+        // tiles of band bi
+        auto band_lo = [&](int bi) { return single ? 0 : (int)sm.band[bi]; };
+        auto band_hi = [&](int bi) { return single ? bc.ntl : (int)sm.band[bi + 1]; };
+        if (!single && s_huge) {   // a single tile exceeds shared memory: the caller reruns on the direct path
             if (threadIdx.x == 0) {
                 atomicOr(&a.st->need_direct, 1);
                 if (MODE == MODE_COUNT) o.cnt_out[it] = 0;
             }
         } else {
-            const int nbands = (int)s_nbands;
+            const int nbands = single ? 1 : (int)s_nbands;
             // a block staged in several bands first lists its entries per tile
             // row, so that every band reads only the entries of its rows
             const RowLists *rl = nullptr;
@@ -1525,7 +1529,7 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
             }
             // band bi into shared memory (a single band has its offsets already)
             auto stage = [&](int bi, int &nRb, int &nSb) {
-                stage_band(sm, bc, sm.band[bi], sm.band[bi + 1], nbands == 1, nR0, nS0, rl, nRb, nSb);
+                stage_band(sm, bc, band_lo(bi), band_hi(bi), nbands == 1, nR0, nS0, rl, nRb, nSb);
             };
             // pairs of the staged band at out[base + s_cursor ...]
             auto write = [&](int nRb, int nSb, unsigned long long base) {
@@ -1552,9 +1556,9 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                         __syncthreads();
                     } else {
                         unsigned *tp = MODE == MODE_TILES ? o.tile_pairs : nullptr;
-                        const unsigned c = GBDA ? gbda_sweep<0>(sm, bc, sm.band[bi], nRb, nSb, nullptr, nullptr,
+                        const unsigned c = GBDA ? gbda_sweep<0>(sm, bc, band_lo(bi), nRb, nSb, nullptr, nullptr,
                                                                 nullptr, 0, tp, a.g.nx)
-                                                : band_count(sm, bc, sm.band[bi], nRb, nSb, tp, a.g.nx);
+                                                : band_count(sm, bc, band_lo(bi), nRb, nSb, tp, a.g.nx);
                         tot += block_sum(c, s_red);
                     }
                 }
@@ -1596,6 +1600,13 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                 }
             }
         }
+        // clear the counters this block used (every reader of them is behind
+        // one of the barriers above) for the next block's count
+        if (!ADAPT)
+            for (int k = threadIdx.x; k < bc.ntl; k += kBJThreads) {
+                sm.cnt[0][k] = 0;
+                sm.cnt[1][k] = 0;
+            }
         if (threadIdx.x == 0) {
             load_meta(raw_next, s_meta[cur ^ 1]);
             raw_next = raw_after;

@@ -13,7 +13,7 @@ constexpr int kFineCap = 3072;       // tile entries staged in shared memory per
 constexpr int kMaxG = 32;            // tiles per block side
 constexpr int kLoadBatch = 4;        // entries a thread loads before using them
 constexpr int kMaxJoins = 4096;      // joins in one batch
-constexpr int kPairBuf = 1536;       // pairs a one-pass block collects in shared memory
+constexpr int kPairBuf = 768;        // pairs a one-pass block collects in shared memory
 constexpr int kPairSpill = 16384;    // ... and then in its CTA's global spill area
 constexpr int kMaxFine = kMaxG * kMaxG;
 
