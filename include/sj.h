@@ -306,8 +306,10 @@ int sj_set_schedule(sj_ctx *ctx, int heaviest_first);
  * exact re-run of the blocks that did not fit, and a regroup of every block's
  * pairs into its join's range; direct launches, two synchronisations (the
  * capacity, the offsets).  The pairs are the same in every mode.
- * o->sort_output is ignored (each join's range is unsorted); o->flags
- * (adaptive axis, GBDA) apply to single joins only.
+ * With o->sort_output every join's range is sorted by (r, s) after the join
+ * (one device sort of the whole buffer with every join's r shifted past the
+ * joins before it; the R inputs must total fewer than 2^32 rectangles, else
+ * SJ_EINVAL); o->flags (adaptive axis, GBDA) apply to single joins only.
  * Joins whose tiles exceed shared memory fall back to sj_join_into each
  * (exact two-pass). */
 int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const int64_t *nR,

@@ -98,7 +98,7 @@ void sj::release(sj_ctx *ctx, Workspace &w) {
                   &w.fail_c, &w.fail_l, &w.sort_tmp, &w.ps_hist, &w.ps_part, &w.in_r, &w.in_s, &w.out, &w.bH,
                   &w.bTot, &w.bBoR, &w.bBoS, &w.bItems, &w.bEntR, &w.bEntS, &w.bPc, &w.bPoff,
                   &w.bResv, &w.bFail, &w.bImeta, &w.bIns, &w.bFeatRaw, &w.bFeat, &w.bPred,
-                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bSpill, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff, &w.bScanPart,
+                  &w.bOrder, &w.bCapTot, &w.bCur, &w.bList, &w.bSpill, &w.bJd, &w.bIjoin, &w.bJfirst, &w.bJoff, &w.bScanPart, &w.bSortOff,
                   &w.lstart, &w.lcoff, &w.lvb, &w.ly, &w.st_order, &w.dsq_r, &w.dsq_s, &w.dmask, &w.dcnt, &w.doff, &w.dstats,
                   &w.band_r, &w.band_s, &w.band_ir, &w.band_is, &w.tpairs, &w.item_of, &w.cnt64};
     for (Buf *b : all) {

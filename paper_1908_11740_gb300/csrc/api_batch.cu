@@ -349,7 +349,8 @@ extern "C" int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, con
     int st = join_batch_body(ctx, nj, d_R, nR, d_S, nS, g_in, o, d_out, cap, h_offsets);
     if (st == SJ_OK) {
         DeviceGuard dg(ctx->device);
-        st = check_tail(ctx, ctx->ws);
+        if (o && o->sort_output) st = sort_pairs_by_join(ctx, ctx->ws, (int2 *)d_out, h_offsets, nR, nj);
+        if (st == SJ_OK) st = check_tail(ctx, ctx->ws);
     }
     return st;
 }

@@ -34,6 +34,7 @@ struct Workspace {
     Buf bSpill;                                    // one-pass pair spill per block-join CTA
     Buf bJd, bIjoin, bJfirst, bJoff;               // join table (batches: per-join offsets)
     Buf bScanPart;                                 // block scan: sums per chunk of blocks
+    Buf bSortOff;                                  // sorted batch output: pair and R offsets per join
     Buf lstart, lcoff, lvb, ly;                    // candidate-parallel sweep of the large tiles
     Buf st_order;                                  // stripe kernel: every stripe's sorted keys and order
     Buf dsq_r, dsq_s, dmask, dcnt, doff, dstats;   // eps-distance join: squares, refinement
@@ -119,6 +120,8 @@ int join_one_pass_spec(sj_ctx *ctx, Workspace &w, const float4 *R, long long nR,
                        const GridDev &gd, const sj_opts *o, int heuristic, OutSpec &os, int64_t *npairs,
                        sj_pair **lib_out);
 int sort_pairs(sj_ctx *ctx, Workspace &w, int2 *pairs, unsigned long long n);
+// the pairs of every join of a batch (ranges h_off[j] .. h_off[j + 1]) sorted by (r, s)
+int sort_pairs_by_join(sj_ctx *ctx, Workspace &w, int2 *pairs, const int64_t *h_off, const int64_t *nR, int nj);
 void mlp_release(sj_ctx *ctx);
 
 // Where the pairs of a join go once their number P is known.

@@ -15,7 +15,16 @@
 //      and the warp walks its pairs 32 at a time in order, placing each pair
 //      at its digit's next slot (rank among equal digits by lane), so the
 //      pass is stable.
+//
+// A batch's pairs are sorted join by join with the same sort: the r of every
+// pair of join j is shifted by the R rectangles of the joins before it, so
+// that the joins' r ranges follow each other; one sort of the whole buffer
+// then orders every join's pairs by (r, s) and keeps each join in its own
+// range (the joins' pair counts do not change), and the shift is undone.
 #define SJ_FILE_CODE 7
+#include <algorithm>
+#include <vector>
+
 #include "sj_internal.h"
 
 namespace sj {
@@ -176,6 +185,57 @@ __global__ void __launch_bounds__(kPsThreads) k_ps_scatter(const int2 *__restric
         }
         __syncwarp();
     }
+}
+
+// r of every pair of join j += sign * roff[j] (modulo 2^32), where j is the
+// join whose range [joff[j], joff[j + 1]) holds the pair.
+__global__ void __launch_bounds__(256) k_join_shift(int2 *__restrict__ pairs, unsigned long long n,
+                                                    const unsigned long long *__restrict__ joff,
+                                                    const unsigned long long *__restrict__ roff, int nj, int sign) {
+    extern __shared__ unsigned long long s_off[];   // nj + 1 pair offsets
+    for (int j = threadIdx.x; j <= nj; j += blockDim.x) s_off[j] = joff[j];
+    __syncthreads();
+    for (unsigned long long i = blockIdx.x * 256ull + threadIdx.x; i < n; i += 256ull * gridDim.x) {
+        int lo = 0, hi = nj;   // last j with s_off[j] <= i
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        const unsigned d = (unsigned)roff[lo];
+        int2 p = pairs[i];
+        p.x = (int)(sign > 0 ? (unsigned)p.x + d : (unsigned)p.x - d);
+        pairs[i] = p;
+    }
+}
+
+int sort_pairs_by_join(sj_ctx *ctx, Workspace &w, int2 *pairs, const int64_t *h_off, const int64_t *nR, int nj) {
+    const unsigned long long n = (unsigned long long)h_off[nj];
+    if (n < 2) return SJ_OK;
+    std::vector<unsigned long long> tab(2 * (size_t)(nj + 1));
+    unsigned long long r = 0;
+    for (int j = 0; j <= nj; j++) {
+        tab[j] = (unsigned long long)h_off[j];
+        tab[nj + 1 + j] = r;
+        if (j < nj) r += (unsigned long long)nR[j];
+    }
+    if (r >= (1ull << 32)) return fail(ctx, SJ_EINVAL, "sort_output of a batch needs fewer than 2^32 R rectangles");
+    int st;
+    if ((st = ensure(ctx, w.bSortOff, 8ull * tab.size()))) return st;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(w.bSortOff.p, tab.data(), 8ull * tab.size(), cudaMemcpyHostToDevice, ctx->stream)))
+        return cuda_fail(ctx, e, "copy of the join offsets");
+    const unsigned long long *joff = (const unsigned long long *)w.bSortOff.p, *roff = joff + nj + 1;
+    const unsigned grid = (unsigned)std::min<unsigned long long>((n + 255) / 256, 4096ull);
+    const size_t sm = 8ull * (nj + 1);
+    k_join_shift<<<grid, 256, sm, ctx->stream>>>(pairs, n, joff, roff, nj, 1);
+    if ((e = cudaGetLastError())) return cuda_fail(ctx, e, "join shift kernel");
+    if ((st = sort_pairs(ctx, w, pairs, n))) return st;
+    k_join_shift<<<grid, 256, sm, ctx->stream>>>(pairs, n, joff, roff, nj, -1);
+    if ((e = cudaGetLastError())) return cuda_fail(ctx, e, "join shift kernel");
+    // the host table must outlive the copy
+    if ((e = cudaStreamSynchronize(ctx->stream))) return cuda_fail(ctx, e, "stream sync");
+    return SJ_OK;
 }
 
 int sort_pairs(sj_ctx *ctx, Workspace &w, int2 *pairs, unsigned long long n) {

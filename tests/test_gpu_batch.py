@@ -112,3 +112,27 @@ def test_batch_one_pass_matches_oracle(sj, ctx, kind):
         sj.sj_set_model(ctx, None)
         if model is not None:
             model.free()
+
+
+@pytest.mark.parametrize("mode", ["two_pass", "one_pass_heur"])
+def test_batch_sorted_output(sj, ctx, mode):
+    """sort_output on a batch: every join's range comes back in (r, s) order,
+    exactly the oracle's sorted pairs (no sorting on the host), in both
+    sizing modes; a batch whose tiles exceed shared memory (joined join by
+    join) is sorted the same way."""
+    joins = _batch()
+    Rs = [dev(r) for r, _ in joins]
+    Ss = [dev(s) for _, s in joins]
+    pairs, offs = sj.sj_join_batch(ctx, Rs, Ss, None, opts=sj.make_opts(mode, sort_output=True))
+    got = pairs.cpu().numpy()
+    for j, (r, s) in enumerate(joins):
+        want = oracle.brute(r, s) if len(r) * len(s) < 2e7 else oracle.sweep(r, s)
+        np.testing.assert_array_equal(got[offs[j]:offs[j + 1]], want)
+    # hot tiles beyond shared memory in one join of the batch
+    hot = inputs.zipf_pair(40_000, 40_000, seed=77, lattice=64, r_max_extent=1e-4, s_max_extent=1e-3, rho=0.02)
+    mix = [joins[0], hot, joins[1]]
+    pairs, offs = sj.sj_join_batch(ctx, [dev(r) for r, _ in mix], [dev(s) for _, s in mix],
+                                   [sj.make_grid(k) for k in (16, 64, 16)], opts=sj.make_opts(mode, sort_output=True))
+    got = pairs.cpu().numpy()
+    for j, (r, s) in enumerate(mix):
+        np.testing.assert_array_equal(got[offs[j]:offs[j + 1]], oracle.pbsm(r, s, 16 if j != 1 else 64))
