@@ -89,10 +89,10 @@ typedef struct { int32_t nx, ny; float x0, y0, x1, y1; } sj_grid;
                                 estimate of intersecting projections (k = 8 buckets
                                 per tile axis, built from all of the tile's
                                 entries); without it every tile is swept along x
-                                (Algorithm 1).  Two-level path of single joins
-                                only: the single-level path (tiles beyond shared
-                                memory) and batches sweep along x.  The pairs
-                                are the same either way.  See sj_tile_axes.      */
+                                (Algorithm 1).  Two-level path (single joins and
+                                batches); the single-level path (tiles beyond
+                                shared memory) sweeps along x.  The pairs are
+                                the same either way.  See sj_tile_axes.          */
 #define SJ_DEDUP_GBDA     2  /* grouping-based duplicate avoidance instead of the
                                 reference-point test of Eq. 1: the entries of a
                                 tile are grouped in four classes by where their
@@ -101,8 +101,8 @@ typedef struct { int32_t nx, ny; float x0, y0, x1, y1; } sj_grid;
                                 only the 9 class pairs that can report a pair
                                 in this tile are joined (A with any, any with A,
                                 B with C, C with B), with no test per pair.  The
-                                pairs are the same.  Two-level path of single
-                                joins; the single-level path and batches use
+                                pairs are the same.  Two-level path (single
+                                joins and batches); the single-level path uses
                                 Eq. 1.  Not combinable with SJ_SWEEP_ADAPTIVE.  */
 
 typedef struct {
@@ -309,7 +309,7 @@ int sj_set_schedule(sj_ctx *ctx, int heaviest_first);
  * With o->sort_output every join's range is sorted by (r, s) after the join
  * (one device sort of the whole buffer with every join's r shifted past the
  * joins before it; the R inputs must total fewer than 2^32 rectangles, else
- * SJ_EINVAL); o->flags (adaptive axis, GBDA) apply to single joins only.
+ * SJ_EINVAL); o->flags (adaptive axis, GBDA) apply to every join of the batch.
  * Joins whose tiles exceed shared memory fall back to sj_join_into each
  * (exact two-pass). */
 int sj_join_batch(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const int64_t *nR,

@@ -216,6 +216,8 @@ static int batch_one_pass(sj_ctx *ctx, std::vector<JoinDesc> &jd, int nbt, long 
         a.scan_part = (unsigned long long *)w.bScanPart.p;
         a.feat_raw = (unsigned *)w.bFeatRaw.p;
         a.fine_cap = kFineCap;
+        a.adaptive = o && (o->flags & SJ_SWEEP_ADAPTIVE);
+        a.gbda = o && (o->flags & SJ_DEDUP_GBDA);
         a.st = (Stats *)w.stats.p;
         cudaError_t e;
         {
@@ -468,6 +470,8 @@ static int join_batch_body(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const
         a.lpool_cap = list_pool_cap(w);
         a.scan_part = (unsigned long long *)w.bScanPart.p;
         a.fine_cap = kFineCap;
+        a.adaptive = o && (o->flags & SJ_SWEEP_ADAPTIVE);
+        a.gbda = o && (o->flags & SJ_DEDUP_GBDA);
         a.st = (Stats *)w.stats.p;
         // the arguments that shape the captured work
         unsigned long long key = 1469598103934665603ull;
@@ -547,10 +551,11 @@ static int join_batch_body(sj_ctx *ctx, int nj, const sj_rect *const *d_R, const
             }
             if (cap < h_offsets[nj])
                 return fail(ctx, SJ_EOVERFLOW, "need %lld pairs, cap %lld", (long long)h_offsets[nj], (long long)cap);
+            sj_opts each{SJ_TWO_PASS, 0, 0.25f, o ? o->flags : 0};   // the batch's sweep options, exact
             for (int j = 0; j < nj; j++) {
                 int64_t n = 0;
                 if (h_offsets[j + 1] == h_offsets[j]) continue;
-                if ((st = sj_join_into(ctx, d_R[j], nR[j], d_S[j], nS[j], &grids[j], nullptr, d_out + h_offsets[j],
+                if ((st = sj_join_into(ctx, d_R[j], nR[j], d_S[j], nS[j], &grids[j], &each, d_out + h_offsets[j],
                                        h_offsets[j + 1] - h_offsets[j], &n)))
                     return st;
             }

@@ -1327,7 +1327,7 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
     constexpr int GBDA = VARIANT == 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BJSmem &sm = *reinterpret_cast<BJSmem *>(smem_raw);
-    __shared__ unsigned s_meta[2][12];  // current / next item: item, block, r0, nr, s0, ns, join geometry
+    __shared__ unsigned s_meta[2][16];  // current / next item: item, block, r0, nr, s0, ns, join geometry
     __shared__ unsigned s_nbands, s_cursor, s_pc;
     __shared__ RowLists s_rows;
     __shared__ int s_ok, s_huge;
@@ -1355,6 +1355,10 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
             m[7] = (unsigned)d.bx;
             m[8] = (unsigned)d.g.nx;
             m[9] = (unsigned)d.g.ny;
+            m[10] = __float_as_uint(d.g.x0);   // the join's grid (adaptive axis: the Eq. 2 buckets)
+            m[11] = __float_as_uint(d.g.gx);
+            m[12] = __float_as_uint(d.g.y0);
+            m[13] = __float_as_uint(d.g.gy);
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.bent_r + q.y),
                          "r"(q.z * (unsigned)sizeof(BEnt)) : "memory");
             asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a.bent_s + q.w),
@@ -1430,10 +1434,12 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                 const int ly0 = max(cy0 - bc.cyb, 0), ly1 = min(cy1 - bc.cyb, bc.gh - 1);
                 int fx0 = 0, fx1 = 0, fy0 = 0, fy1 = 0;
                 if (ADAPT) {
-                    fx0 = cell8_of(__uint_as_float(hd[u].x), a.g.x0, a.g.gx, a.g.nx);
-                    fx1 = cell8_of(__uint_as_float(hd[u].z), a.g.x0, a.g.gx, a.g.nx);
-                    fy0 = cell8_of(__uint_as_float(hd[u].y), a.g.y0, a.g.gy, a.g.ny);
-                    fy1 = cell8_of(__uint_as_float(hd[u].w), a.g.y0, a.g.gy, a.g.ny);
+                    const float gx0 = __uint_as_float(m[10]), ggx = __uint_as_float(m[11]);
+                    const float gy0 = __uint_as_float(m[12]), ggy = __uint_as_float(m[13]);
+                    fx0 = cell8_of(__uint_as_float(hd[u].x), gx0, ggx, jnx);
+                    fx1 = cell8_of(__uint_as_float(hd[u].z), gx0, ggx, jnx);
+                    fy0 = cell8_of(__uint_as_float(hd[u].y), gy0, ggy, jny);
+                    fy1 = cell8_of(__uint_as_float(hd[u].w), gy0, ggy, jny);
                 }
                 for (int ly = ly0; ly <= ly1; ly++)
                     for (int lx = lx0; lx <= lx1; lx++) {
@@ -1557,8 +1563,8 @@ __global__ void __launch_bounds__(kBJThreads, 2) k_bjoin(BArgs a, BJoinOut o) {
                     } else {
                         unsigned *tp = MODE == MODE_TILES ? o.tile_pairs : nullptr;
                         const unsigned c = GBDA ? gbda_sweep<0>(sm, bc, band_lo(bi), nRb, nSb, nullptr, nullptr,
-                                                                nullptr, 0, tp, a.g.nx)
-                                                : band_count(sm, bc, band_lo(bi), nRb, nSb, tp, a.g.nx);
+                                                                nullptr, 0, tp, jnx)
+                                                : band_count(sm, bc, band_lo(bi), nRb, nSb, tp, jnx);
                         tot += block_sum(c, s_red);
                     }
                 }
@@ -1829,7 +1835,7 @@ cudaError_t launch_bscatter(const BArgs &a, int nc, cudaStream_t s) {
 
 cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, cudaStream_t s) {
     const size_t sm = sizeof(BJSmem);
-    if (a.gbda && a.nj == 1) {
+    if (a.gbda) {
         switch (mode) {
             case MODE_COUNT: k_bjoin<MODE_COUNT, 2><<<grid, kBJThreads, sm, s>>>(a, o); break;
             case MODE_WRITE: k_bjoin<MODE_WRITE, 2><<<grid, kBJThreads, sm, s>>>(a, o); break;
@@ -1838,7 +1844,7 @@ cudaError_t launch_bjoin(int mode, const BArgs &a, const BJoinOut &o, int grid, 
         }
         return cudaGetLastError();
     }
-    if (a.adaptive && a.nj == 1) {
+    if (a.adaptive) {
         switch (mode) {
             case MODE_COUNT: k_bjoin<MODE_COUNT, 1><<<grid, kBJThreads, sm, s>>>(a, o); break;
             case MODE_WRITE: k_bjoin<MODE_WRITE, 1><<<grid, kBJThreads, sm, s>>>(a, o); break;

@@ -77,8 +77,8 @@ struct BArgs {
     unsigned long long lpool_cap;
     int pts;                    // 1: R, S hold float2 points, read as squares of half-width h
     float h;
-    int adaptive;               // single join: sweep axis per tile from Eq. 2 histograms (Sec. 3.3)
-    int gbda;                   // single join: grouping-based duplicate avoidance instead of Eq. 1
+    int adaptive;               // sweep axis per tile from Eq. 2 histograms (Sec. 3.3)
+    int gbda;                   // grouping-based duplicate avoidance instead of Eq. 1
     int fine_cap;               // entries one tile may hold for the consumer of the partition
     int stop_direct;            // one-pass sizing: skip the feature sample once a tile exceeds shared memory
     Stats *st;

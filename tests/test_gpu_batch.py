@@ -136,3 +136,21 @@ def test_batch_sorted_output(sj, ctx, mode):
     got = pairs.cpu().numpy()
     for j, (r, s) in enumerate(mix):
         np.testing.assert_array_equal(got[offs[j]:offs[j + 1]], oracle.pbsm(r, s, 16 if j != 1 else 64))
+
+
+@pytest.mark.parametrize("variant", [{"axis": "adaptive"}, {"dedup": "gbda"}])
+@pytest.mark.parametrize("mode", ["two_pass", "one_pass_heur"])
+def test_batch_sweep_options(sj, ctx, mode, variant):
+    """The adaptive sweep axis and GBDA on a batch (each join's own grid for
+    the Eq. 2 buckets): every join's range equals the oracle's pairs, the
+    graphs of the option are their own (a plain batch after it is exact too)."""
+    joins = _batch()
+    joins.append(inputs.aniso_pair(20_000, 30_000, seed=91))
+    Rs = [dev(r) for r, _ in joins]
+    Ss = [dev(s) for _, s in joins]
+    for opts in (sj.make_opts(mode, **variant), sj.make_opts(mode)):
+        pairs, offs = sj.sj_join_batch(ctx, Rs, Ss, None, opts=opts)
+        got = pairs.cpu().numpy()
+        for j, (r, s) in enumerate(joins):
+            want = oracle.brute(r, s) if len(r) * len(s) < 2e7 else oracle.sweep(r, s)
+            np.testing.assert_array_equal(srt(got[offs[j]:offs[j + 1]]), want)
