@@ -53,7 +53,9 @@ extern "C" {
 #define SJ_EOVERFLOW  3   /* caller-owned output too small (see sj_join_into)     */
 #define SJ_ETIMEOUT   4   /* a bounded device-side wait gave up                   */
 #define SJ_ECUDA      5   /* a CUDA runtime call failed                           */
-#define SJ_EINTERNAL  6   /* an internal consistency check failed                 */
+#define SJ_EINTERNAL  6   /* an internal consistency check failed (in the debug
+                             build also a failed bounds check; sj_last_error names
+                             its source file and line)                           */
 
 #define SJ_MAX_N      ((int64_t)1 << 30)   /* ids carry two flag bits above bit 29 */
 #define SJ_MAX_TILES  ((int64_t)1 << 26)   /* nx * ny                               */
