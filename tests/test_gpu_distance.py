@@ -125,12 +125,14 @@ def test_path_points_on_the_fly_and_materialised(sj, ctx):
     got, _ = gpu_dist(sj, ctx, P, Q, 5e-4, 400)
     assert sj.sj_last_stats(ctx)["path"] == 1
     np.testing.assert_array_equal(srt(got), want)
+    # three points repeated thousands of times: their tiles hold more than
+    # 3,072 entries (about 3,300 each)
     rng = np.random.default_rng(45)
-    base = rng.random((12, 2)).astype(np.float32)
-    Ph = np.concatenate([base[rng.integers(0, 12, 60_000)], P[:20_000]])
-    Qh = np.concatenate([base[rng.integers(0, 12, 40_000)], Q[:20_000]])
+    base = rng.random((3, 2)).astype(np.float32)
+    Ph = np.concatenate([base[np.arange(6_000) % 3], P[:20_000]])
+    Qh = np.concatenate([base[np.arange(4_000) % 3], Q[:20_000]])
+    want = oracle.dist_pbsm(Ph, Qh, 2e-3, 50)
     for mode in ("two_pass", "one_pass_heur"):
-        want = oracle.dist_pbsm(Ph, Qh, 2e-3, 50)
         got, _ = gpu_dist(sj, ctx, Ph, Qh, 2e-3, 64, mode=mode)
         assert sj.sj_last_stats(ctx)["path"] == 0
         np.testing.assert_array_equal(srt(got), want)
