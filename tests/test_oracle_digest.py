@@ -67,3 +67,18 @@ def test_digest_sees_changes_not_order():
     assert digest(np.concatenate([p, p[:1]])) != d
     # a transposed pair list (r and s swapped) differs as well
     assert digest(p[:, ::-1]) != d
+
+
+def test_chunked_threaded_digest_equals_whole():
+    """digest_device (chunks copied to the host and digested by several
+    threads, as the full-size GPU tests use it) combines to the digest of the
+    whole set, for chunk sizes that do and do not divide the length."""
+    torch = pytest.importorskip("torch")
+    from pair_digest import digest_device
+
+    rng = np.random.default_rng(5)
+    a = rng.integers(0, 1 << 30, (100_003, 2)).astype(np.int32)
+    whole = digest(a)
+    t = torch.from_numpy(a)
+    for chunk in (1 << 10, 4_096, 100_003, 1 << 20):
+        assert digest_device(t, chunk=chunk, threads=4) == whole
