@@ -853,9 +853,7 @@ __device__ __forceinline__ void band_fill(BJSmem &sm, const BlockCtx &bc, int ta
 #pragma unroll
             for (int u = 0; u < kStageU; u++)
                 if (e[u] >= 0) {
-                    const uint4 *w = entry_words(bc, e[u]);
-                    hd[u] = w[0];
-                    t[u] = w[1];
+                    load_bent(entry_words(bc, e[u]), hd[u], t[u]);
                 }
 #pragma unroll
             for (int u = 0; u < kStageU; u++)
@@ -870,9 +868,7 @@ __device__ __forceinline__ void band_fill(BJSmem &sm, const BlockCtx &bc, int ta
 #pragma unroll
             for (int u = 0; u < kStageU; u++)
                 if (eb + u * NT < n1) {
-                    const uint4 *w = entry_words(bc, eb + u * NT);
-                    hd[u] = w[0];
-                    t[u] = w[1];
+                    load_bent(entry_words(bc, eb + u * NT), hd[u], t[u]);
                 }
 #pragma unroll
             for (int u = 0; u < kStageU; u++)

@@ -27,6 +27,13 @@ struct __align__(32) BEnt {
 };
 
 // One 32-byte store of an L1 entry (a whole sector in one instruction).
+// One L1 entry with one 256-bit load (read-only for the kernel that reads it).
+__device__ __forceinline__ void load_bent(const uint4 *src, uint4 &h, uint4 &t) {
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(h.x), "=r"(h.y), "=r"(h.z), "=r"(h.w), "=r"(t.x), "=r"(t.y), "=r"(t.z), "=r"(t.w)
+                 : "l"(src));
+}
+
 __device__ __forceinline__ void store_bent(BEnt *dst, uint4 h, uint4 t) {
     asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "r"(h.x), "r"(h.y), "r"(h.z),
                  "r"(h.w), "r"(t.x), "r"(t.y), "r"(t.z), "r"(t.w)
