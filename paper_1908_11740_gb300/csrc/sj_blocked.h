@@ -26,7 +26,6 @@ struct __align__(32) BEnt {
     unsigned pad;
 };
 
-// One 32-byte store of an L1 entry (a whole sector in one instruction).
 // One L1 entry with one 256-bit load (read-only for the kernel that reads it).
 __device__ __forceinline__ void load_bent(const uint4 *src, uint4 &h, uint4 &t) {
     asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -34,6 +33,7 @@ __device__ __forceinline__ void load_bent(const uint4 *src, uint4 &h, uint4 &t) 
                  : "l"(src));
 }
 
+// One 32-byte store of an L1 entry (a whole sector in one instruction).
 __device__ __forceinline__ void store_bent(BEnt *dst, uint4 h, uint4 t) {
     asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "r"(h.x), "r"(h.y), "r"(h.z),
                  "r"(h.w), "r"(t.x), "r"(t.y), "r"(t.z), "r"(t.w)

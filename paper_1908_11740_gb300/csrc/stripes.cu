@@ -228,10 +228,12 @@ __global__ void __launch_bounds__(kStThreads, 1) k_stripe_join(StArgs a, BJoinOu
         unsigned my = 0;
         for (int e = threadIdx.x; e < n; e += kStThreads) {
             const bool isS = e < ns;
-            const BEnt &me = isS ? es[e] : er[e - ns];
-            const float4 m = me.mbr;
-            const unsigned pid = me.id;
-            const int cx0 = (int)(me.cx & 0xffffu), cy0 = (int)(me.cy & 0xffffu);
+            uint4 mh, mt2;   // the pivot's entry: MBR, then id, columns, rows
+            load_bent(reinterpret_cast<const uint4 *>(isS ? es + e : er + (e - ns)), mh, mt2);
+            const float4 m = make_float4(__uint_as_float(mh.x), __uint_as_float(mh.y), __uint_as_float(mh.z),
+                                         __uint_as_float(mh.w));
+            const unsigned pid = mt2.x;
+            const int cx0 = (int)(mt2.y & 0xffffu), cy0 = (int)(mt2.z & 0xffffu);
             const float hi = a.vert ? m.w : m.z;
             const float olo = a.vert ? m.x : m.y, ohi = a.vert ? m.z : m.w;
             const unsigned khi = xkey(hi);
@@ -239,17 +241,17 @@ __global__ void __launch_bounds__(kStThreads, 1) k_stripe_join(StArgs a, BJoinOu
                 const unsigned c = SJ_AT(a.st, sm.val[k], n);
                 const bool cS = c < (unsigned)ns;
                 if (cS == isS) continue;   // same side
-                const BEnt &ce = cS ? es[c] : er[c - ns];
-                const float4 cm = ce.mbr;
-                const float clo = a.vert ? cm.x : cm.y, chi = a.vert ? cm.z : cm.w;
+                uint4 ch, ct;   // the candidate's entry
+                load_bent(reinterpret_cast<const uint4 *>(cS ? es + c : er + (c - ns)), ch, ct);
+                const float clo = __uint_as_float(a.vert ? ch.x : ch.y), chi = __uint_as_float(a.vert ? ch.z : ch.w);
                 if (!(clo <= ohi && olo <= chi)) continue;
                 // Eq. 1 in 1D: the pair's reference point lies in this stripe
-                const int ccx0 = (int)(ce.cx & 0xffffu), ccy0 = (int)(ce.cy & 0xffffu);
+                const int ccx0 = (int)(ct.y & 0xffffu), ccy0 = (int)(ct.z & 0xffffu);
                 if (max(cx0, ccx0) != col || max(cy0, ccy0) != row) continue;
                 if (MODE == MODE_COUNT) {
                     my++;
                 } else {
-                    const unsigned oid = ce.id;
+                    const unsigned oid = ct.x;
                     const int2 pr = isS ? make_int2((int)oid, (int)pid) : make_int2((int)pid, (int)oid);
                     const unsigned msk = __activemask();
                     const int leader = __ffs(msk) - 1;
